@@ -1,0 +1,341 @@
+"""FP64 CPU oracle of the brute-force charge-transport Monte Carlo (arXiv 2506.09712).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  The product (the CUDA library and its
+binding) never imports this package, and this package never imports the
+product.  The arithmetic lives in ``cts_oracle.c`` (plain C, FP64, OpenMP);
+this module only marshals arguments through ctypes.
+
+Parameter dictionaries use the same field names as the workload presets in
+``workloads``: sensor geometry and bias, field switches, mobility parameters.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cts_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "libcts_oracle.so")
+
+PHOTON, TRACK, EXPLICIT = 0, 1, 2
+HOLES, BOTH = 1, 3
+MOB_CT, MOB_CONST = 0, 1
+ACTIVE, COLLECTED, RETIRED = 0, 1, 2
+OK, EMAXSTEPS = 0, -6
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP, no fast-math) into _build/."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("thickness_um", C.c_double), ("bias_V", C.c_double), ("depletion_V", C.c_double),
+        ("temperature_K", C.c_double), ("eps_r", C.c_double), ("pitch_um", C.c_double),
+        ("grid_n", C.c_int32), ("dt_ps", C.c_double), ("max_steps", C.c_int64),
+        ("species", C.c_int32), ("softening_um", C.c_double),
+        ("repulsion", C.c_int32), ("drift", C.c_int32), ("diffusion", C.c_int32),
+        ("mob_model", C.c_int32),
+        ("mu0_h", C.c_double), ("vsat_h", C.c_double), ("beta_h", C.c_double),
+        ("mu0_e", C.c_double), ("vsat_e", C.c_double), ("beta_e", C.c_double),
+    ]
+
+
+class _Event(C.Structure):
+    _fields_ = [
+        ("seed", C.c_uint64), ("event_id", C.c_uint64), ("kind", C.c_int32),
+        ("energy_keV", C.c_double), ("n_pairs", C.c_int32), ("depth_um", C.c_double),
+        ("x_um", C.c_double), ("y_um", C.c_double), ("sigma_um", C.c_double),
+        ("track_len_um", C.c_double), ("theta_deg", C.c_double), ("phi_deg", C.c_double),
+        ("explicit_xyz", C.POINTER(C.c_double)), ("explicit_sign", C.POINTER(C.c_int8)),
+    ]
+
+
+class _Result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32), ("n_steps", C.c_int64), ("n_collected", C.c_int64),
+        ("n_outside", C.c_int64), ("n_lost", C.c_int64), ("interactions", C.c_int64),
+        ("pixels", C.POINTER(C.c_int32)), ("final_x", C.POINTER(C.c_double)),
+        ("final_y", C.POINTER(C.c_double)), ("retire_step", C.POINTER(C.c_int32)),
+        ("pos_out", C.POINTER(C.c_double)), ("state_out", C.POINTER(C.c_int8)),
+        ("sign_out", C.POINTER(C.c_int8)),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        d, i64, i32, u32, u64 = C.c_double, C.c_int64, C.c_int32, C.c_uint32, C.c_uint64
+        P = C.POINTER
+        _lib.or_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+        _lib.or_normals3.argtypes = [u64, u64, u32, u32, u32, P(d)]
+        _lib.or_coulomb_k.argtypes = [d]; _lib.or_coulomb_k.restype = d
+        _lib.or_thermal_voltage.argtypes = [d]; _lib.or_thermal_voltage.restype = d
+        _lib.or_n_pairs.argtypes = [d]; _lib.or_n_pairs.restype = i32
+        _lib.or_sigma_um.argtypes = [d]; _lib.or_sigma_um.restype = d
+        _lib.or_drift_field.argtypes = [P(_Params), d]; _lib.or_drift_field.restype = d
+        _lib.or_mobility.argtypes = [P(_Params), C.c_int, d]; _lib.or_mobility.restype = d
+        _lib.or_field_rows.argtypes = [i64, P(d), P(d), P(d), P(C.c_int8), P(C.c_int8),
+                                       P(i64), i64, d, d, C.c_int, P(d), P(d), P(d)]
+        _lib.or_field.argtypes = [i64, P(d), P(d), P(d), P(C.c_int8), P(C.c_int8), d, d,
+                                  C.c_int, P(d), P(d), P(d)]
+        _lib.or_pixel_of.argtypes = [P(_Params), d, d, P(i32), P(i32)]
+        _lib.or_pixel_of.restype = C.c_int
+        _lib.or_bin.argtypes = [P(_Params), i64, P(d), P(d), P(i32), P(i64)]
+        _lib.or_event_carriers.argtypes = [P(_Params), P(_Event)]
+        _lib.or_event_carriers.restype = i64
+        _lib.or_init_event.argtypes = [P(_Params), P(_Event), P(d), P(d), P(d), P(C.c_int8)]
+        _lib.or_run_event.argtypes = [P(_Params), P(_Event), P(_Result), C.c_int]
+        _lib.or_run_event.restype = C.c_int
+        _lib.or_run_events.argtypes = [P(_Params), P(_Event), i64, P(_Result)]
+        _lib.or_max_threads.restype = C.c_int
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+# ----------------------------------------------------------------------------
+# Parameters
+# ----------------------------------------------------------------------------
+def make_params(sensor: dict, field: dict | None = None, mobility: dict | None = None) -> _Params:
+    """Build the oracle's parameter block from preset dictionaries."""
+    field = field or {}
+    mobility = mobility or {}
+    p = _Params()
+    p.thickness_um = sensor["thickness_um"]
+    p.bias_V = sensor["bias_V"]
+    p.depletion_V = sensor["depletion_V"]
+    p.temperature_K = sensor.get("temperature_K", 293.0)
+    p.eps_r = sensor.get("eps_r", 11.7)
+    p.pitch_um = sensor.get("pitch_um", 25.0)
+    p.grid_n = sensor.get("grid_n", 9)
+    p.dt_ps = sensor["dt_ps"]
+    p.max_steps = sensor.get("max_steps", 1_000_000)
+    p.species = sensor.get("species", HOLES)
+    p.softening_um = sensor.get("oracle_softening_um", 0.0)
+    p.repulsion = field.get("repulsion", 1)
+    p.drift = field.get("drift", 1)
+    p.diffusion = field.get("diffusion", 1)
+    p.mob_model = mobility.get("model", MOB_CT)
+    p.mu0_h = mobility["mu0_h"]
+    p.vsat_h = mobility["vsat_h"]
+    p.beta_h = mobility["beta_h"]
+    p.mu0_e = mobility.get("mu0_e", 0.0)
+    p.vsat_e = mobility.get("vsat_e", 1.0)
+    p.beta_e = mobility.get("beta_e", 1.0)
+    return p
+
+
+def make_event(ev: dict, keep: list) -> _Event:
+    e = _Event()
+    e.seed = ev.get("seed", 0)
+    e.event_id = ev.get("event_id", 0)
+    e.kind = ev.get("kind", PHOTON)
+    e.energy_keV = ev.get("energy_keV", 0.0)
+    e.n_pairs = ev.get("n_pairs", 0)
+    e.depth_um = ev.get("depth_um", 0.0)
+    e.x_um = ev.get("x_um", 0.0)
+    e.y_um = ev.get("y_um", 0.0)
+    e.sigma_um = ev.get("sigma_um", -1.0)
+    e.track_len_um = ev.get("track_len_um", 0.0)
+    e.theta_deg = ev.get("theta_deg", 0.0)
+    e.phi_deg = ev.get("phi_deg", 0.0)
+    if e.kind == EXPLICIT:
+        xyz = np.ascontiguousarray(ev["explicit_xyz"], dtype=np.float64).reshape(-1)
+        keep.append(xyz)
+        e.explicit_xyz = _ptr(xyz, C.c_double)
+        e.n_pairs = xyz.size // 3
+        if ev.get("explicit_sign") is not None:
+            sg = np.ascontiguousarray(ev["explicit_sign"], dtype=np.int8)
+            keep.append(sg)
+            e.explicit_sign = _ptr(sg, C.c_int8)
+    return e
+
+
+# ----------------------------------------------------------------------------
+# Small exported pieces (pinned individually by the tests)
+# ----------------------------------------------------------------------------
+def philox4x32_10(ctr, key):
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    lib().or_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def normals3(seed, event_id, purpose, carrier, step):
+    o = (C.c_double * 3)()
+    lib().or_normals3(seed, event_id, purpose, carrier, step, o)
+    return [o[0], o[1], o[2]]
+
+
+def coulomb_k(eps_r=11.7):
+    return lib().or_coulomb_k(eps_r)
+
+
+def thermal_voltage(T):
+    return lib().or_thermal_voltage(T)
+
+
+def n_pairs(energy_keV):
+    return lib().or_n_pairs(energy_keV)
+
+
+def sigma_um(energy_keV):
+    return lib().or_sigma_um(energy_keV)
+
+
+def drift_field(params: _Params, z):
+    return lib().or_drift_field(C.byref(params), z)
+
+
+def mobility(params: _Params, sign, E):
+    return lib().or_mobility(C.byref(params), int(sign), E)
+
+
+def field(xyz, sign=None, active=None, kc=None, eps=0.0, rows=None, parallel=True):
+    """FP64 repulsion field (Eq. 4 read as a field) at `rows` (default: all)."""
+    xyz = np.asarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    x = np.ascontiguousarray(xyz[:, 0]); y = np.ascontiguousarray(xyz[:, 1])
+    z = np.ascontiguousarray(xyz[:, 2])
+    sg = None if sign is None else np.ascontiguousarray(sign, dtype=np.int8)
+    ac = None if active is None else np.ascontiguousarray(active, dtype=np.int8)
+    if kc is None:
+        kc = coulomb_k()
+    rows = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    ex = np.zeros(rows.size); ey = np.zeros(rows.size); ez = np.zeros(rows.size)
+    lib().or_field_rows(n, _ptr(x, C.c_double), _ptr(y, C.c_double), _ptr(z, C.c_double),
+                        _ptr(sg, C.c_int8), _ptr(ac, C.c_int8), _ptr(rows, C.c_int64),
+                        rows.size, kc, eps, 1 if parallel else 0,
+                        _ptr(ex, C.c_double), _ptr(ey, C.c_double), _ptr(ez, C.c_double))
+    return np.stack([ex, ey, ez], axis=1)
+
+
+def pixel_of(params: _Params, x, y):
+    ix = C.c_int32(); iy = C.c_int32()
+    ok = lib().or_pixel_of(C.byref(params), x, y, C.byref(ix), C.byref(iy))
+    return (ix.value, iy.value) if ok else None
+
+
+def bin_positions(params: _Params, x, y):
+    x = np.ascontiguousarray(x, dtype=np.float64); y = np.ascontiguousarray(y, dtype=np.float64)
+    pix = np.zeros(params.grid_n * params.grid_n, dtype=np.int32)
+    out = C.c_int64(0)
+    lib().or_bin(C.byref(params), x.size, _ptr(x, C.c_double), _ptr(y, C.c_double),
+                 _ptr(pix, C.c_int32), C.byref(out))
+    return pix.reshape(params.grid_n, params.grid_n), out.value
+
+
+def init_event(params: _Params, ev: dict):
+    keep = []
+    e = make_event(ev, keep)
+    n = lib().or_event_carriers(C.byref(params), C.byref(e))
+    x = np.zeros(n); y = np.zeros(n); z = np.zeros(n); s = np.zeros(n, dtype=np.int8)
+    lib().or_init_event(C.byref(params), C.byref(e), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                        _ptr(z, C.c_double), _ptr(s, C.c_int8))
+    return np.stack([x, y, z], axis=1), s
+
+
+# ----------------------------------------------------------------------------
+# Whole events (Algorithm 1)
+# ----------------------------------------------------------------------------
+@dataclass
+class EventResult:
+    status: int
+    n_steps: int
+    n_collected: int
+    n_outside: int
+    n_lost: int
+    interactions: int
+    pixels: np.ndarray
+    final_xy: np.ndarray
+    retire_step: np.ndarray
+    pos: np.ndarray
+    state: np.ndarray
+    sign: np.ndarray
+
+
+def _alloc_result(params, n):
+    bufs = dict(pixels=np.zeros(params.grid_n * params.grid_n, dtype=np.int32),
+                fx=np.zeros(max(n, 1)), fy=np.zeros(max(n, 1)),
+                rs=np.zeros(max(n, 1), dtype=np.int32), pos=np.zeros(3 * max(n, 1)),
+                st=np.zeros(max(n, 1), dtype=np.int8), sg=np.zeros(max(n, 1), dtype=np.int8))
+    r = _Result()
+    r.pixels = _ptr(bufs["pixels"], C.c_int32)
+    r.final_x = _ptr(bufs["fx"], C.c_double)
+    r.final_y = _ptr(bufs["fy"], C.c_double)
+    r.retire_step = _ptr(bufs["rs"], C.c_int32)
+    r.pos_out = _ptr(bufs["pos"], C.c_double)
+    r.state_out = _ptr(bufs["st"], C.c_int8)
+    r.sign_out = _ptr(bufs["sg"], C.c_int8)
+    return r, bufs
+
+
+def _wrap(params, r, bufs, n):
+    return EventResult(
+        status=r.status, n_steps=r.n_steps, n_collected=r.n_collected, n_outside=r.n_outside,
+        n_lost=r.n_lost, interactions=r.interactions,
+        pixels=bufs["pixels"].reshape(params.grid_n, params.grid_n).copy(),
+        final_xy=np.stack([bufs["fx"][:n], bufs["fy"][:n]], axis=1),
+        retire_step=bufs["rs"][:n].copy(), pos=bufs["pos"][:3 * n].reshape(n, 3).copy(),
+        state=bufs["st"][:n].copy(), sign=bufs["sg"][:n].copy())
+
+
+def run_events(params: _Params, events: list[dict]) -> list[EventResult]:
+    """Run independent events (OpenMP across events when there are several)."""
+    keep = []
+    evs = (_Event * max(len(events), 1))()
+    for k, ev in enumerate(events):
+        evs[k] = make_event(ev, keep)
+    results = (_Result * max(len(events), 1))()
+    sizes, bufl = [], []
+    for k in range(len(events)):
+        n = lib().or_event_carriers(C.byref(params), C.byref(evs[k]))
+        r, b = _alloc_result(params, n)
+        results[k] = r
+        sizes.append(n); bufl.append(b)
+    if len(events) == 1:
+        lib().or_run_event(C.byref(params), C.byref(evs[0]), C.byref(results[0]), 1)
+    elif events:
+        lib().or_run_events(C.byref(params), evs, len(events), results)
+    return [_wrap(params, results[k], bufl[k], sizes[k]) for k in range(len(events))]
+
+
+def run_event(params: _Params, ev: dict) -> EventResult:
+    return run_events(params, [ev])[0]
+
+
+def max_threads() -> int:
+    return lib().or_max_threads()
+
+
+def count_interactions(retire_step: np.ndarray, n_steps: int) -> int:
+    """Sum over steps of N_act (N_act - 1), from per-carrier retire steps."""
+    rs = np.asarray(retire_step, dtype=np.int64)
+    total = 0
+    for k in range(n_steps):
+        a = int(np.count_nonzero((rs == -2) | (rs >= k)))
+        total += a * (a - 1)
+    return total
+

@@ -1,0 +1,483 @@
+/*
+ * cts_oracle.c -- plain FP64 CPU oracle of the brute-force drift-diffusion-
+ * repulsion charge-transport Monte Carlo (Xie et al., "Optimization and
+ * validation of charge transport simulation for hybrid pixel detectors
+ * incorporating the repulsion effect", arXiv 2506.09712).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * execute this file; only the test suite, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no source with the CUDA path.
+ *
+ * Everything here is written for clarity, not speed: double loops, FP64,
+ * one OpenMP pragma over carriers (or over events).  Each function names the
+ * passage of the paper (or the published definition) it follows.
+ *
+ * Frame and units (readings of the paper, all listed in the design notes):
+ *   lengths in um, times in ns, potentials in V, fields in V/um,
+ *   mobilities in um^2/(V ns), velocities in um/ns.
+ *   z is measured from the collecting (pixel) surface: z = 0 is the readout
+ *   electrode, z = H the entrance (back) surface.  The paper's Eq. 6 puts the
+ *   entrance at z_paper = 0, so z = H - z_paper and the drift-field vector is
+ *   -E(z) e_z with E(z) = (Vb - Vd)/H + 2 Vd (H - z)/H^2.
+ *
+ * Parity status: pinned (closed forms, invariants, a library Philox, exact
+ * small configurations) -- see tests/test_oracle_*.py.  The paper's own
+ * printed physics numbers (Table 1, GGD betas) depend on unprinted mobility
+ * parameters and are checked only qualitatively.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Physical constants: SI 2019 exact values (e, k_B) and CODATA 2018 eps0.   */
+/* ------------------------------------------------------------------------ */
+static const double OR_E_CHARGE = 1.602176634e-19;  /* C   */
+static const double OR_EPS0 = 8.8541878128e-12;     /* F/m */
+static const double OR_KB = 1.380649e-23;           /* J/K */
+static const double OR_PI = 3.14159265358979323846;
+/* Section 2: 3.62 eV per electron-hole pair. */
+static const double OR_EV_PER_PAIR = 3.62;
+
+enum { OR_OK = 0, OR_EMAXSTEPS = -6, OR_EINVAL = -1 };
+enum { OR_HOLES = 1, OR_BOTH = 3 };
+enum { OR_MOB_CT = 0, OR_MOB_CONST = 1 };
+enum { OR_PHOTON = 0, OR_TRACK = 1, OR_EXPLICIT = 2 };
+enum { OR_ACTIVE = 0, OR_COLLECTED = 1, OR_RETIRED = 2 };
+enum { OR_PURPOSE_DIFFUSION = 0, OR_PURPOSE_INIT = 1 };
+
+typedef struct {
+  double thickness_um;   /* H */
+  double bias_V;         /* V_bias */
+  double depletion_V;    /* V_depletion */
+  double temperature_K;  /* T */
+  double eps_r;          /* relative permittivity, 11.7 for Si (Sec. 2.1) */
+  double pitch_um;       /* pixel pitch */
+  int32_t grid_n;        /* pixels per side of the readout grid */
+  double dt_ps;          /* time step */
+  int64_t max_steps;     /* step cap */
+  int32_t species;       /* OR_HOLES or OR_BOTH */
+  double softening_um;   /* Plummer softening; 0 = exact Eq. 4 */
+  int32_t repulsion, drift, diffusion; /* switches of the three terms */
+  int32_t mob_model;     /* OR_MOB_CT or OR_MOB_CONST */
+  double mu0_h, vsat_h, beta_h; /* holes: cm^2/Vs, cm/s, - */
+  double mu0_e, vsat_e, beta_e; /* electrons */
+} or_params_t;
+
+typedef struct {
+  uint64_t seed, event_id;
+  int32_t kind;
+  double energy_keV;
+  int32_t n_pairs;        /* 0: round(E / 3.62 eV) */
+  double depth_um;        /* absorption depth below the entrance surface */
+  double x_um, y_um;      /* entry point */
+  double sigma_um;        /* < 0: Eq. 2 */
+  double track_len_um, theta_deg, phi_deg; /* OR_TRACK */
+  const double* explicit_xyz; /* OR_EXPLICIT: 3*n_pairs, x0 y0 z0 x1 ... */
+  const int8_t* explicit_sign; /* +1 hole, -1 electron; NULL = all holes */
+} or_event_t;
+
+typedef struct {
+  int32_t status;
+  int64_t n_steps, n_collected, n_outside, n_lost, interactions;
+  int32_t* pixels;      /* grid_n^2, may be NULL */
+  double* final_x;      /* per carrier; holes that were collected */
+  double* final_y;
+  int32_t* retire_step; /* per carrier; -2 = never retired */
+  double* pos_out;      /* 3 * n_carriers, positions when the run stopped */
+  int8_t* state_out;    /* per carrier */
+  int8_t* sign_out;     /* per carrier */
+} or_result_t;
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11): four 32-bit counter words, two key words, ten   */
+/* rounds of two 32x32->64 multiplies; the key is bumped by the Weyl        */
+/* constants between rounds.                                                 */
+/* ------------------------------------------------------------------------ */
+void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2],
+                      uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+  uint32_t k0 = key_in[0], k1 = key_in[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n1 = lo1;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    uint32_t n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The stream layout of this project: key = seed, counter = (carrier, step,
+ * event low word, event high word XOR purpose << 28). */
+static void or_stream_words(uint64_t seed, uint64_t event_id, uint32_t purpose,
+                            uint32_t carrier, uint32_t step, uint32_t out[4]) {
+  uint32_t ctr[4] = {carrier, step, (uint32_t)event_id,
+                     (uint32_t)(event_id >> 32) ^ (purpose << 28)};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  or_philox4x32_10(ctr, key, out);
+}
+
+/* Uniform in (0,1) from the top 24 bits: ((w >> 8) + 1/2) / 2^24. */
+static double or_uniform(uint32_t w) {
+  return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0);
+}
+
+/* Three standard normals by the Box-Muller transform (Box & Muller 1958):
+ * (n0, n1) from the pair (u0, u1), n2 from the cosine branch of (u2, u3). */
+void or_normals3(uint64_t seed, uint64_t event_id, uint32_t purpose,
+                 uint32_t carrier, uint32_t step, double n[3]) {
+  uint32_t w[4];
+  or_stream_words(seed, event_id, purpose, carrier, step, w);
+  double u0 = or_uniform(w[0]), u1 = or_uniform(w[1]);
+  double u2 = or_uniform(w[2]), u3 = or_uniform(w[3]);
+  double r01 = sqrt(-2.0 * log(u0));
+  double r23 = sqrt(-2.0 * log(u2));
+  n[0] = r01 * cos(2.0 * OR_PI * u1);
+  n[1] = r01 * sin(2.0 * OR_PI * u1);
+  n[2] = r23 * cos(2.0 * OR_PI * u3);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Material model                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* k_C = e / (4 pi eps0 eps_r), in V um (Eq. 4 prefactor per unit charge). */
+double or_coulomb_k(double eps_r) {
+  return OR_E_CHARGE / (4.0 * OR_PI * OR_EPS0 * eps_r) * 1.0e6;
+}
+
+/* kT/e in V (Einstein relation, Eq. 1: D = mu kT/e). */
+double or_thermal_voltage(double temperature_K) {
+  return OR_KB * temperature_K / OR_E_CHARGE;
+}
+
+/* Carrier count, Section 2 and Algorithm 1: N = round(E / 3.62 eV). */
+int32_t or_n_pairs(double energy_keV) {
+  return (int32_t)lround(energy_keV * 1000.0 / OR_EV_PER_PAIR);
+}
+
+/* Initial cloud width, Eq. 2: sigma = 0.0044 * E^1.75 um (E in keV). */
+double or_sigma_um(double energy_keV) {
+  return 0.0044 * pow(energy_keV, 1.75);
+}
+
+/* Drift-field magnitude, Eq. 6, with z measured from the pixel side. */
+double or_drift_field(const or_params_t* P, double z) {
+  double H = P->thickness_um;
+  return (P->bias_V - P->depletion_V) / H +
+         2.0 * P->depletion_V * (H - z) / (H * H);
+}
+
+/* Field-dependent mobility (Sec. 2.1, Jacoboni-Canali form):
+ * mu(E) = mu0 / (1 + (mu0 E / vsat)^beta)^(1/beta); returns um^2/(V ns). */
+double or_mobility(const or_params_t* P, int sign, double E) {
+  double mu0 = (sign > 0 ? P->mu0_h : P->mu0_e) * 0.1;   /* cm^2/Vs -> um^2/(V ns) */
+  double vsat = (sign > 0 ? P->vsat_h : P->vsat_e) * 1e-5; /* cm/s -> um/ns */
+  double beta = sign > 0 ? P->beta_h : P->beta_e;
+  if (P->mob_model == OR_MOB_CONST) return mu0;
+  return mu0 / pow(1.0 + pow(mu0 * E / vsat, beta), 1.0 / beta);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Repulsion field, Eq. 4, read as a field: E_i = sum_{j != i} q_j r_ij /    */
+/* (4 pi eps0 eps_r |r_ij|^3), r_ij from carrier j to carrier i.  The       */
+/* printed q_i q_j is a force; the velocity below carries the sign of q_i.  */
+/* With softening eps > 0 the denominator is (r^2 + eps^2)^(3/2).  A pair   */
+/* at zero distance (with eps = 0) contributes nothing.                     */
+/* Rows in [row0, row1) are computed; only active carriers are sources.     */
+/* ------------------------------------------------------------------------ */
+void or_field_rows(int64_t n, const double* x, const double* y, const double* z,
+                   const int8_t* sign, const int8_t* active,
+                   const int64_t* rows, int64_t n_rows, double kc, double eps,
+                   int parallel, double* ex, double* ey, double* ez) {
+  double eps2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16) if (parallel)
+  for (int64_t r = 0; r < n_rows; ++r) {
+    int64_t i = rows[r];
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      if (j == i) continue;
+      if (active && active[j] != OR_ACTIVE) continue;
+      double dx = x[i] - x[j], dy = y[i] - y[j], dz = z[i] - z[j];
+      double r2 = dx * dx + dy * dy + dz * dz + eps2;
+      if (r2 == 0.0) continue;
+      double inv_r3 = 1.0 / (r2 * sqrt(r2));
+      double q = sign ? (double)sign[j] : 1.0;
+      sx += q * dx * inv_r3;
+      sy += q * dy * inv_r3;
+      sz += q * dz * inv_r3;
+    }
+    ex[r] = kc * sx;
+    ey[r] = kc * sy;
+    ez[r] = kc * sz;
+  }
+}
+
+void or_field(int64_t n, const double* x, const double* y, const double* z,
+              const int8_t* sign, const int8_t* active, double kc, double eps,
+              int parallel, double* ex, double* ey, double* ez) {
+  int64_t* rows = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) rows[i] = i;
+  or_field_rows(n, x, y, z, sign, active, rows, n, kc, eps, parallel, ex, ey, ez);
+  free(rows);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Readout: pixel index floor(x / pitch + n/2) on a grid centred on x = 0.   */
+/* ------------------------------------------------------------------------ */
+int or_pixel_of(const or_params_t* P, double x, double y, int32_t* ix, int32_t* iy) {
+  double fx = floor(x / P->pitch_um + 0.5 * (double)P->grid_n);
+  double fy = floor(y / P->pitch_um + 0.5 * (double)P->grid_n);
+  if (fx < 0.0 || fy < 0.0 || fx >= (double)P->grid_n || fy >= (double)P->grid_n)
+    return 0;
+  *ix = (int32_t)fx;
+  *iy = (int32_t)fy;
+  return 1;
+}
+
+void or_bin(const or_params_t* P, int64_t n, const double* x, const double* y,
+            int32_t* pixels, int64_t* outside) {
+  int64_t out = 0;
+  for (int64_t c = 0; c < n; ++c) {
+    int32_t ix, iy;
+    if (or_pixel_of(P, x[c], y[c], &ix, &iy))
+      pixels[(int64_t)iy * P->grid_n + ix] += 1;
+    else
+      ++out;
+  }
+  *outside += out;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Event initialisation (Algorithm 1, first step; Sec. 2.1 and Eq. 2).       */
+/* ------------------------------------------------------------------------ */
+int64_t or_event_carriers(const or_params_t* P, const or_event_t* ev) {
+  int64_t n = ev->kind == OR_EXPLICIT ? ev->n_pairs
+              : (ev->n_pairs > 0 ? ev->n_pairs : or_n_pairs(ev->energy_keV));
+  if (ev->kind == OR_EXPLICIT) return n;
+  return P->species == OR_BOTH ? 2 * n : n;
+}
+
+void or_init_event(const or_params_t* P, const or_event_t* ev, double* x,
+                   double* y, double* z, int8_t* sign) {
+  if (ev->kind == OR_EXPLICIT) {
+    for (int64_t c = 0; c < ev->n_pairs; ++c) {
+      x[c] = ev->explicit_xyz[3 * c + 0];
+      y[c] = ev->explicit_xyz[3 * c + 1];
+      z[c] = ev->explicit_xyz[3 * c + 2];
+      sign[c] = ev->explicit_sign ? ev->explicit_sign[c] : (int8_t)1;
+    }
+    return;
+  }
+  int64_t np = ev->n_pairs > 0 ? ev->n_pairs : or_n_pairs(ev->energy_keV);
+  double sigma = ev->sigma_um >= 0.0 ? ev->sigma_um : or_sigma_um(ev->energy_keV);
+  double z_entry = P->thickness_um - ev->depth_um;
+  /* Track direction: polar angle theta from the inward normal (-e_z), azimuth
+   * phi; the segment starts at the entry point on the back surface. */
+  double th = ev->theta_deg * OR_PI / 180.0, ph = ev->phi_deg * OR_PI / 180.0;
+  double ux = sin(th) * cos(ph), uy = sin(th) * sin(ph), uz = -cos(th);
+  /* two unit vectors perpendicular to the track */
+  double ax = cos(th) * cos(ph), ay = cos(th) * sin(ph), az = sin(th);
+  double bx = -sin(ph), by = cos(ph), bz = 0.0;
+  for (int64_t p = 0; p < np; ++p) {
+    double n[3];
+    or_normals3(ev->seed, ev->event_id, OR_PURPOSE_INIT, (uint32_t)p, 0u, n);
+    double cx, cy, cz;
+    if (ev->kind == OR_TRACK) {
+      uint32_t w[4];
+      or_stream_words(ev->seed, ev->event_id, OR_PURPOSE_INIT, (uint32_t)p, 1u, w);
+      double s = or_uniform(w[0]) * ev->track_len_um;
+      cx = ev->x_um + s * ux + sigma * (n[0] * ax + n[1] * bx);
+      cy = ev->y_um + s * uy + sigma * (n[0] * ay + n[1] * by);
+      cz = P->thickness_um + s * uz + sigma * (n[0] * az + n[1] * bz);
+    } else {
+      cx = ev->x_um + sigma * n[0];
+      cy = ev->y_um + sigma * n[1];
+      cz = z_entry + sigma * n[2];
+    }
+    x[p] = cx; y[p] = cy; z[p] = cz; sign[p] = 1;
+    if (P->species == OR_BOTH) {
+      x[np + p] = cx; y[np + p] = cy; z[np + p] = cz; sign[np + p] = -1;
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Boundaries.  Holes reaching z <= 0 are collected by the readout (stop    */
+/* rule of Sec. 2.1); holes beyond the back surface are reflected.          */
+/* Electrons reaching z >= H leave through the back contact; electrons      */
+/* below z = 0 are reflected.                                               */
+/* ------------------------------------------------------------------------ */
+static void or_boundaries(const or_params_t* P, int64_t n, double* x, double* y,
+                          double* z, const int8_t* sign, int8_t* state,
+                          int64_t step, or_result_t* R) {
+  double H = P->thickness_um;
+  for (int64_t c = 0; c < n; ++c) {
+    if (state[c] != OR_ACTIVE) continue;
+    if (sign[c] > 0) {
+      if (z[c] <= 0.0) {
+        state[c] = OR_COLLECTED;
+        if (R->final_x) R->final_x[c] = x[c];
+        if (R->final_y) R->final_y[c] = y[c];
+        if (R->retire_step) R->retire_step[c] = (int32_t)step;
+      } else if (z[c] > H) {
+        z[c] = 2.0 * H - z[c];
+      }
+    } else {
+      if (z[c] >= H) {
+        state[c] = OR_RETIRED;
+        if (R->retire_step) R->retire_step[c] = (int32_t)step;
+      } else if (z[c] < 0.0) {
+        z[c] = -z[c];
+      }
+    }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One event, Algorithm 1: repeat {repulsion field of every carrier from the */
+/* positions at the start of the step; drift field Eq. 6; mobility from     */
+/* |E_drift + E_repulsion|; D = mu kT/e; x, y by Eq. 3 and z by Eq. 5 with  */
+/* Gaussian steps of variance 2 D dt} until every hole is collected.         */
+/* ------------------------------------------------------------------------ */
+int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
+                 int parallel) {
+  int64_t n = or_event_carriers(P, ev);
+  double* x = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* y = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* z = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* ex = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* ey = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* ez = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  int64_t* rows = (int64_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int64_t));
+  int8_t* sign = (int8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  int8_t* state = (int8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+
+  double kc = or_coulomb_k(P->eps_r);
+  double kT = or_thermal_voltage(P->temperature_K);
+  double dt = P->dt_ps * 1e-3; /* ps -> ns */
+
+  double* nx = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* ny = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* nz = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+
+  R->status = OR_OK;
+  R->n_steps = R->n_collected = R->n_outside = R->n_lost = R->interactions = 0;
+  if (R->pixels)
+    memset(R->pixels, 0, sizeof(int32_t) * (size_t)P->grid_n * (size_t)P->grid_n);
+  if (R->retire_step)
+    for (int64_t c = 0; c < n; ++c) R->retire_step[c] = -2;
+  if (R->final_x)
+    for (int64_t c = 0; c < n; ++c) R->final_x[c] = NAN;
+  if (R->final_y)
+    for (int64_t c = 0; c < n; ++c) R->final_y[c] = NAN;
+
+  or_init_event(P, ev, x, y, z, sign);
+  for (int64_t c = 0; c < n; ++c) state[c] = OR_ACTIVE;
+  or_boundaries(P, n, x, y, z, sign, state, -1, R);
+
+  int64_t step = 0;
+  for (;; ++step) {
+    int64_t holes_active = 0, n_act = 0;
+    for (int64_t c = 0; c < n; ++c) {
+      if (state[c] != OR_ACTIVE) continue;
+      rows[n_act++] = c;
+      if (sign[c] > 0) ++holes_active;
+    }
+    if (holes_active == 0) break;
+    if (step >= P->max_steps) { R->status = OR_EMAXSTEPS; break; }
+    R->interactions += n_act * (n_act - 1);
+
+    /* Field of every active carrier from the positions at the step start. */
+    if (P->repulsion) {
+      or_field_rows(n, x, y, z, sign, state, rows, n_act, kc, P->softening_um,
+                    parallel, ex, ey, ez);
+    } else {
+      for (int64_t r = 0; r < n_act; ++r) ex[r] = ey[r] = ez[r] = 0.0;
+    }
+    /* Moves (all from step-start positions, then committed together). */
+#pragma omp parallel for schedule(static) if (parallel)
+    for (int64_t r = 0; r < n_act; ++r) {
+      int64_t c = rows[r];
+      double Ex = ex[r], Ey = ey[r], Ez = ez[r];
+      if (P->drift) Ez += -or_drift_field(P, z[c]);
+      double Emag = sqrt(Ex * Ex + Ey * Ey + Ez * Ez);
+      double mu = or_mobility(P, sign[c], Emag);
+      double s = (double)sign[c];
+      double dx = s * mu * Ex * dt, dy = s * mu * Ey * dt, dz = s * mu * Ez * dt;
+      if (P->diffusion) {
+        double D = mu * kT;
+        double g[3];
+        or_normals3(ev->seed, ev->event_id, OR_PURPOSE_DIFFUSION, (uint32_t)c,
+                    (uint32_t)step, g);
+        double a = sqrt(2.0 * D * dt);
+        dx += a * g[0]; dy += a * g[1]; dz += a * g[2];
+      }
+      nx[r] = x[c] + dx; ny[r] = y[c] + dy; nz[r] = z[c] + dz;
+    }
+    for (int64_t r = 0; r < n_act; ++r) {
+      int64_t c = rows[r];
+      x[c] = nx[r]; y[c] = ny[r]; z[c] = nz[r];
+    }
+    or_boundaries(P, n, x, y, z, sign, state, step, R);
+  }
+  R->n_steps = step;
+
+  /* Readout of the collected holes; electrons still moving are dropped. */
+  int64_t outside = 0;
+  for (int64_t c = 0; c < n; ++c) {
+    if (state[c] == OR_COLLECTED) {
+      R->n_collected += 1;
+      int32_t ix, iy;
+      if (or_pixel_of(P, x[c], y[c], &ix, &iy)) {
+        if (R->pixels) R->pixels[(int64_t)iy * P->grid_n + ix] += 1;
+      } else {
+        ++outside;
+      }
+    } else if (state[c] == OR_ACTIVE && sign[c] < 0) {
+      R->n_lost += 1;
+    }
+  }
+  R->n_outside = outside;
+  if (R->pos_out)
+    for (int64_t c = 0; c < n; ++c) {
+      R->pos_out[3 * c + 0] = x[c];
+      R->pos_out[3 * c + 1] = y[c];
+      R->pos_out[3 * c + 2] = z[c];
+    }
+  if (R->state_out) memcpy(R->state_out, state, (size_t)n);
+  if (R->sign_out) memcpy(R->sign_out, sign, (size_t)n);
+
+  free(x); free(y); free(z); free(ex); free(ey); free(ez);
+  free(nx); free(ny); free(nz);
+  free(rows); free(sign); free(state);
+  return R->status;
+}
+
+/* Independent events in parallel (one OpenMP thread per event). */
+void or_run_events(const or_params_t* P, const or_event_t* evs, int64_t n_ev,
+                   or_result_t* R) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t e = 0; e < n_ev; ++e) or_run_event(P, &evs[e], &R[e], 0);
+}
+
+int or_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
