@@ -1,0 +1,247 @@
+/*
+ * cts.h -- C ABI of the GB300 (sm_103a) charge-transport library.
+ *
+ * The library simulates the brute-force drift-diffusion-repulsion Monte Carlo
+ * of Xie et al., arXiv 2506.09712 (Sec. 2.1 and Algorithm 1): the cloud of
+ * electron-hole pairs that one X-ray photon (or one electron track) leaves in
+ * a planar silicon sensor is stepped in time; each step computes the O(N^2)
+ * Coulomb field on every carrier (Eq. 4), adds the sensor's drift field
+ * (Eq. 6), moves each carrier by mu(|E|) E dt plus a Gaussian diffusion step
+ * of variance 2 D dt per axis with D = mu kT/e (Eqs. 1, 3, 5), collects holes
+ * at the readout surface and finally bins the collected holes into pixels
+ * (the readout of Sec. 4.2).
+ *
+ * Units: lengths um, times ps (dt) / ns (results), potentials V, mobility
+ * cm^2/(V s), saturation velocity cm/s, temperature K.  Frame: z is measured
+ * from the collecting (pixel) surface, z = 0 the readout electrode and
+ * z = thickness the entrance surface; the drift field is -E(z) e_z with
+ * E(z) = (V_bias - V_depletion)/H + 2 V_depletion (H - z)/H^2 (Eq. 6 with
+ * z = H - z_paper).  The pixel grid is grid_n x grid_n pixels of pitch_um,
+ * centred on x = y = 0: pixel index floor(x / pitch + grid_n / 2).
+ *
+ * Conventions of every entry point:
+ *   - return 0 (SIM_OK) or a negative SIM_E* code; no exceptions or aborts
+ *     cross the ABI; sim_strerror() names a code;
+ *   - pointers are host pointers unless the name says dev_; the library copies
+ *     what it needs before returning and never keeps a caller pointer;
+ *   - the handle owns all device memory it allocates (cudaMalloc at sim_init,
+ *     sized by sim_options_t) and frees it in sim_destroy;
+ *   - one thread may call sim_submit while another calls sim_poll; any other
+ *     concurrent use of one handle is not allowed.
+ */
+#ifndef CTS_H_
+#define CTS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define SIM_OK 0
+#define SIM_EINVAL (-1)        /* invalid argument or parameter */
+#define SIM_ENOMEM_BUDGET (-2) /* event larger than the handle's device budget */
+#define SIM_EAGAIN (-3)        /* admission queue full: retry later */
+#define SIM_ETIMEOUT (-4)      /* sim_poll: nothing completed in time; or a
+                                  bounded device wait gave up */
+#define SIM_ECUDA (-5)         /* a CUDA call failed (the handle is unusable) */
+#define SIM_EMAXSTEPS (-6)     /* per event: step cap reached, holes remain */
+#define SIM_ENUMERIC (-7)      /* per event: non-finite field or position */
+#define SIM_ESTATE (-8)        /* call not valid in this mode or state */
+#define SIM_ENODEV (-9)        /* no CUDA device, or not an sm_103 device */
+
+/* ---- enumerations ------------------------------------------------------- */
+#define CTS_HOLES 1      /* only holes are tracked (the readout collects holes) */
+#define CTS_BOTH 3       /* electrons and holes (Sec. 2.1: both species) */
+#define CTS_MOB_CT 0     /* mu0 / (1 + (mu0 E / vsat)^beta)^(1/beta) */
+#define CTS_MOB_CONST 1  /* mu = mu0 (closed-form tests) */
+#define CTS_PHOTON 0     /* Gaussian cloud around the absorption point */
+#define CTS_TRACK 1      /* pairs uniform along a straight segment */
+#define CTS_EXPLICIT 2   /* initial positions given by the caller */
+#define CTS_MODE_PLAIN 0   /* one event at a time, two launches per step */
+#define CTS_MODE_BATCHED 1 /* resident events packed per launch, graph chunks */
+#define CTS_MODE_SERVE 2   /* BATCHED driven by a background engine thread */
+
+/* Sensor and stepping (Sec. 2; Algorithm 1 inputs H, T, V_bias, V_depletion).
+ * species: CTS_HOLES or CTS_BOTH.  softening_um: Plummer length eps in the
+ * pair field (r^2 + eps^2)^(-3/2); 0 selects the default 1e-6 um. */
+typedef struct sim_sensor_t {
+  double thickness_um;
+  double bias_V;
+  double depletion_V;
+  double temperature_K;
+  double eps_r;
+  double pitch_um;
+  double dt_ps;
+  double softening_um;
+  int64_t max_steps;
+  int32_t grid_n;
+  int32_t species;
+} sim_sensor_t;
+
+/* Switches of the three transport terms (1 = on); all on reproduces Eqs. 3, 5. */
+typedef struct sim_field_t {
+  int32_t repulsion;
+  int32_t drift;
+  int32_t diffusion;
+  int32_t reserved;
+} sim_field_t;
+
+/* Field-dependent mobility (Sec. 2.1, Jacoboni-Canali form), per species. */
+typedef struct sim_mobility_t {
+  int32_t model;      /* CTS_MOB_CT or CTS_MOB_CONST */
+  int32_t reserved;
+  double mu0_h, vsat_h, beta_h; /* holes: cm^2/Vs, cm/s, exponent */
+  double mu0_e, vsat_e, beta_e; /* electrons (CTS_BOTH only) */
+} sim_mobility_t;
+
+/* Execution options.  Zero fields select defaults. */
+typedef struct sim_options_t {
+  int32_t mode;            /* CTS_MODE_* */
+  int32_t device;          /* CUDA device ordinal */
+  int32_t max_slots;       /* events resident at once (default 256) */
+  int32_t chunk_steps;     /* steps per chunk between host checks (default 32) */
+  int64_t max_carriers;    /* carrier arena capacity (default: from budget) */
+  int64_t hbm_budget_bytes;/* device bytes the handle may allocate (default 1 GiB) */
+  int32_t queue_capacity;  /* bound of the admission queue (default 65536) */
+  int32_t variant;         /* pair-kernel variant + 1; 0 = default choice */
+  int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
+  int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */
+  void* stream;            /* cudaStream_t to launch on; NULL = own stream */
+} sim_options_t;
+
+/* One event (Algorithm 1 inputs: E, absorption depth h, plus the entry point).
+ * n_pairs = 0 takes round(E / 3.62 eV) (Sec. 2); sigma_um < 0 takes Eq. 2,
+ * sigma = 0.0044 E^1.75 um.  With CTS_BOTH each pair is one hole and one
+ * electron at the same start point.  CTS_TRACK: segment of track_len_um from
+ * the entry point on the back surface, polar angle theta from the inward
+ * normal, azimuth phi, Gaussian sigma perpendicular to it.  CTS_EXPLICIT:
+ * explicit_xyz holds n_pairs positions (x0 y0 z0 x1 ...), explicit_sign +1
+ * (hole) / -1 (electron) or NULL for all holes; both are copied at submit. */
+typedef struct sim_event_t {
+  uint64_t event_id;
+  uint64_t seed;
+  int32_t kind;
+  int32_t n_pairs;
+  double energy_keV;
+  double depth_um;
+  double x_um, y_um;
+  double sigma_um;
+  double track_len_um, theta_deg, phi_deg;
+  const double* explicit_xyz;
+  const int8_t* explicit_sign;
+} sim_event_t;
+
+/* One completed event.  The caller owns the arrays and sets their pointers
+ * (and capacity) before sim_poll / sim_collect; NULL arrays are skipped.
+ * final_xy: (x, y) at collection per carrier id (NaN if not collected);
+ * retire_step: step of collection/exit per carrier id, -1 = before the first
+ * step, -2 = never.  Times are host steady-clock ns. */
+typedef struct sim_result_t {
+  uint64_t event_id;
+  int32_t status;        /* SIM_OK, SIM_EMAXSTEPS, SIM_ENUMERIC */
+  int32_t n_carriers;    /* carriers of the event (both species) */
+  int64_t n_steps;       /* steps executed until every hole was collected */
+  int64_t n_collected;   /* holes collected by the readout */
+  int64_t n_outside;     /* collected holes outside the pixel grid */
+  int64_t n_lost;        /* electrons still moving when the event stopped */
+  int64_t interactions;  /* sum over steps of N_act (N_act - 1) */
+  double t_submit_ns, t_start_ns, t_done_ns;
+  int32_t* pixels;       /* grid_n * grid_n counts, row-major [iy][ix] */
+  double* final_xy;      /* 2 * capacity */
+  int32_t* retire_step;  /* capacity */
+  int64_t capacity;      /* entries available in final_xy / retire_step */
+} sim_result_t;
+
+typedef struct sim_stats_t {
+  int64_t events_done;
+  int64_t interactions;
+  int64_t steps_launched;   /* step-kernel launches (one per step per chunk) */
+  int64_t kernel_launches;  /* all kernel launches issued by the library */
+  int64_t chunks;
+  int64_t queue_depth;
+  int64_t rejected;
+  int32_t sm_count;
+  int32_t variant;          /* pair-kernel variant in use */
+  double device_ms;         /* device time of executed chunks (CUDA events) */
+} sim_stats_t;
+
+typedef struct sim_t sim_t;
+
+/* Create a handle: validates parameters (SIM_EINVAL), checks for an sm_103
+ * device (SIM_ENODEV) and allocates the device arena (SIM_ECUDA on failure). */
+int sim_init(const sim_sensor_t* sensor, const sim_field_t* field,
+             const sim_mobility_t* mobility, const sim_options_t* options,
+             sim_t** out);
+
+/* Queue n_ev events (copied).  *n_accepted counts the accepted prefix; the
+ * first event not accepted sets the return code: SIM_EINVAL (bad event),
+ * SIM_ENOMEM_BUDGET (larger than the arena), SIM_EAGAIN (queue full). */
+int sim_submit(sim_t* sim, const sim_event_t* ev, int n_ev, int* n_accepted);
+
+/* Fill up to max_out completed results (arrays supplied by the caller).
+ * Waits up to timeout_ms for the first one (0 = do not wait, < 0 = until
+ * one completes).  In PLAIN and BATCHED modes the calling thread drives the
+ * GPU; in SERVE mode the engine thread does.  SIM_ETIMEOUT if none. */
+int sim_poll(sim_t* sim, sim_result_t* out, int max_out, int* n_out,
+             int timeout_ms);
+
+/* Convenience: submit n events, drive them to completion, return results in
+ * submission order (out[k] receives event k). */
+int sim_run(sim_t* sim, const sim_event_t* ev, int n, sim_result_t* out);
+
+/* Device-resident batch (BATCHED mode): sim_stage admits the events and
+ * uploads their descriptors; sim_execute runs all staged events to completion
+ * with results kept in device memory (only per-chunk control words cross to
+ * the host); sim_collect copies the results out, in staging order. */
+int sim_stage(sim_t* sim, const sim_event_t* ev, int n);
+int sim_execute(sim_t* sim);
+int sim_collect(sim_t* sim, sim_result_t* out, int max_out, int* n_out);
+
+int sim_get_stats(sim_t* sim, sim_stats_t* out);
+int sim_destroy(sim_t* sim);
+const char* sim_strerror(int code);
+
+/* ---- kernel-level entry points (used by the parity tests) ---------------- */
+
+/* Eq. 4 field of n_h holes followed by n_e electrons at FP32 positions
+ * x, y, z (um), through the same pair kernel and tile schedule as the step
+ * loop.  out_E receives 3*(n_h+n_e) doubles (Ex, Ey, Ez per carrier, V/um)
+ * holding the FP32 results. */
+int sim_debug_field(sim_t* sim, const float* x, const float* y, const float* z,
+                    int32_t n_h, int32_t n_e, double* out_E);
+
+/* Readout binning kernel on n collected positions; pixels gets grid_n^2
+ * counts (overwritten), *outside the number outside the grid. */
+int sim_debug_bin(sim_t* sim, const double* x, const double* y, int64_t n,
+                  int32_t* pixels, int64_t* outside);
+
+/* Philox4x32-10 on the device: ctr[4n], key[2n] -> out[4n]; and the same
+ * blocks from the CUDA toolkit's curand Philox for ctr words (c0, c1, 0, 0)
+ * when curand_out is not NULL (both on device 0 of the handle-less call). */
+int sim_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n,
+                     uint32_t* out, uint32_t* curand_out);
+
+/* The device's diffusion normals for (seed, event, purpose, carrier, step)
+ * tuples: in[5n] as u64 (seed, event, purpose, carrier, step) -> out[3n]. */
+int sim_debug_normals(const uint64_t* in, int64_t n, double* out);
+
+/* Run one event for at most n_steps steps (or until every hole is
+ * collected) and return FP64 positions (3 per carrier id) and states
+ * (0 active, 1 collected, 2 exited) when it stopped; *steps_done receives the
+ * steps executed.  Uses the BATCHED path with a single slot. */
+int sim_debug_trajectory(sim_t* sim, const sim_event_t* ev, int64_t n_steps,
+                         double* pos_out, int8_t* state_out, int64_t capacity,
+                         int64_t* steps_done);
+
+/* Host-side fault injection for the failure-path tests: the next chunk (or
+ * poll) reports the given code as if the device or queue had raised it
+ * (SIM_ENUMERIC, SIM_ETIMEOUT, SIM_ECUDA); 0 clears. */
+int sim_debug_inject(sim_t* sim, int fault);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTS_H_ */

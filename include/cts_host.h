@@ -1,0 +1,55 @@
+/*
+ * cts_host.h -- host-side planning entry points of the charge-transport
+ * library (no GPU needed).  They expose the scheduler's pure host logic so it
+ * can be checked on machines without a device; the GPU path calls the same
+ * code.  Paper reference: the pair sum of Eq. 4 (Sec. 2.1) must cover every
+ * ordered pair (i, j) of carriers of one event exactly once per step; these
+ * functions decide how that O(N^2) work is cut into units for the GPU.
+ */
+#ifndef CTS_HOST_H_
+#define CTS_HOST_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One unit of pair work: i's [i0, i0 + ni) of species spec (0 holes, 1
+ * electrons) of slot `slot`, against sources [j0, j1) of the slot's
+ * concatenated [holes | electrons] list.  Units of one i-block share iblock
+ * and are split into nsplit j ranges (split = 0 .. nsplit - 1); pbase is the
+ * float offset of the i-block's partial sums (nsplit > 1 only). */
+typedef struct cts_unit_t {
+  int32_t slot, spec, i0, ni, j0, j1, split, nsplit, iblock, pbase;
+} cts_unit_t;
+
+/* Plan the units of one step for n_slots resident events with n_h[s] holes
+ * and n_e[s] electrons (negative or zero counts: slot idle).  tile_i = i's per
+ * unit (threads x i's per thread of the pair kernel), grid = persistent CTAs,
+ * allow_split = 0 forbids j splits (then every unit covers all sources).
+ * Units are written to out (capacity max_units) in decreasing cost order;
+ * *n_out their count, *partial_floats the partial-sum floats they need.
+ * Returns 0, SIM_EINVAL (-1) for bad sizes, or -2 if max_units or
+ * partial_cap is too small even without splits. */
+int cts_plan_units(const int32_t* n_h, const int32_t* n_e, int32_t n_slots, int32_t tile_i,
+                   int32_t grid, int32_t allow_split, int32_t max_units, int64_t partial_cap,
+                   cts_unit_t* out, int32_t* n_out, int64_t* partial_floats);
+
+/* First-fit carrier arena of the scheduler, for tests: replays n_ops
+ * operations (size > 0: allocate size entries and write the offset, or -1 if
+ * it does not fit, to result[k]; size < 0: free the block allocated by
+ * operation -size-1) on an arena of `capacity` entries. Returns 0 or -1. */
+int cts_arena_replay(int64_t capacity, const int64_t* ops, int32_t n_ops, int64_t* result);
+
+/* Estimated transit steps of a hole from depth_um below the entrance surface
+ * to the readout, by the drift-only integral dt = dz / (mu(E) E) over the
+ * Eq. 6 field (the integral of Eq. 9); used to order work longest first. */
+double cts_estimate_steps(double thickness_um, double bias_V, double depletion_V,
+                          double mu0_cm2, double vsat_cms, double beta, double dt_ps,
+                          double depth_um);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTS_HOST_H_ */

@@ -1,0 +1,467 @@
+"""Python binding of the GB300 charge-transport library (include/cts.h).
+
+Brute-force drift-diffusion-repulsion Monte Carlo of Xie et al., arXiv
+2506.09712 (Sec. 2.1, Algorithm 1), run by hand-written sm_103a kernels in
+``_build/libcts.so``.  This module only marshals arguments through ctypes: the
+functions keep the C names (``sim_init``, ``sim_submit``, ``sim_poll`` ...),
+and ``Simulator`` wraps a handle for convenience.  There is no fallback: if
+the library is missing or no sm_103 device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcts.so")
+
+SIM_OK, SIM_EINVAL, SIM_ENOMEM_BUDGET, SIM_EAGAIN, SIM_ETIMEOUT = 0, -1, -2, -3, -4
+SIM_ECUDA, SIM_EMAXSTEPS, SIM_ENUMERIC, SIM_ESTATE, SIM_ENODEV = -5, -6, -7, -8, -9
+CTS_HOLES, CTS_BOTH = 1, 3
+CTS_MOB_CT, CTS_MOB_CONST = 0, 1
+CTS_PHOTON, CTS_TRACK, CTS_EXPLICIT = 0, 1, 2
+CTS_MODE_PLAIN, CTS_MODE_BATCHED, CTS_MODE_SERVE = 0, 1, 2
+
+
+class sim_sensor_t(C.Structure):
+    _fields_ = [("thickness_um", C.c_double), ("bias_V", C.c_double),
+                ("depletion_V", C.c_double), ("temperature_K", C.c_double),
+                ("eps_r", C.c_double), ("pitch_um", C.c_double), ("dt_ps", C.c_double),
+                ("softening_um", C.c_double), ("max_steps", C.c_int64),
+                ("grid_n", C.c_int32), ("species", C.c_int32)]
+
+
+class sim_field_t(C.Structure):
+    _fields_ = [("repulsion", C.c_int32), ("drift", C.c_int32), ("diffusion", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class sim_mobility_t(C.Structure):
+    _fields_ = [("model", C.c_int32), ("reserved", C.c_int32),
+                ("mu0_h", C.c_double), ("vsat_h", C.c_double), ("beta_h", C.c_double),
+                ("mu0_e", C.c_double), ("vsat_e", C.c_double), ("beta_e", C.c_double)]
+
+
+class sim_options_t(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("device", C.c_int32), ("max_slots", C.c_int32),
+                ("chunk_steps", C.c_int32), ("max_carriers", C.c_int64),
+                ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32),
+                ("variant", C.c_int32), ("disable_graphs", C.c_int32),
+                ("keep_final_xy", C.c_int32), ("stream", C.c_void_p)]
+
+
+class sim_event_t(C.Structure):
+    _fields_ = [("event_id", C.c_uint64), ("seed", C.c_uint64), ("kind", C.c_int32),
+                ("n_pairs", C.c_int32), ("energy_keV", C.c_double), ("depth_um", C.c_double),
+                ("x_um", C.c_double), ("y_um", C.c_double), ("sigma_um", C.c_double),
+                ("track_len_um", C.c_double), ("theta_deg", C.c_double),
+                ("phi_deg", C.c_double), ("explicit_xyz", C.POINTER(C.c_double)),
+                ("explicit_sign", C.POINTER(C.c_int8))]
+
+
+class sim_result_t(C.Structure):
+    _fields_ = [("event_id", C.c_uint64), ("status", C.c_int32), ("n_carriers", C.c_int32),
+                ("n_steps", C.c_int64), ("n_collected", C.c_int64), ("n_outside", C.c_int64),
+                ("n_lost", C.c_int64), ("interactions", C.c_int64),
+                ("t_submit_ns", C.c_double), ("t_start_ns", C.c_double),
+                ("t_done_ns", C.c_double), ("pixels", C.POINTER(C.c_int32)),
+                ("final_xy", C.POINTER(C.c_double)), ("retire_step", C.POINTER(C.c_int32)),
+                ("capacity", C.c_int64)]
+
+
+class sim_stats_t(C.Structure):
+    _fields_ = [("events_done", C.c_int64), ("interactions", C.c_int64),
+                ("steps_launched", C.c_int64), ("kernel_launches", C.c_int64),
+                ("chunks", C.c_int64), ("queue_depth", C.c_int64), ("rejected", C.c_int64),
+                ("sm_count", C.c_int32), ("variant", C.c_int32), ("device_ms", C.c_double)]
+
+
+class cts_unit_t(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in
+                ("slot", "spec", "i0", "ni", "j0", "j1", "split", "nsplit", "iblock", "pbase")]
+
+
+# Every symbol that include/cts.h and include/cts_host.h declare.
+EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_execute",
+            "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
+            "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
+            "sim_debug_inject", "cts_plan_units", "cts_arena_replay", "cts_estimate_steps"]
+
+_lib = None
+
+
+class SimError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else strerror(code))
+
+
+def load(build_if_missing: bool = True):
+    """Load libcts.so (building it in-tree first if needed).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH) and build_if_missing:
+        from . import build as _b
+        _b.build()
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH}")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    i32, i64, u32, u64, d = C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+    sig = {
+        "sim_init": [P(sim_sensor_t), P(sim_field_t), P(sim_mobility_t), P(sim_options_t),
+                     P(C.c_void_p)],
+        "sim_submit": [C.c_void_p, P(sim_event_t), C.c_int, P(C.c_int)],
+        "sim_poll": [C.c_void_p, P(sim_result_t), C.c_int, P(C.c_int), C.c_int],
+        "sim_run": [C.c_void_p, P(sim_event_t), C.c_int, P(sim_result_t)],
+        "sim_stage": [C.c_void_p, P(sim_event_t), C.c_int],
+        "sim_execute": [C.c_void_p],
+        "sim_collect": [C.c_void_p, P(sim_result_t), C.c_int, P(C.c_int)],
+        "sim_get_stats": [C.c_void_p, P(sim_stats_t)],
+        "sim_destroy": [C.c_void_p],
+        "sim_strerror": [C.c_int],
+        "sim_debug_field": [C.c_void_p, P(C.c_float), P(C.c_float), P(C.c_float), i32, i32,
+                            P(d)],
+        "sim_debug_bin": [C.c_void_p, P(d), P(d), i64, P(i32), P(i64)],
+        "sim_debug_philox": [P(u32), P(u32), i64, P(u32), P(u32)],
+        "sim_debug_normals": [P(u64), i64, P(d)],
+        "sim_debug_trajectory": [C.c_void_p, P(sim_event_t), i64, P(d), P(C.c_int8), i64,
+                                 P(i64)],
+        "sim_debug_inject": [C.c_void_p, C.c_int],
+        "cts_plan_units": [P(i32), P(i32), i32, i32, i32, i32, i32, i64, P(cts_unit_t), P(i32),
+                           P(i64)],
+        "cts_arena_replay": [i64, P(i64), i32, P(i64)],
+        "cts_estimate_steps": [d, d, d, d, d, d, d, d],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.sim_strerror.restype = C.c_char_p
+    lib.cts_estimate_steps.restype = C.c_double
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().sim_strerror(int(code)).decode()
+
+
+def _check(rc, what):
+    if rc != SIM_OK:
+        raise SimError(rc, what)
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype)) if a is not None else None
+
+
+# ----------------------------------------------------------------------------
+# Same-name thin wrappers (argument marshalling only)
+# ----------------------------------------------------------------------------
+def sim_init(sensor: sim_sensor_t, field: sim_field_t, mobility: sim_mobility_t,
+             options: sim_options_t | None = None):
+    h = C.c_void_p()
+    rc = load().sim_init(C.byref(sensor), C.byref(field), C.byref(mobility),
+                         C.byref(options) if options is not None else None, C.byref(h))
+    return rc, h
+
+
+def sim_submit(h, events, n=None):
+    n = len(events) if n is None else n
+    acc = C.c_int(0)
+    rc = load().sim_submit(h, events, n, C.byref(acc))
+    return rc, acc.value
+
+
+def sim_poll(h, results, max_out, timeout_ms):
+    n = C.c_int(0)
+    rc = load().sim_poll(h, results, max_out, C.byref(n), timeout_ms)
+    return rc, n.value
+
+
+def sim_run(h, events, n, results):
+    return load().sim_run(h, events, n, results)
+
+
+def sim_stage(h, events, n):
+    return load().sim_stage(h, events, n)
+
+
+def sim_execute(h):
+    return load().sim_execute(h)
+
+
+def sim_collect(h, results, max_out):
+    n = C.c_int(0)
+    rc = load().sim_collect(h, results, max_out, C.byref(n))
+    return rc, n.value
+
+
+def sim_get_stats(h):
+    st = sim_stats_t()
+    _check(load().sim_get_stats(h, C.byref(st)), "sim_get_stats")
+    return st
+
+
+def sim_destroy(h):
+    return load().sim_destroy(h)
+
+
+def sim_strerror(code):
+    return strerror(code)
+
+
+def sim_debug_field(h, xyz, n_h, n_e=0):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    x = np.ascontiguousarray(xyz[:, 0]); y = np.ascontiguousarray(xyz[:, 1])
+    z = np.ascontiguousarray(xyz[:, 2])
+    out = np.zeros((xyz.shape[0], 3), dtype=np.float64)
+    rc = load().sim_debug_field(h, _ptr(x, C.c_float), _ptr(y, C.c_float), _ptr(z, C.c_float),
+                                int(n_h), int(n_e), _ptr(out, C.c_double))
+    _check(rc, "sim_debug_field")
+    return out
+
+
+def sim_debug_bin(h, x, y, grid_n):
+    x = np.ascontiguousarray(x, dtype=np.float64); y = np.ascontiguousarray(y, dtype=np.float64)
+    pix = np.zeros(grid_n * grid_n, dtype=np.int32)
+    out = C.c_int64(0)
+    _check(load().sim_debug_bin(h, _ptr(x, C.c_double), _ptr(y, C.c_double), x.size,
+                                _ptr(pix, C.c_int32), C.byref(out)), "sim_debug_bin")
+    return pix.reshape(grid_n, grid_n), out.value
+
+
+def sim_debug_philox(ctr, key, with_curand=False):
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    n = ctr.shape[0]
+    out = np.zeros((n, 4), dtype=np.uint32)
+    cur = np.zeros((n, 4), dtype=np.uint32) if with_curand else None
+    _check(load().sim_debug_philox(_ptr(ctr, C.c_uint32), _ptr(key, C.c_uint32), n,
+                                   _ptr(out, C.c_uint32), _ptr(cur, C.c_uint32)),
+           "sim_debug_philox")
+    return (out, cur) if with_curand else out
+
+
+def sim_debug_normals(tuples):
+    t = np.ascontiguousarray(tuples, dtype=np.uint64).reshape(-1, 5)
+    out = np.zeros((t.shape[0], 3), dtype=np.float64)
+    _check(load().sim_debug_normals(_ptr(t, C.c_uint64), t.shape[0], _ptr(out, C.c_double)),
+           "sim_debug_normals")
+    return out
+
+
+def sim_debug_trajectory(h, event: sim_event_t, n_steps, n_carriers):
+    pos = np.zeros((max(n_carriers, 1), 3), dtype=np.float64)
+    st = np.zeros(max(n_carriers, 1), dtype=np.int8)
+    done = C.c_int64(0)
+    rc = load().sim_debug_trajectory(h, C.byref(event), int(n_steps), _ptr(pos, C.c_double),
+                                     _ptr(st, C.c_int8), pos.shape[0], C.byref(done))
+    _check(rc, "sim_debug_trajectory")
+    return pos[:n_carriers], st[:n_carriers], done.value
+
+
+def sim_debug_inject(h, fault):
+    return load().sim_debug_inject(h, int(fault))
+
+
+def cts_plan_units(n_h, n_e, tile_i, grid, allow_split=1, max_units=65536,
+                   partial_cap=1 << 26):
+    n_h = np.ascontiguousarray(n_h, dtype=np.int32); n_e = np.ascontiguousarray(n_e, dtype=np.int32)
+    out = (cts_unit_t * max_units)()
+    n = C.c_int32(0)
+    pf = C.c_int64(0)
+    rc = load().cts_plan_units(_ptr(n_h, C.c_int32), _ptr(n_e, C.c_int32), n_h.size, tile_i,
+                               grid, allow_split, max_units, partial_cap, out, C.byref(n),
+                               C.byref(pf))
+    if rc != 0:
+        return rc, None, 0
+    arr = np.array([[getattr(out[k], f) for f, _ in cts_unit_t._fields_] for k in range(n.value)],
+                   dtype=np.int64).reshape(-1, 10)
+    return rc, arr, pf.value
+
+
+def cts_arena_replay(capacity, ops):
+    ops = np.ascontiguousarray(ops, dtype=np.int64)
+    res = np.zeros(ops.size, dtype=np.int64)
+    rc = load().cts_arena_replay(int(capacity), _ptr(ops, C.c_int64), ops.size, _ptr(res, C.c_int64))
+    return rc, res
+
+
+def cts_estimate_steps(thickness_um, bias_V, depletion_V, mu0, vsat, beta, dt_ps, depth_um):
+    return load().cts_estimate_steps(thickness_um, bias_V, depletion_V, mu0, vsat, beta, dt_ps,
+                                     depth_um)
+
+
+# ----------------------------------------------------------------------------
+# Convenience layer: presets (dicts) -> structs, and a handle object
+# ----------------------------------------------------------------------------
+def make_sensor(d: dict) -> sim_sensor_t:
+    s = sim_sensor_t()
+    s.thickness_um = d["thickness_um"]; s.bias_V = d["bias_V"]; s.depletion_V = d["depletion_V"]
+    s.temperature_K = d.get("temperature_K", 293.0); s.eps_r = d.get("eps_r", 11.7)
+    s.pitch_um = d.get("pitch_um", 25.0); s.dt_ps = d["dt_ps"]
+    s.softening_um = d.get("softening_um", 1e-6); s.max_steps = d.get("max_steps", 200_000)
+    s.grid_n = d.get("grid_n", 9); s.species = d.get("species", CTS_HOLES)
+    return s
+
+
+def make_field(d: dict | None = None) -> sim_field_t:
+    d = d or {}
+    return sim_field_t(d.get("repulsion", 1), d.get("drift", 1), d.get("diffusion", 1), 0)
+
+
+def make_mobility(d: dict) -> sim_mobility_t:
+    m = sim_mobility_t()
+    m.model = d.get("model", CTS_MOB_CT)
+    m.mu0_h, m.vsat_h, m.beta_h = d["mu0_h"], d["vsat_h"], d["beta_h"]
+    m.mu0_e, m.vsat_e, m.beta_e = d.get("mu0_e", 0.0), d.get("vsat_e", 0.0), d.get("beta_e", 0.0)
+    return m
+
+
+def make_options(mode=CTS_MODE_BATCHED, **kw) -> sim_options_t:
+    o = sim_options_t()
+    o.mode = mode
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_events(events: list[dict]):
+    """Array of sim_event_t from dicts (explicit positions are kept alive on it)."""
+    arr = (sim_event_t * max(len(events), 1))()
+    keep = []
+    for k, ev in enumerate(events):
+        e = arr[k]
+        e.event_id = ev.get("event_id", k); e.seed = ev.get("seed", 0)
+        e.kind = ev.get("kind", CTS_PHOTON); e.n_pairs = ev.get("n_pairs", 0)
+        e.energy_keV = ev.get("energy_keV", 0.0); e.depth_um = ev.get("depth_um", 0.0)
+        e.x_um = ev.get("x_um", 0.0); e.y_um = ev.get("y_um", 0.0)
+        e.sigma_um = ev.get("sigma_um", -1.0); e.track_len_um = ev.get("track_len_um", 0.0)
+        e.theta_deg = ev.get("theta_deg", 0.0); e.phi_deg = ev.get("phi_deg", 0.0)
+        if e.kind == CTS_EXPLICIT:
+            xyz = np.ascontiguousarray(ev["explicit_xyz"], dtype=np.float64).reshape(-1)
+            keep.append(xyz)
+            e.explicit_xyz = _ptr(xyz, C.c_double)
+            e.n_pairs = xyz.size // 3
+            if ev.get("explicit_sign") is not None:
+                sg = np.ascontiguousarray(ev["explicit_sign"], dtype=np.int8)
+                keep.append(sg)
+                e.explicit_sign = _ptr(sg, C.c_int8)
+    arr._keep = keep
+    return arr
+
+
+class Results:
+    """Caller-owned result buffers for n events."""
+
+    def __init__(self, n: int, grid_n: int, capacity: int = 0):
+        self.n, self.grid_n, self.capacity = n, grid_n, capacity
+        self.pixels = np.zeros((max(n, 1), grid_n, grid_n), dtype=np.int32)
+        self.final_xy = np.zeros((max(n, 1), max(capacity, 1), 2), dtype=np.float64)
+        self.retire_step = np.zeros((max(n, 1), max(capacity, 1)), dtype=np.int32)
+        self.arr = (sim_result_t * max(n, 1))()
+        for k in range(max(n, 1)):
+            r = self.arr[k]
+            r.pixels = _ptr(self.pixels[k], C.c_int32)
+            if capacity:
+                r.final_xy = _ptr(self.final_xy[k], C.c_double)
+                r.retire_step = _ptr(self.retire_step[k], C.c_int32)
+                r.capacity = capacity
+
+    def record(self, k: int) -> dict:
+        r = self.arr[k]
+        return dict(event_id=r.event_id, status=r.status, n_carriers=r.n_carriers,
+                    n_steps=r.n_steps, n_collected=r.n_collected, n_outside=r.n_outside,
+                    n_lost=r.n_lost, interactions=r.interactions, t_submit_ns=r.t_submit_ns,
+                    t_start_ns=r.t_start_ns, t_done_ns=r.t_done_ns,
+                    pixels=self.pixels[k].copy(),
+                    final_xy=self.final_xy[k, :r.n_carriers].copy() if self.capacity else None,
+                    retire_step=self.retire_step[k, :r.n_carriers].copy() if self.capacity else None)
+
+
+class Simulator:
+    """A library handle built from preset dictionaries (see ``workloads``)."""
+
+    def __init__(self, sensor: dict, mobility: dict, field: dict | None = None,
+                 mode=CTS_MODE_BATCHED, **options):
+        self.sensor_d = dict(sensor)
+        self.grid_n = int(sensor.get("grid_n", 9))
+        self._sensor = make_sensor(sensor)
+        self._field = make_field(field)
+        self._mob = make_mobility(mobility)
+        self._opt = make_options(mode, **options)
+        rc, self.h = sim_init(self._sensor, self._field, self._mob, self._opt)
+        _check(rc, "sim_init")
+
+    def close(self):
+        if self.h:
+            sim_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, events: list[dict], keep_xy_capacity: int = 0) -> list[dict]:
+        evs = make_events(events)
+        res = Results(len(events), self.grid_n, keep_xy_capacity)
+        _check(sim_run(self.h, evs, len(events), res.arr), "sim_run")
+        return [res.record(k) for k in range(len(events))]
+
+    def stage(self, events: list[dict]):
+        self._staged = make_events(events)
+        _check(sim_stage(self.h, self._staged, len(events)), "sim_stage")
+
+    def execute(self):
+        _check(sim_execute(self.h), "sim_execute")
+
+    def collect(self, n: int, keep_xy_capacity: int = 0) -> list[dict]:
+        res = Results(n, self.grid_n, keep_xy_capacity)
+        rc, got = sim_collect(self.h, res.arr, n)
+        _check(rc, "sim_collect")
+        return [res.record(k) for k in range(got)]
+
+    def submit(self, events: list[dict]) -> tuple[int, int]:
+        evs = make_events(events)
+        return sim_submit(self.h, evs, len(events))
+
+    def poll(self, max_out: int, timeout_ms: int, keep_xy_capacity: int = 0) -> list[dict]:
+        res = Results(max_out, self.grid_n, keep_xy_capacity)
+        rc, n = sim_poll(self.h, res.arr, max_out, timeout_ms)
+        if rc == SIM_ETIMEOUT:
+            return []
+        _check(rc, "sim_poll")
+        return [res.record(k) for k in range(n)]
+
+    def stats(self) -> dict:
+        st = sim_get_stats(self.h)
+        return {f: getattr(st, f) for f, _ in sim_stats_t._fields_}
+
+    def field(self, xyz, n_h, n_e=0):
+        return sim_debug_field(self.h, xyz, n_h, n_e)
+
+    def bin(self, x, y):
+        return sim_debug_bin(self.h, x, y, self.grid_n)
+
+    def trajectory(self, event: dict, n_steps: int):
+        evs = make_events([event])
+        n = event.get("n_carriers")
+        if n is None:
+            raise ValueError("trajectory needs event['n_carriers']")
+        return sim_debug_trajectory(self.h, evs[0], n_steps, n)
+
+    def inject(self, fault: int):
+        return sim_debug_inject(self.h, fault)

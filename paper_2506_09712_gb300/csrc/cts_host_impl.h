@@ -1,0 +1,40 @@
+// cts_host_impl.h -- C++ interface of the pure host logic (cts_host.cpp).
+#pragma once
+#include <cstdint>
+#include <map>
+#include <vector>
+
+namespace cts {
+
+constexpr int kPlanMinJ = 1024;     // smallest j range of a split (one smem stage)
+constexpr int kPlanMaxSplit = 16;   // most j splits of one i tile
+constexpr int64_t kArenaAlign = 32; // arena entries are handed out in multiples of this
+
+struct UnitPlan {
+  int32_t slot, spec, i0, ni, j0, j1, split, nsplit, iblock, pbase;
+};
+
+int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, int grid,
+               bool allow_split, int max_units, int64_t partial_cap, std::vector<UnitPlan>* out,
+               int64_t* partial_floats);
+
+class ArenaAllocator {
+ public:
+  explicit ArenaAllocator(int64_t capacity = 0);
+  int64_t alloc(int64_t n);  // offset, or -1 if no block fits
+  void release(int64_t off);
+  int64_t capacity() const { return capacity_; }
+  int64_t in_use() const { return in_use_; }
+  int64_t largest_free() const;
+
+ private:
+  int64_t capacity_;
+  int64_t in_use_ = 0;
+  std::map<int64_t, int64_t> free_;  // offset -> length
+  std::map<int64_t, int64_t> used_;  // offset -> length
+};
+
+double estimate_steps(double H, double Vb, double Vd, double mu0_cm2, double vsat_cms,
+                      double beta, double dt_ps, double depth);
+
+}  // namespace cts

@@ -1,0 +1,166 @@
+// cts_internal.h -- data layout shared by the kernels (cts_kernels.cu) and the
+// host runtime (cts_runtime.cu).  Not part of the public ABI (include/cts.h).
+//
+// Device memory layout (one arena of carriers shared by all resident events):
+//   px, py, pz   FP64 absolute positions (um), by arena index
+//   sh[2]        FP32 float4 shadow (x - ax, y - ay, z - az[species], 0),
+//                double-buffered by step parity; the pair kernel reads only it
+//   cid          carrier id inside its event (Philox counter, result index)
+//   fx, fy       FP64 collection position, by (slot base + carrier id)
+//   rstep        retire step by (slot base + carrier id)
+//   cstate       state by (slot base + carrier id): bits 0-1 = 0 active,
+//                1 collected, 2 exited; bit 2 = electron
+// Each event (slot) owns [base, base + cap_h + cap_e): holes first (compacted
+// to n_h entries at every chunk boundary), electrons from base + cap_h.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cts {
+
+constexpr int kStateActive = 0;
+constexpr int kStateCollected = 1;
+constexpr int kStateExited = 2;
+constexpr int kStateMask = 3;
+constexpr int kElectronBit = 4;
+
+constexpr int kErrNumeric = 1;    // non-finite displacement
+constexpr int kErrTimeout = 2;    // bounded wait on a copy gave up
+constexpr int kErrBounds = 4;     // index outside its slot (checked build)
+
+constexpr float kParked = 1.0e18f;  // shadow coordinate of retired carriers
+constexpr int kChunkJ = 1024;       // j entries per shared-memory stage
+constexpr int kMaxK = 256;          // largest chunk (steps per host check)
+
+// Derived physical constants (all in um, ns, V).
+struct Phys {
+  double H;          // thickness
+  double ea, eb;     // drift field magnitude E(z) = ea - eb z
+  double kc;         // e / (4 pi eps0 eps_r), V um
+  double kT;         // kT / e, V
+  double dt;         // ns
+  double mu0[2], vsat[2], beta[2];  // [0] holes, [1] electrons; um^2/(V ns), um/ns
+  double pitch;
+  float f_ea, f_eb, f_kc, f_kT, f_dt, f_eps2, f_H;
+  float f_mu0[2], f_vsat[2], f_beta[2], f_ibeta[2];
+  int32_t mob_model, repulsion, drift, diffusion;
+  int32_t species, grid_n;
+  int64_t max_steps;
+};
+
+// Per-slot state, resident in device memory.
+struct SlotDev {
+  uint64_t seed, event_id;
+  int64_t base;             // arena offset
+  int32_t cap_h, cap_e;     // allocated entries per species
+  int32_t n_h, n_e;         // range lengths (compacted at chunk boundaries)
+  int32_t act_h, act_e;     // active carriers at the chunk start
+  int32_t n_total;          // carrier ids 0 .. n_total-1
+  int32_t step0;            // event-local step at the chunk start
+  int32_t running;          // 1 while stepping
+  int32_t flags;            // kErr* bits
+  int32_t n_steps;          // steps executed so far
+  int32_t status;           // final status (set at the close)
+  double ax, ay;            // lateral anchor (um)
+  double az[2][2];          // [step parity][species] z anchor (um)
+  unsigned long long interactions;
+  // initial condition
+  int32_t kind, n_pairs;
+  double energy_keV, depth_um, x0, y0, sigma_um, track_len_um, theta_deg, phi_deg;
+  int64_t explicit_off;     // offset (records) into the explicit staging buffer
+};
+
+// One explicit carrier, already in arena order (holes then electrons).
+struct ExplicitRec {
+  double x, y, z;
+  int32_t cid;
+  int32_t sign;
+};
+
+// A unit of pair work: TI i's of one species of one slot against the j range
+// [j0, j1) of the concatenated [holes | electrons] list.
+struct Unit {
+  int32_t slot;
+  int32_t spec;      // species of the i's: 0 holes, 1 electrons
+  int32_t i0, ni;
+  int32_t j0, j1;
+  int32_t split, nsplit;
+  int32_t iblock;    // combine counter (nsplit > 1)
+  int32_t pbase;     // float offset of the i-block's partial sums
+};
+
+// Summary of one slot after a chunk (copied to the host).
+struct SlotSummary {
+  int32_t running;
+  int32_t done;
+  int32_t status;
+  int32_t n_steps;
+  int32_t n_h, n_e;        // range lengths after compaction
+  int32_t act_h, act_e;
+  int32_t flags;
+  int32_t pad;
+  unsigned long long interactions;
+};
+
+// Per-slot readout results (device), filled by the binning kernel.
+struct SlotReadout {
+  long long n_collected;
+  long long n_outside;
+  long long n_lost;
+  long long pad;
+};
+
+struct Arena {
+  double *px, *py, *pz;
+  float4* sh[2];
+  int32_t* cid;
+  double *fx, *fy;
+  int32_t* rstep;
+  int8_t* cstate;
+  int64_t capacity;
+};
+
+struct StepArgs {
+  Arena A;
+  SlotDev* slots;
+  const Unit* units;
+  const int32_t* n_units;
+  int32_t* unit_counter;     // [K]
+  int32_t* ret;              // [K][S][2]
+  float* partial;            // j-split partial sums
+  int32_t* combine_count;    // per i-block
+  float* field_out;          // FIELD_ONLY output, SoA [3][capacity]
+  int32_t* err;              // global error bits
+  Phys ph;
+  int32_t S;                 // slot count
+  int32_t fused;             // 1: update positions; 0: write field_out
+};
+
+// ---- kernel launchers (cts_kernels.cu) ----------------------------------
+struct Variant {
+  int nt;       // threads per CTA
+  int r;        // i's per thread
+  const char* name;
+};
+int variant_count();
+Variant variant_info(int v);
+cudaError_t variant_occupancy(int v, int* blocks_per_sm);
+size_t variant_smem(int v);
+
+cudaError_t launch_step(int v, const StepArgs& a, int k, int grid, cudaStream_t s);
+cudaError_t launch_update(const StepArgs& a, int k, int n_slots_list, const int32_t* slot_list,
+                          int grid, cudaStream_t s);
+cudaError_t launch_init(const Phys& ph, Arena A, SlotDev* slots, const int32_t* slot_list,
+                        int n, const ExplicitRec* explicit_buf, cudaStream_t s);
+cudaError_t launch_close(const Phys& ph, Arena A, SlotDev* slots, const int32_t* slot_list,
+                         int n, const int32_t* ret, int S, int K, SlotSummary* summary,
+                         cudaStream_t s);
+cudaError_t launch_bin(const Phys& ph, Arena A, const SlotDev* slots, const int32_t* slot_list,
+                       int n, int32_t* pixels, SlotReadout* readout, cudaStream_t s);
+cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, int64_t n,
+                              int32_t* pixels, long long* outside, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                          uint32_t* curand_out, cudaStream_t s);
+cudaError_t launch_normals(const unsigned long long* in, int64_t n, double* out, cudaStream_t s);
+
+}  // namespace cts

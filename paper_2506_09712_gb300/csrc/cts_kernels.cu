@@ -1,0 +1,941 @@
+// cts_kernels.cu -- sm_103a kernels of the brute-force charge-transport step
+// (Xie et al., arXiv 2506.09712, Sec. 2.1 and Algorithm 1).
+//
+//   step_kernel   one time step for every resident event: the Eq. 4 pair
+//                 field of a tile of carriers (FP32, rsqrt, Kahan-compensated
+//                 across j chunks staged in shared memory by TMA bulk copies),
+//                 then drift (Eq. 6), mobility, diffusion and the FP64
+//                 position update of Eqs. 3 and 5, collection and exit.
+//                 Persistent CTAs pull (event, i-tile, j-split) units from a
+//                 per-step counter; j-splits are combined in FP64 by the CTA
+//                 that finishes last.
+//   update_kernel the update alone (two-launch PLAIN path).
+//   init_kernel   the initial cloud of each new event (Algorithm 1, Eq. 2).
+//   close_kernel  end-of-chunk bookkeeping and order-preserving compaction.
+//   bin_kernel    warp-aggregated pixel readout of collected holes.
+#include <cuda_runtime.h>
+#include <curand_kernel.h>
+
+#include <cstdint>
+
+#include "cts_internal.h"
+
+namespace cts {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers: Philox4x32-10 (Salmon et al., SC'11).
+// Counter = (carrier, step, event lo, event hi ^ purpose << 28), key = seed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ uint4 stream_words(uint64_t seed, uint64_t ev, uint32_t purpose,
+                                              uint32_t carrier, uint32_t step) {
+  const uint4 c = make_uint4(carrier, step, (uint32_t)ev, (uint32_t)(ev >> 32) ^ (purpose << 28));
+  return philox10(c, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// ((w >> 9) + 1/2) * 2^-23: exact in FP32 and FP64.
+__device__ __forceinline__ float uniform_f(uint32_t w) {
+  return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+__device__ __forceinline__ double uniform_d(uint32_t w) {
+  return ((double)(w >> 9) + 0.5) * 1.1920928955078125e-07;
+}
+
+// Box-Muller: (n0, n1) from (u0, u1), n2 from the cosine branch of (u2, u3).
+__device__ __forceinline__ float3 normals_f(uint4 w) {
+  const float r01 = sqrtf(-2.0f * logf(uniform_f(w.x)));
+  const float r23 = sqrtf(-2.0f * logf(uniform_f(w.z)));
+  float s1, c1;
+  sincospif(2.0f * uniform_f(w.y), &s1, &c1);
+  const float c3 = cospif(2.0f * uniform_f(w.w));
+  return make_float3(r01 * c1, r01 * s1, r23 * c3);
+}
+__device__ __forceinline__ double3 normals_d(uint4 w) {
+  const double r01 = sqrt(-2.0 * log(uniform_d(w.x)));
+  const double r23 = sqrt(-2.0 * log(uniform_d(w.z)));
+  double s1, c1;
+  sincospi(2.0 * uniform_d(w.y), &s1, &c1);
+  const double c3 = cospi(2.0 * uniform_d(w.w));
+  return make_double3(r01 * c1, r01 * s1, r23 * c3);
+}
+
+// ---------------------------------------------------------------------------
+// Material model (Sec. 2.1): mu(E) = mu0 / (1 + (mu0 E / vsat)^beta)^(1/beta).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float mobility_f(const Phys& ph, int spec, float E) {
+  const float mu0 = ph.f_mu0[spec];
+  if (ph.mob_model == 1) return mu0;
+  const float x = mu0 * E / ph.f_vsat[spec];
+  return mu0 / powf(1.0f + powf(x, ph.f_beta[spec]), ph.f_ibeta[spec]);
+}
+__device__ __forceinline__ double mobility_d(const Phys& ph, int spec, double E) {
+  const double mu0 = ph.mu0[spec];
+  if (ph.mob_model == 1) return mu0;
+  const double x = __ddiv_rn(__dmul_rn(mu0, E), ph.vsat[spec]);
+  return __ddiv_rn(mu0, pow(__dadd_rn(1.0, pow(x, ph.beta[spec])), __drcp_rn(ph.beta[spec])));
+}
+
+// Frame anchor of a species for the next step: the drift-only motion of the
+// cloud centre.  One body (noinline, explicit rounding) so every CTA that
+// evaluates it for a slot gets the same bits.
+__device__ __noinline__ double anchor_next(const Phys& ph, int spec, double z) {
+  if (!ph.drift) return z;
+  const double E = __dsub_rn(ph.ea, __dmul_rn(ph.eb, z));
+  const double v = __dmul_rn(mobility_d(ph, spec, E), E);
+  const double dz = __dmul_rn(v, ph.dt);
+  const double zn = spec == 0 ? __dsub_rn(z, dz) : __dadd_rn(z, dz);
+  return fmin(fmax(zn, 0.0), ph.H);
+}
+
+// ---------------------------------------------------------------------------
+// TMA bulk copies into shared memory, completed on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes,
+                                            uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after kWaitLimit polls (far beyond any copy time).
+constexpr uint32_t kWaitLimit = 1u << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// The pair loop over n staged sources: acc_i += (r_i - r_j) / (|r_i - r_j|^2 +
+// eps^2)^(3/2), or the reversed difference for sources of the opposite sign.
+template <int R, bool NEG>
+__device__ __forceinline__ void pair_chunk(const float4* __restrict__ sj, int n,
+                                           const float (&xi)[R], const float (&yi)[R],
+                                           const float (&zi)[R], float (&ax)[R], float (&ay)[R],
+                                           float (&az)[R], float eps2) {
+  int j = 0;
+  for (; j + 2 <= n; j += 2) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float4 q = sj[j + h];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float dx = NEG ? q.x - xi[r] : xi[r] - q.x;
+        const float dy = NEG ? q.y - yi[r] : yi[r] - q.y;
+        const float dz = NEG ? q.z - zi[r] : zi[r] - q.z;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+        const float rs = rsqrt_approx(r2);
+        const float w = (rs * rs) * rs;
+        ax[r] = fmaf(dx, w, ax[r]);
+        ay[r] = fmaf(dy, w, ay[r]);
+        az[r] = fmaf(dz, w, az[r]);
+      }
+    }
+  }
+  for (; j < n; ++j) {
+    const float4 q = sj[j];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float dx = NEG ? q.x - xi[r] : xi[r] - q.x;
+      const float dy = NEG ? q.y - yi[r] : yi[r] - q.y;
+      const float dz = NEG ? q.z - zi[r] : zi[r] - q.z;
+      const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+      const float rs = rsqrt_approx(r2);
+      const float w = (rs * rs) * rs;
+      ax[r] = fmaf(dx, w, ax[r]);
+      ay[r] = fmaf(dy, w, ay[r]);
+      az[r] = fmaf(dz, w, az[r]);
+    }
+  }
+}
+
+// Kahan step (Higham, Accuracy and Stability, Alg. 4.2): s += t with the
+// running compensation c.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float t) {
+  const float y = t - c;
+  const float u = s + y;
+  c = (u - s) - y;
+  s = u;
+}
+
+// Position update of one carrier (Eqs. 3, 5, 6; Sec. 2.1) with the field E
+// (V/um) of its step, collection/exit and the next shadow entry.
+__device__ __forceinline__ void update_carrier(const StepArgs& a, SlotDev* S, int slot, int spec,
+                                               int64_t idx, int step, int p, int k, float Ex,
+                                               float Ey, float Ez, double azn) {
+  const Phys& ph = a.ph;
+  float4* __restrict__ shout = a.A.sh[p ^ 1];
+  const int id = a.A.cid[idx];
+  const int64_t rid = S->base + id;
+  const int8_t st = a.A.cstate[rid];
+  if ((st & kStateMask) != kStateActive) {
+    shout[idx] = make_float4(kParked, kParked, kParked, 0.0f);
+    return;
+  }
+  double x = a.A.px[idx], y = a.A.py[idx], z = a.A.pz[idx];
+  if (ph.drift) Ez -= ph.f_ea - ph.f_eb * (float)z;
+  const float Em = sqrtf(Ex * Ex + Ey * Ey + Ez * Ez);
+  const float mu = mobility_f(ph, spec, Em);
+  const float c = (spec ? -mu : mu) * ph.f_dt;
+  float dx = c * Ex, dy = c * Ey, dz = c * Ez;
+  if (ph.diffusion) {
+    const float3 n = normals_f(stream_words(S->seed, S->event_id, 0u, (uint32_t)id, (uint32_t)step));
+    const float amp = sqrtf(2.0f * mu * ph.f_kT * ph.f_dt);
+    dx = fmaf(amp, n.x, dx);
+    dy = fmaf(amp, n.y, dy);
+    dz = fmaf(amp, n.z, dz);
+  }
+  if (!(isfinite(dx) && isfinite(dy) && isfinite(dz))) atomicOr(&S->flags, kErrNumeric);
+  x += (double)dx;
+  y += (double)dy;
+  z += (double)dz;
+  int retire = 0;
+  if (spec == 0) {
+    if (z <= 0.0) retire = kStateCollected;
+    else if (z > ph.H) z = 2.0 * ph.H - z;
+  } else {
+    if (z >= ph.H) retire = kStateExited;
+    else if (z < 0.0) z = -z;
+  }
+  a.A.px[idx] = x;
+  a.A.py[idx] = y;
+  a.A.pz[idx] = z;
+  if (retire) {
+    a.A.cstate[rid] = (int8_t)((st & kElectronBit) | retire);
+    a.A.rstep[rid] = step;
+    if (retire == kStateCollected) {
+      a.A.fx[rid] = x;
+      a.A.fy[rid] = y;
+    }
+    atomicAdd(&a.ret[((int64_t)k * a.S + slot) * 2 + spec], 1);
+    shout[idx] = make_float4(kParked, kParked, kParked, 0.0f);
+  } else {
+    shout[idx] = make_float4((float)(x - S->ax), (float)(y - S->ay), (float)(z - azn), 0.0f);
+  }
+}
+
+// Per-slot duties of a step, done once per slot: interaction count, step
+// count and the next frame anchors.
+__device__ __forceinline__ void slot_duties(const StepArgs& a, SlotDev* S, int step, int p,
+                                            int nah, int nae) {
+  const long long n = (long long)nah + (long long)nae;
+  atomicAdd(&S->interactions, (unsigned long long)(n * (n - 1)));
+  S->n_steps = step + 1;
+  S->az[p ^ 1][0] = anchor_next(a.ph, 0, S->az[p][0]);
+  S->az[p ^ 1][1] = anchor_next(a.ph, 1, S->az[p][1]);
+}
+
+// Active carriers of a slot at chunk step k.
+__device__ __forceinline__ void active_counts(const StepArgs& a, const SlotDev* S, int slot, int k,
+                                              int& nah, int& nae) {
+  nah = S->act_h;
+  nae = S->act_e;
+  for (int kk = 0; kk < k; ++kk) {
+    nah -= a.ret[((int64_t)kk * a.S + slot) * 2 + 0];
+    nae -= a.ret[((int64_t)kk * a.S + slot) * 2 + 1];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The step kernel.
+// ---------------------------------------------------------------------------
+template <int NT, int R>
+__global__ void __launch_bounds__(NT) step_kernel(StepArgs a, int k) {
+  constexpr int TI = NT * R;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float4* stage = reinterpret_cast<float4*>(smem_raw);  // [2][kChunkJ]
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_u, s_skip, s_last, s_nah, s_nae, s_step;
+  __shared__ double s_azn[2];
+  __shared__ float s_off;
+
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  uint32_t uses[2] = {0u, 0u};
+  bool failed = false;
+  const int n_units = *a.n_units;
+  const float eps2 = a.ph.f_eps2;
+
+  for (;;) {
+    if (tid == 0) s_u = atomicAdd(&a.unit_counter[k], 1);
+    __syncthreads();
+    const int u = s_u;
+    if (u >= n_units) break;
+    const Unit U = a.units[u];
+    SlotDev* S = a.slots + U.slot;
+    if (tid == 0) {
+      int nah, nae;
+      active_counts(a, S, U.slot, k, nah, nae);
+      const int step = S->step0 + k;
+      s_nah = nah;
+      s_nae = nae;
+      s_step = step;
+      s_skip = (!S->running) || nah <= 0 || (int64_t)step >= a.ph.max_steps;
+      if (!s_skip) {
+        const int p = step & 1;
+        s_azn[0] = anchor_next(a.ph, 0, S->az[p][0]);
+        s_azn[1] = anchor_next(a.ph, 1, S->az[p][1]);
+        s_off = (float)(S->az[p][1] - S->az[p][0]);
+        if (a.fused && U.spec == 0 && U.i0 == 0 && U.split == 0)
+          slot_duties(a, S, step, p, nah, nae);
+      }
+    }
+    __syncthreads();
+    if (s_skip) {
+      __syncthreads();
+      continue;
+    }
+    const int step = s_step;
+    const int p = step & 1;
+    const float4* __restrict__ shin = a.A.sh[p];
+    const int64_t ibase = S->base + (U.spec ? S->cap_h : 0);
+    const int nh = S->n_h, ne = S->n_e;
+
+    float xi[R], yi[R], zi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int li = r * NT + tid;
+      const float4 q = li < U.ni ? shin[ibase + U.i0 + li]
+                                 : make_float4(kParked, kParked, kParked, 0.0f);
+      xi[r] = q.x;
+      yi[r] = q.y;
+      zi[r] = q.z + (U.spec ? s_off : 0.0f);  // hole frame
+    }
+    float sx[R], sy[R], sz[R], cx[R], cy[R], cz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) sx[r] = sy[r] = sz[r] = cx[r] = cy[r] = cz[r] = 0.0f;
+
+    if (a.ph.repulsion) {
+      const int h0 = max(U.j0, 0), h1 = min(U.j1, nh);
+      const int e0 = max(U.j0, nh), e1 = min(U.j1, nh + ne);
+      const int len_h = max(h1 - h0, 0), len_e = max(e1 - e0, 0);
+      const int nch_h = (len_h + kChunkJ - 1) / kChunkJ;
+      const int nch = nch_h + (len_e + kChunkJ - 1) / kChunkJ;
+      const float4* src_h = shin + S->base + h0;
+      const float4* src_e = shin + S->base + S->cap_h + (e0 - nh);
+      auto chunk_src = [&](int c, int& cnt) -> const float4* {
+        if (c < nch_h) {
+          cnt = min(kChunkJ, len_h - c * kChunkJ);
+          return src_h + (int64_t)c * kChunkJ;
+        }
+        const int ce = c - nch_h;
+        cnt = min(kChunkJ, len_e - ce * kChunkJ);
+        return src_e + (int64_t)ce * kChunkJ;
+      };
+      if (tid == 0 && nch > 0) {
+        int cnt;
+        const float4* src = chunk_src(0, cnt);
+        tma_load_1d(stage, src, (uint32_t)cnt * 16u, &bar[0]);
+      }
+      for (int c = 0; c < nch; ++c) {
+        const int st = c & 1;
+        int cnt;
+        chunk_src(c, cnt);
+        if (tid == 0 && c + 1 < nch) {
+          int cn;
+          const float4* src = chunk_src(c + 1, cn);
+          tma_load_1d(stage + (st ^ 1) * kChunkJ, src, (uint32_t)cn * 16u, &bar[st ^ 1]);
+        }
+        const bool ok = mbar_wait_bounded(&bar[st], uses[st] & 1u);
+        uses[st]++;
+        if (__syncthreads_or(!ok)) {
+          // A copy never completed: record it, give the copy still in flight
+          // a bounded wait, and stop this CTA.
+          if (tid == 0) {
+            atomicOr(a.err, kErrTimeout);
+            if (c + 1 < nch) mbar_wait_bounded(&bar[st ^ 1], uses[st ^ 1] & 1u);
+          }
+          failed = true;
+          break;
+        }
+        if (c == nch_h) {
+          // electron sources: positions of the i's in the electron frame
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int li = r * NT + tid;
+            const float zq = li < U.ni ? shin[ibase + U.i0 + li].z : kParked;
+            zi[r] = U.spec ? zq : zq - s_off;
+          }
+        }
+        float tx[R], ty[R], tz[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) tx[r] = ty[r] = tz[r] = 0.0f;
+        const float4* sj = stage + st * kChunkJ;
+        if (c < nch_h)
+          pair_chunk<R, false>(sj, cnt, xi, yi, zi, tx, ty, tz, eps2);
+        else
+          pair_chunk<R, true>(sj, cnt, xi, yi, zi, tx, ty, tz, eps2);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          kahan_add(sx[r], cx[r], tx[r]);
+          kahan_add(sy[r], cy[r], ty[r]);
+          kahan_add(sz[r], cz[r], tz[r]);
+        }
+        __syncthreads();
+      }
+      if (failed) break;
+    }
+    float vx[R], vy[R], vz[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      vx[r] = sx[r] - cx[r];
+      vy[r] = sy[r] - cy[r];
+      vz[r] = sz[r] - cz[r];
+    }
+
+    if (U.nsplit > 1) {
+      float* part = a.partial + U.pbase + (int64_t)U.split * 3 * TI;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int li = r * NT + tid;
+        part[li] = vx[r];
+        part[TI + li] = vy[r];
+        part[2 * TI + li] = vz[r];
+      }
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        const int old = atomicAdd(&a.combine_count[U.iblock], 1);
+        s_last = (old == U.nsplit - 1);
+        if (s_last) a.combine_count[U.iblock] = 0;
+      }
+      __syncthreads();
+      if (!s_last) {
+        __syncthreads();
+        continue;
+      }
+      __threadfence();
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int li = r * NT + tid;
+        double bx = 0.0, by = 0.0, bz = 0.0;
+        for (int s = 0; s < U.nsplit; ++s) {
+          const float* q = a.partial + U.pbase + (int64_t)s * 3 * TI;
+          bx += (double)__ldcg(q + li);
+          by += (double)__ldcg(q + TI + li);
+          bz += (double)__ldcg(q + 2 * TI + li);
+        }
+        vx[r] = (float)bx;
+        vy[r] = (float)by;
+        vz[r] = (float)bz;
+      }
+    }
+
+    const float kc = a.ph.f_kc;
+    if (a.fused) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int li = r * NT + tid;
+        if (li < U.ni)
+          update_carrier(a, S, U.slot, U.spec, ibase + U.i0 + li, step, p, k, kc * vx[r],
+                         kc * vy[r], kc * vz[r], s_azn[U.spec]);
+      }
+    } else {
+      const int64_t cap = a.A.capacity;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int li = r * NT + tid;
+        if (li < U.ni) {
+          const int64_t idx = ibase + U.i0 + li;
+          a.field_out[idx] = kc * vx[r];
+          a.field_out[cap + idx] = kc * vy[r];
+          a.field_out[2 * cap + idx] = kc * vz[r];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Update alone: reads the field written by a FIELD_ONLY step launch.
+__global__ void update_kernel(StepArgs a, int k, const int32_t* slot_list, int n_slots) {
+  for (int q = 0; q < n_slots; ++q) {
+    const int slot = slot_list[q];
+    SlotDev* S = a.slots + slot;
+    int nah, nae;
+    active_counts(a, S, slot, k, nah, nae);
+    const int step = S->step0 + k;
+    if (!S->running || nah <= 0 || (int64_t)step >= a.ph.max_steps) continue;
+    const int p = step & 1;
+    const double azn0 = anchor_next(a.ph, 0, S->az[p][0]);
+    const double azn1 = anchor_next(a.ph, 1, S->az[p][1]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) slot_duties(a, S, step, p, nah, nae);
+    const int n = S->n_h + S->n_e;
+    const int64_t cap = a.A.capacity;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+      const int spec = t < S->n_h ? 0 : 1;
+      const int64_t idx = S->base + (spec ? S->cap_h + (t - S->n_h) : t);
+      update_carrier(a, S, slot, spec, idx, step, p, k, a.field_out[idx], a.field_out[cap + idx],
+                     a.field_out[2 * cap + idx], spec ? azn1 : azn0);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block-wide order-preserving compaction of one species range (in place).
+// ---------------------------------------------------------------------------
+constexpr int kAuxThreads = 256;
+
+__device__ int block_exclusive_scan(int v, int* warp_sums, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, v != 0);
+  const int within = __popc(m & ((1u << lane) - 1u));
+  if (lane == 0) warp_sums[warp] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      const int t = warp_sums[w];
+      warp_sums[w] = acc;
+      acc += t;
+    }
+    *total = acc;
+  }
+  __syncthreads();
+  return warp_sums[warp] + within;
+}
+
+__device__ int compact_range(const Arena& A, int64_t start, int n, int64_t rbase, int p,
+                             int* warp_sums, int* total) {
+  int out = 0;
+  for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+    const int i = c0 + threadIdx.x;
+    int keep = 0, id = 0;
+    double x = 0, y = 0, z = 0;
+    float4 s = make_float4(0, 0, 0, 0);
+    if (i < n) {
+      id = A.cid[start + i];
+      keep = (A.cstate[rbase + id] & kStateMask) == kStateActive;
+      if (keep) {
+        x = A.px[start + i];
+        y = A.py[start + i];
+        z = A.pz[start + i];
+        s = A.sh[p][start + i];
+      }
+    }
+    const int pos = block_exclusive_scan(keep, warp_sums, total);
+    const int tot = *total;
+    __syncthreads();
+    if (keep) {
+      const int64_t d = start + out + pos;
+      A.px[d] = x;
+      A.py[d] = y;
+      A.pz[d] = z;
+      A.cid[d] = id;
+      A.sh[p][d] = s;
+    }
+    out += tot;
+    __syncthreads();
+  }
+  return out;
+}
+
+__global__ void __launch_bounds__(kAuxThreads) close_kernel(Phys ph, Arena A, SlotDev* slots,
+                                                            const int32_t* ret, int S_count, int K,
+                                                            SlotSummary* summary) {
+  __shared__ int warp_sums[kAuxThreads / 32];
+  __shared__ int total;
+  const int slot = blockIdx.x;
+  SlotDev* S = slots + slot;
+  SlotSummary sm{};
+  if (!S->running) {
+    if (threadIdx.x == 0) summary[slot] = sm;
+    return;
+  }
+  int nah = S->act_h, nae = S->act_e;
+  for (int kk = 0; kk < K; ++kk) {
+    nah -= ret[((int64_t)kk * S_count + slot) * 2 + 0];
+    nae -= ret[((int64_t)kk * S_count + slot) * 2 + 1];
+  }
+  int done = 0, status = 0;
+  if (S->flags & kErrNumeric) {
+    done = 1;
+    status = -7;
+  } else if (nah <= 0) {
+    done = 1;
+  } else if ((int64_t)S->step0 + K >= ph.max_steps) {
+    done = 1;
+    status = -6;
+  }
+  int n_h = S->n_h, n_e = S->n_e;
+  if (!done) {
+    const int p = (S->step0 + K) & 1;
+    if (nah != n_h) n_h = compact_range(A, S->base, n_h, S->base, p, warp_sums, &total);
+    if (nae != n_e) n_e = compact_range(A, S->base + S->cap_h, n_e, S->base, p, warp_sums, &total);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!done) {
+      S->n_h = n_h;
+      S->n_e = n_e;
+      S->act_h = nah;
+      S->act_e = nae;
+      S->step0 += K;
+    } else {
+      S->running = 0;
+      S->status = status;
+      S->act_h = nah;
+      S->act_e = nae;
+    }
+    sm.running = !done;
+    sm.done = done;
+    sm.status = status;
+    sm.n_steps = S->n_steps;
+    sm.n_h = n_h;
+    sm.n_e = n_e;
+    sm.act_h = nah;
+    sm.act_e = nae;
+    sm.flags = S->flags;
+    sm.interactions = S->interactions;
+    summary[slot] = sm;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial cloud (Algorithm 1, first step; Eq. 2), one CTA per new slot.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, SlotDev* slots,
+                                                           const int32_t* slot_list,
+                                                           const ExplicitRec* ex) {
+  __shared__ int ret_h, ret_e;
+  SlotDev* S = slots + slot_list[blockIdx.x];
+  if (threadIdx.x == 0) {
+    ret_h = 0;
+    ret_e = 0;
+  }
+  __syncthreads();
+  const int np = S->n_pairs;
+  const int n_tot = S->n_total;
+  const double H = ph.H;
+  const double sigma = S->sigma_um >= 0.0 ? S->sigma_um : 0.0044 * pow(S->energy_keV, 1.75);
+  const double z_entry = H - S->depth_um;
+  const double th = S->theta_deg * (M_PI / 180.0), phi = S->phi_deg * (M_PI / 180.0);
+  const double ux = sin(th) * cos(phi), uy = sin(th) * sin(phi), uz = -cos(th);
+  const double axv = cos(th) * cos(phi), ayv = cos(th) * sin(phi), azv = sin(th);
+  const double bxv = -sin(phi), byv = cos(phi);
+  const double az0 = fmin(fmax(S->kind == 1 ? H - 0.5 * S->track_len_um * cos(th) : z_entry, 0.0), H);
+  const int total_entries = S->cap_h + S->cap_e;
+
+  for (int e = threadIdx.x; e < total_entries; e += blockDim.x) {
+    const int spec = e < S->cap_h ? 0 : 1;
+    const int64_t idx = S->base + e;
+    double x, y, z;
+    int id;
+    if (S->kind == 2) {
+      const ExplicitRec r = ex[S->explicit_off + e];
+      x = r.x; y = r.y; z = r.z; id = r.cid;
+    } else {
+      const int pidx = spec ? e - S->cap_h : e;
+      id = spec ? np + pidx : pidx;
+      const double3 n = normals_d(stream_words(S->seed, S->event_id, 1u, (uint32_t)pidx, 0u));
+      if (S->kind == 1) {
+        const uint4 w = stream_words(S->seed, S->event_id, 1u, (uint32_t)pidx, 1u);
+        const double s = uniform_d(w.x) * S->track_len_um;
+        x = S->x0 + s * ux + sigma * (n.x * axv + n.y * bxv);
+        y = S->y0 + s * uy + sigma * (n.x * ayv + n.y * byv);
+        z = H + s * uz + sigma * (n.x * azv);
+      } else {
+        x = S->x0 + sigma * n.x;
+        y = S->y0 + sigma * n.y;
+        z = z_entry + sigma * n.z;
+      }
+    }
+    const int64_t rid = S->base + id;
+    int state = kStateActive;
+    if (spec == 0) {
+      if (z <= 0.0) state = kStateCollected;
+      else if (z > H) z = 2.0 * H - z;
+    } else {
+      if (z >= H) state = kStateExited;
+      else if (z < 0.0) z = -z;
+    }
+    A.px[idx] = x;
+    A.py[idx] = y;
+    A.pz[idx] = z;
+    A.cid[idx] = id;
+    A.cstate[rid] = (int8_t)((spec ? kElectronBit : 0) | state);
+    A.rstep[rid] = state == kStateActive ? -2 : -1;
+    A.fx[rid] = state == kStateCollected ? x : __longlong_as_double(0x7ff8000000000000LL);
+    A.fy[rid] = state == kStateCollected ? y : __longlong_as_double(0x7ff8000000000000LL);
+    if (state != kStateActive) {
+      atomicAdd(spec ? &ret_e : &ret_h, 1);
+      A.sh[0][idx] = make_float4(kParked, kParked, kParked, 0.0f);
+    } else {
+      A.sh[0][idx] = make_float4((float)(x - S->x0), (float)(y - S->y0), (float)(z - az0), 0.0f);
+    }
+  }
+  (void)n_tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S->ax = S->x0;
+    S->ay = S->y0;
+    S->az[0][0] = S->az[0][1] = az0;
+    S->az[1][0] = S->az[1][1] = az0;
+    S->n_h = S->cap_h;
+    S->n_e = S->cap_e;
+    S->act_h = S->cap_h - ret_h;
+    S->act_e = S->cap_e - ret_e;
+    S->step0 = 0;
+    S->n_steps = 0;
+    S->flags = 0;
+    S->status = 0;
+    S->interactions = 0ull;
+    S->running = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Readout: pixel = floor(x / pitch + n/2) per axis, warp-aggregated counts.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int pixel_key(const Phys& ph, double x, double y) {
+  const double half = 0.5 * (double)ph.grid_n;
+  const double fx = floor(__dadd_rn(__ddiv_rn(x, ph.pitch), half));
+  const double fy = floor(__dadd_rn(__ddiv_rn(y, ph.pitch), half));
+  if (!(fx >= 0.0 && fy >= 0.0 && fx < (double)ph.grid_n && fy < (double)ph.grid_n)) return -1;
+  return (int)fy * ph.grid_n + (int)fx;
+}
+
+// key >= 0: pixel; -1: outside; -2: nothing.  Lanes with equal keys add once.
+__device__ __forceinline__ void warp_count(int key, int32_t* pix, int* outside) {
+  const unsigned grp = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(grp) - 1;
+  if ((int)(threadIdx.x & 31) == leader) {
+    if (key >= 0) atomicAdd(pix + key, __popc(grp));
+    else if (key == -1) atomicAdd(outside, __popc(grp));
+  }
+}
+
+__global__ void __launch_bounds__(kAuxThreads) bin_kernel(Phys ph, Arena A, const SlotDev* slots,
+                                                          const int32_t* slot_list,
+                                                          int32_t* pixels, SlotReadout* readout) {
+  __shared__ int outside, collected, lost;
+  const int slot = slot_list[blockIdx.x];
+  const SlotDev* S = slots + slot;
+  const int npix = ph.grid_n * ph.grid_n;
+  int32_t* pix = pixels + (int64_t)slot * npix;
+  for (int t = threadIdx.x; t < npix; t += blockDim.x) pix[t] = 0;
+  if (threadIdx.x == 0) outside = collected = lost = 0;
+  __syncthreads();
+  const int n = S->n_total;
+  const int n_round = (n + blockDim.x - 1) / blockDim.x * blockDim.x;
+  for (int id = threadIdx.x; id < n_round; id += blockDim.x) {
+    int key = -2;
+    if (id < n) {
+      const int8_t st = A.cstate[S->base + id];
+      if ((st & kStateMask) == kStateCollected) {
+        key = pixel_key(ph, A.fx[S->base + id], A.fy[S->base + id]);
+        atomicAdd(&collected, 1);
+      } else if ((st & kStateMask) == kStateActive && (st & kElectronBit)) {
+        atomicAdd(&lost, 1);
+      }
+    }
+    warp_count(key, pix, &outside);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    SlotReadout r{};
+    r.n_collected = collected;
+    r.n_outside = outside;
+    r.n_lost = lost;
+    readout[slot] = r;
+  }
+}
+
+__global__ void bin_points_kernel(Phys ph, const double* x, const double* y, int64_t n,
+                                  int32_t* pix, long long* outside_total) {
+  __shared__ int outside;
+  if (threadIdx.x == 0) outside = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n_round = (n + stride - 1) / stride * stride;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_round; i += stride) {
+    const int key = i < n ? pixel_key(ph, x[i], y[i]) : -2;
+    warp_count(key, pix, &outside);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    atomicAdd(reinterpret_cast<unsigned long long*>(outside_total), (unsigned long long)outside);
+}
+
+// ---------------------------------------------------------------------------
+// Test hooks.
+// ---------------------------------------------------------------------------
+__global__ void philox_kernel(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                              uint32_t* curand_out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = make_uint4(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]);
+  const uint4 o = philox10(c, make_uint2(key[2 * i], key[2 * i + 1]));
+  out[4 * i] = o.x;
+  out[4 * i + 1] = o.y;
+  out[4 * i + 2] = o.z;
+  out[4 * i + 3] = o.w;
+  if (curand_out) {
+    // curand's Philox4_32_10 stream: counter words (c0, c1) advance with the
+    // offset (4 outputs per counter value), (c2, c3) hold the subsequence.
+    curandStatePhilox4_32_10_t st;
+    const unsigned long long seed = ((unsigned long long)key[2 * i + 1] << 32) | key[2 * i];
+    const unsigned long long sub = ((unsigned long long)c.w << 32) | c.z;
+    const unsigned long long off = (((unsigned long long)c.y << 32) | c.x) * 4ull;
+    curand_init(seed, sub, off, &st);
+    const uint4 r = curand4(&st);
+    curand_out[4 * i] = r.x;
+    curand_out[4 * i + 1] = r.y;
+    curand_out[4 * i + 2] = r.z;
+    curand_out[4 * i + 3] = r.w;
+  }
+}
+
+__global__ void normals_kernel(const unsigned long long* in, int64_t n, double* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long* t = in + 5 * i;
+  const float3 v = normals_f(stream_words(t[0], t[1], (uint32_t)t[2], (uint32_t)t[3], (uint32_t)t[4]));
+  out[3 * i] = v.x;
+  out[3 * i + 1] = v.y;
+  out[3 * i + 2] = v.z;
+}
+
+// ---------------------------------------------------------------------------
+// Variant table.
+// ---------------------------------------------------------------------------
+struct VariantEntry {
+  int nt, r;
+  const char* name;
+  void (*fn)(StepArgs, int);
+};
+
+const VariantEntry kVariants[] = {
+    {128, 4, "nt128_r4", step_kernel<128, 4>},
+    {256, 4, "nt256_r4", step_kernel<256, 4>},
+    {128, 8, "nt128_r8", step_kernel<128, 8>},
+    {256, 2, "nt256_r2", step_kernel<256, 2>},
+    {64, 8, "nt64_r8", step_kernel<64, 8>},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+constexpr size_t kStageBytes = 2 * kChunkJ * sizeof(float4);
+
+}  // namespace
+
+int variant_count() { return kNumVariants; }
+
+Variant variant_info(int v) {
+  const VariantEntry& e = kVariants[v];
+  return Variant{e.nt, e.r, e.name};
+}
+
+size_t variant_smem(int) { return kStageBytes; }
+
+cudaError_t variant_occupancy(int v, int* blocks_per_sm) {
+  const VariantEntry& e = kVariants[v];
+  cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kStageBytes);
+  if (err != cudaSuccess) return err;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.nt, kStageBytes);
+}
+
+cudaError_t launch_step(int v, const StepArgs& a, int k, int grid, cudaStream_t s) {
+  const VariantEntry& e = kVariants[v];
+  e.fn<<<grid, e.nt, kStageBytes, s>>>(a, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update(const StepArgs& a, int k, int n_slots_list, const int32_t* slot_list,
+                          int grid, cudaStream_t s) {
+  update_kernel<<<grid, 256, 0, s>>>(a, k, slot_list, n_slots_list);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init(const Phys& ph, Arena A, SlotDev* slots, const int32_t* slot_list, int n,
+                        const ExplicitRec* explicit_buf, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  init_kernel<<<n, kAuxThreads, 0, s>>>(ph, A, slots, slot_list, explicit_buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_close(const Phys& ph, Arena A, SlotDev* slots, const int32_t* /*slot_list*/,
+                         int n, const int32_t* ret, int S, int K, SlotSummary* summary,
+                         cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  close_kernel<<<n, kAuxThreads, 0, s>>>(ph, A, slots, ret, S, K, summary);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const Phys& ph, Arena A, const SlotDev* slots, const int32_t* slot_list,
+                       int n, int32_t* pixels, SlotReadout* readout, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  bin_kernel<<<n, kAuxThreads, 0, s>>>(ph, A, slots, slot_list, pixels, readout);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, int64_t n,
+                              int32_t* pixels, long long* outside, cudaStream_t s) {
+  const int threads = 256;
+  int grid = (int)((n + threads - 1) / threads);
+  grid = grid < 1 ? 1 : (grid > 4096 ? 4096 : grid);
+  bin_points_kernel<<<grid, threads, 0, s>>>(ph, x, y, n, pixels, outside);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                          uint32_t* curand_out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  philox_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(ctr, key, n, out, curand_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_normals(const unsigned long long* in, int64_t n, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  normals_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(in, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace cts

@@ -1,0 +1,1413 @@
+// cts_runtime.cu -- host runtime behind include/cts.h: handle, device arena,
+// admission queue, slot scheduler, graph-captured K-step chunks, readout and
+// the serving thread.  All arithmetic of the method runs in cts_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "cts.h"
+#include "cts_host_impl.h"
+#include "cts_internal.h"
+
+using namespace cts;
+
+namespace {
+
+double now_ns() {
+  return (double)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+constexpr int kDefaultSlots = 256;
+constexpr int kDefaultK = 32;
+constexpr int64_t kDefaultBudget = 1ll << 30;
+constexpr int kMaxUnits = 1 << 16;
+constexpr int kDefaultQueue = 1 << 16;
+// arena (positions, two shadows, id, collection point, step, state), explicit
+// staging, j-split partial sums (12 floats) and the PLAIN field buffer
+constexpr int64_t kBytesPerCarrier = 24 + 32 + 4 + 16 + 4 + 1 + 32 + 48 + 12;
+
+struct EventRec {
+  sim_event_t ev{};
+  std::vector<double> xyz;
+  std::vector<int8_t> sign;
+  int32_t n_pairs = 0;
+  int32_t cap_h = 0, cap_e = 0;
+  double t_submit = 0.0;
+  int64_t order = 0;
+};
+
+struct Done {
+  uint64_t event_id = 0;
+  int32_t status = 0, n_carriers = 0;
+  int64_t n_steps = 0, n_collected = 0, n_outside = 0, n_lost = 0, interactions = 0;
+  double t_submit = 0, t_start = 0, t_done = 0;
+  std::vector<int32_t> pixels;
+  std::vector<double> final_xy;
+  std::vector<int32_t> rstep;
+  int64_t order = 0;
+};
+
+struct HostSlot {
+  bool used = false;
+  bool running = false;
+  bool needs_init = false;
+  bool finished_on_device = false;  // readout done, results still on the device
+  EventRec rec;
+  int64_t base = 0;
+  double t_start = 0;
+  int32_t n_h = 0, n_e = 0;
+  int32_t status = 0;
+  int64_t n_steps = 0, interactions = 0;
+};
+
+}  // namespace
+
+struct sim_t {
+  sim_sensor_t sensor{};
+  sim_field_t field{};
+  sim_mobility_t mob{};
+  sim_options_t opt{};
+  Phys ph{};
+  int device = 0, sm_count = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int S = 0, K = 0, variant = 0, grid = 0, tile_i = 0;
+  int64_t capacity = 0, partial_cap = 0;
+  bool broken = false;
+  std::string err;
+
+  // device buffers
+  Arena A{};
+  SlotDev* d_slots = nullptr;
+  SlotSummary* d_summary = nullptr;
+  SlotReadout* d_readout = nullptr;
+  int32_t* d_pixels = nullptr;
+  Unit* d_units = nullptr;
+  int32_t* d_n_units = nullptr;
+  int32_t* d_unit_counter = nullptr;
+  int32_t* d_ret = nullptr;
+  float* d_partial = nullptr;
+  int32_t* d_combine = nullptr;
+  int32_t* d_err = nullptr;
+  float* d_field = nullptr;
+  ExplicitRec* d_explicit = nullptr;
+  int32_t* d_list = nullptr;
+  // pinned host staging
+  SlotSummary* h_summary = nullptr;
+  Unit* h_units = nullptr;
+  int32_t* h_n_units = nullptr;
+  int32_t* h_list = nullptr;
+  SlotDev* h_slotdev = nullptr;
+  SlotReadout* h_readout = nullptr;
+  int32_t* h_pixels = nullptr;
+  int32_t* h_err = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  // host state
+  std::vector<HostSlot> slots;
+  ArenaAllocator alloc;
+  std::vector<UnitPlan> plan;
+  std::mutex qmu;
+  std::condition_variable qcv;
+  std::deque<EventRec> queue;
+  std::mutex dmu;
+  std::condition_variable dcv;
+  std::deque<Done> done;
+  std::mutex drive_mu;
+  std::thread engine;
+  std::atomic<bool> stop{false};
+  int64_t order_counter = 0;
+  int inject = 0;
+  std::vector<int> staged;  // slots admitted by sim_stage, in staging order
+
+  // graph cache
+  cudaGraphExec_t graph = nullptr;
+  int graph_K = -1, graph_v = -1, graph_grid = -1;
+
+  // stats
+  int64_t st_events = 0, st_inter = 0, st_steps = 0, st_launch = 0, st_chunks = 0,
+          st_rejected = 0;
+  double st_ms = 0.0;
+};
+
+namespace {
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      s->broken = true;                                                            \
+      s->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+      return SIM_ECUDA;                                                            \
+    }                                                                              \
+  } while (0)
+
+bool finite_all(std::initializer_list<double> v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+int validate_params(const sim_sensor_t* se, const sim_field_t* f, const sim_mobility_t* m) {
+  if (!se || !f || !m) return SIM_EINVAL;
+  if (!finite_all({se->thickness_um, se->bias_V, se->depletion_V, se->temperature_K, se->eps_r,
+                   se->pitch_um, se->dt_ps, se->softening_um}))
+    return SIM_EINVAL;
+  if (!(se->thickness_um > 0) || !(se->temperature_K > 0) || !(se->eps_r > 0) ||
+      !(se->pitch_um > 0) || !(se->dt_ps > 0) || se->softening_um < 0)
+    return SIM_EINVAL;
+  if (!(se->depletion_V >= 0) || !(se->bias_V >= se->depletion_V)) return SIM_EINVAL;
+  if (se->grid_n < 1 || se->grid_n > 4096 || se->max_steps < 1) return SIM_EINVAL;
+  if (se->species != CTS_HOLES && se->species != CTS_BOTH) return SIM_EINVAL;
+  if (m->model != CTS_MOB_CT && m->model != CTS_MOB_CONST) return SIM_EINVAL;
+  if (!(m->mu0_h > 0) || !(m->vsat_h > 0) || !(m->beta_h > 0)) return SIM_EINVAL;
+  if (se->species == CTS_BOTH && (!(m->mu0_e > 0) || !(m->vsat_e > 0) || !(m->beta_e > 0)))
+    return SIM_EINVAL;
+  return SIM_OK;
+}
+
+Phys make_phys(const sim_sensor_t& se, const sim_field_t& f, const sim_mobility_t& m) {
+  const double e = 1.602176634e-19, eps0 = 8.8541878128e-12, kb = 1.380649e-23;
+  Phys p{};
+  p.H = se.thickness_um;
+  p.ea = (se.bias_V + se.depletion_V) / se.thickness_um;  // E at z = 0
+  p.eb = 2.0 * se.depletion_V / (se.thickness_um * se.thickness_um);
+  p.kc = e / (4.0 * M_PI * eps0 * se.eps_r) * 1e6;
+  p.kT = kb * se.temperature_K / e;
+  p.dt = se.dt_ps * 1e-3;
+  p.mu0[0] = m.mu0_h * 0.1;
+  p.vsat[0] = m.vsat_h * 1e-5;
+  p.beta[0] = m.beta_h;
+  p.mu0[1] = m.mu0_e * 0.1;
+  p.vsat[1] = m.vsat_e * 1e-5;
+  p.beta[1] = m.beta_e > 0 ? m.beta_e : 1.0;
+  p.pitch = se.pitch_um;
+  p.f_ea = (float)p.ea;
+  p.f_eb = (float)p.eb;
+  p.f_kc = (float)p.kc;
+  p.f_kT = (float)p.kT;
+  p.f_dt = (float)p.dt;
+  const double eps = se.softening_um > 0 ? se.softening_um : 1e-6;
+  p.f_eps2 = (float)(eps * eps);
+  p.f_H = (float)p.H;
+  for (int s = 0; s < 2; ++s) {
+    p.f_mu0[s] = (float)p.mu0[s];
+    p.f_vsat[s] = (float)(p.vsat[s] > 0 ? p.vsat[s] : 1.0);
+    p.f_beta[s] = (float)p.beta[s];
+    p.f_ibeta[s] = (float)(1.0 / p.beta[s]);
+    if (!(p.vsat[s] > 0)) p.vsat[s] = 1.0;
+  }
+  p.mob_model = m.model;
+  p.repulsion = f.repulsion;
+  p.drift = f.drift;
+  p.diffusion = f.diffusion;
+  p.species = se.species;
+  p.grid_n = se.grid_n;
+  p.max_steps = se.max_steps;
+  return p;
+}
+
+// Resolve and validate one event; fills counts of holes and electrons.
+int prepare_event(sim_t* s, const sim_event_t* ev, EventRec* r) {
+  if (!ev) return SIM_EINVAL;
+  r->ev = *ev;
+  r->ev.explicit_xyz = nullptr;
+  r->ev.explicit_sign = nullptr;
+  if (ev->kind != CTS_PHOTON && ev->kind != CTS_TRACK && ev->kind != CTS_EXPLICIT)
+    return SIM_EINVAL;
+  if (ev->n_pairs < 0) return SIM_EINVAL;
+  if (ev->kind == CTS_EXPLICIT) {
+    if (ev->n_pairs > 0 && !ev->explicit_xyz) return SIM_EINVAL;
+    const int n = ev->n_pairs;
+    r->xyz.assign(ev->explicit_xyz, ev->explicit_xyz + 3 * (size_t)n);
+    r->sign.assign((size_t)n, 1);
+    if (ev->explicit_sign) r->sign.assign(ev->explicit_sign, ev->explicit_sign + n);
+    for (double v : r->xyz)
+      if (!std::isfinite(v)) return SIM_EINVAL;
+    int nh = 0;
+    for (int8_t g : r->sign) {
+      if (g != 1 && g != -1) return SIM_EINVAL;
+      nh += g > 0;
+    }
+    if (nh < n && s->sensor.species != CTS_BOTH) return SIM_EINVAL;
+    r->n_pairs = n;
+    r->cap_h = nh;
+    r->cap_e = n - nh;
+  } else {
+    if (!finite_all({ev->energy_keV, ev->depth_um, ev->x_um, ev->y_um, ev->sigma_um,
+                     ev->track_len_um, ev->theta_deg, ev->phi_deg}))
+      return SIM_EINVAL;
+    if (ev->energy_keV < 0) return SIM_EINVAL;
+    if (ev->kind == CTS_PHOTON && (ev->depth_um < 0 || ev->depth_um > s->sensor.thickness_um))
+      return SIM_EINVAL;
+    if (ev->kind == CTS_TRACK && (ev->track_len_um < 0 || ev->theta_deg < 0 ||
+                                  ev->theta_deg >= 90.0))
+      return SIM_EINVAL;
+    const double np = ev->n_pairs > 0 ? (double)ev->n_pairs
+                                      : std::llround(ev->energy_keV * 1000.0 / 3.62);
+    if (np > 5.0e8) return SIM_ENOMEM_BUDGET;
+    r->n_pairs = (int32_t)np;
+    r->cap_h = r->n_pairs;
+    r->cap_e = s->sensor.species == CTS_BOTH ? r->n_pairs : 0;
+  }
+  if ((int64_t)r->cap_h + r->cap_e > s->capacity) return SIM_ENOMEM_BUDGET;
+  return SIM_OK;
+}
+
+int free_slot_index(sim_t* s) {
+  for (int k = 0; k < s->S; ++k)
+    if (!s->slots[k].used) return k;
+  return -1;
+}
+
+int running_limit(sim_t* s) { return s->opt.mode == CTS_MODE_PLAIN ? 1 : s->S; }
+
+int count_used(sim_t* s) {
+  int c = 0;
+  for (auto& h : s->slots) c += h.used;
+  return c;
+}
+
+// Place an event into a free slot: arena block, host mirror, descriptor upload.
+int place_event(sim_t* s, int slot, EventRec&& r, int64_t base) {
+  HostSlot& h = s->slots[slot];
+  h = HostSlot{};
+  h.used = true;
+  h.running = true;
+  h.needs_init = true;
+  h.base = base;
+  h.t_start = now_ns();
+  h.n_h = r.cap_h;
+  h.n_e = r.cap_e;
+  SlotDev& d = s->h_slotdev[slot];
+  d = SlotDev{};
+  d.seed = r.ev.seed;
+  d.event_id = r.ev.event_id;
+  d.base = base;
+  d.cap_h = r.cap_h;
+  d.cap_e = r.cap_e;
+  d.n_total = r.cap_h + r.cap_e;
+  d.kind = r.ev.kind;
+  d.n_pairs = r.n_pairs;
+  d.energy_keV = r.ev.energy_keV;
+  d.depth_um = r.ev.depth_um;
+  d.x0 = r.ev.x_um;
+  d.y0 = r.ev.y_um;
+  d.sigma_um = r.ev.sigma_um;
+  d.track_len_um = r.ev.track_len_um;
+  d.theta_deg = r.ev.theta_deg;
+  d.phi_deg = r.ev.phi_deg;
+  d.explicit_off = base;
+  if (r.ev.kind == CTS_EXPLICIT) {
+    // records in arena order: holes first, then electrons; the anchor is the
+    // centroid of the given positions
+    std::vector<ExplicitRec> rec((size_t)d.n_total);
+    double cx = 0, cy = 0, cz = 0;
+    int kh = 0, ke = r.cap_h;
+    for (int c = 0; c < r.n_pairs; ++c) {
+      ExplicitRec e{r.xyz[3 * c], r.xyz[3 * c + 1], r.xyz[3 * c + 2], c, r.sign[c]};
+      rec[r.sign[c] > 0 ? kh++ : ke++] = e;
+      cx += e.x;
+      cy += e.y;
+      cz += e.z;
+    }
+    if (r.n_pairs > 0) {
+      d.x0 = cx / r.n_pairs;
+      d.y0 = cy / r.n_pairs;
+      d.depth_um = s->sensor.thickness_um - cz / r.n_pairs;
+    }
+    if (!rec.empty())
+      CK(cudaMemcpyAsync(s->d_explicit + base, rec.data(), rec.size() * sizeof(ExplicitRec),
+                         cudaMemcpyHostToDevice, s->stream));
+    // keep the staging alive until the copy is done
+    CK(cudaStreamSynchronize(s->stream));
+  }
+  h.rec = std::move(r);
+  CK(cudaMemcpyAsync(s->d_slots + slot, &d, sizeof(SlotDev), cudaMemcpyHostToDevice, s->stream));
+  return SIM_OK;
+}
+
+// Admit queued events while slots and arena space allow (FIFO).
+int admit(sim_t* s) {
+  std::lock_guard<std::mutex> lk(s->qmu);
+  while (!s->queue.empty()) {
+    if (count_used(s) >= running_limit(s)) break;
+    const int slot = free_slot_index(s);
+    if (slot < 0) break;
+    EventRec& r = s->queue.front();
+    const int64_t n = std::max<int64_t>((int64_t)r.cap_h + r.cap_e, 1);
+    const int64_t base = s->alloc.alloc(n);
+    if (base < 0) break;
+    EventRec rec = std::move(r);
+    s->queue.pop_front();
+    const int rc = place_event(s, slot, std::move(rec), base);
+    if (rc) return rc;
+  }
+  return SIM_OK;
+}
+
+int launch_inits(sim_t* s) {
+  int n = 0;
+  for (int k = 0; k < s->S; ++k)
+    if (s->slots[k].used && s->slots[k].needs_init) {
+      s->h_list[n++] = k;
+      s->slots[k].needs_init = false;
+    }
+  if (!n) return SIM_OK;
+  CK(cudaMemcpyAsync(s->d_list, s->h_list, n * sizeof(int32_t), cudaMemcpyHostToDevice,
+                     s->stream));
+  CK(launch_init(s->ph, s->A, s->d_slots, s->d_list, n, s->d_explicit, s->stream));
+  // keep h_list stable until the copy has been consumed
+  CK(cudaStreamSynchronize(s->stream));
+  s->st_launch += 1;
+  return SIM_OK;
+}
+
+StepArgs step_args(sim_t* s, bool fused) {
+  StepArgs a{};
+  a.A = s->A;
+  a.slots = s->d_slots;
+  a.units = s->d_units;
+  a.n_units = s->d_n_units;
+  a.unit_counter = s->d_unit_counter;
+  a.ret = s->d_ret;
+  a.partial = s->d_partial;
+  a.combine_count = s->d_combine;
+  a.field_out = s->d_field;
+  a.err = s->d_err;
+  a.ph = s->ph;
+  a.S = s->S;
+  a.fused = fused ? 1 : 0;
+  return a;
+}
+
+// Build and upload the unit list of the running slots.
+int upload_units(sim_t* s, bool allow_split) {
+  std::vector<int32_t> nh(s->S, 0), ne(s->S, 0);
+  for (int k = 0; k < s->S; ++k)
+    if (s->slots[k].used && s->slots[k].running) {
+      nh[k] = s->slots[k].n_h;
+      ne[k] = s->slots[k].n_e;
+    }
+  int64_t pfl = 0;
+  const int rc = plan_units(nh.data(), ne.data(), s->S, s->tile_i, s->grid,
+                            allow_split && s->ph.repulsion, kMaxUnits, s->partial_cap, &s->plan,
+                            &pfl);
+  if (rc != 0) {
+    s->err = "unit plan does not fit the unit buffer";
+    return SIM_EINVAL;
+  }
+  const int n = (int)s->plan.size();
+  static_assert(sizeof(UnitPlan) == sizeof(Unit), "unit layout");
+  std::memcpy(s->h_units, s->plan.data(), n * sizeof(Unit));
+  *s->h_n_units = n;
+  CK(cudaMemcpyAsync(s->d_units, s->h_units, std::max(n, 1) * sizeof(Unit),
+                     cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->d_n_units, s->h_n_units, sizeof(int32_t), cudaMemcpyHostToDevice,
+                     s->stream));
+  return SIM_OK;
+}
+
+// Issue one chunk: K fused steps (or, in PLAIN mode, field + update launches
+// for one step), the close kernel and the summary copy.
+int issue_chunk(sim_t* s, int K) {
+  const bool plain = s->opt.mode == CTS_MODE_PLAIN;
+  CK(cudaMemsetAsync(s->d_unit_counter, 0, K * sizeof(int32_t), s->stream));
+  CK(cudaMemsetAsync(s->d_ret, 0, (size_t)K * s->S * 2 * sizeof(int32_t), s->stream));
+  if (plain) {
+    const StepArgs a = step_args(s, false);
+    CK(launch_step(s->variant, a, 0, s->grid, s->stream));
+    CK(launch_update(a, 0, 1, s->d_list, std::max(1, s->sm_count * 4), s->stream));
+    s->st_launch += 2;
+  } else {
+    const StepArgs a = step_args(s, true);
+    for (int k = 0; k < K; ++k) CK(launch_step(s->variant, a, k, s->grid, s->stream));
+    s->st_launch += K;
+  }
+  CK(launch_close(s->ph, s->A, s->d_slots, nullptr, s->S, s->d_ret, s->S, K, s->d_summary,
+                  s->stream));
+  s->st_launch += 1;
+  CK(cudaMemcpyAsync(s->h_summary, s->d_summary, s->S * sizeof(SlotSummary),
+                     cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  return SIM_OK;
+}
+
+int run_chunk(sim_t* s) {
+  const bool plain = s->opt.mode == CTS_MODE_PLAIN;
+  const int K = plain ? 1 : s->K;
+  if (plain) {
+    // the update launch walks the running slot listed in d_list
+    int n = 0;
+    for (int k = 0; k < s->S; ++k)
+      if (s->slots[k].used && s->slots[k].running) s->h_list[n++] = k;
+    CK(cudaMemcpyAsync(s->d_list, s->h_list, std::max(n, 1) * sizeof(int32_t),
+                       cudaMemcpyHostToDevice, s->stream));
+  }
+  int rc = upload_units(s, !plain);
+  if (rc) return rc;
+  CK(cudaEventRecord(s->ev0, s->stream));
+  if (!plain && !s->opt.disable_graphs) {
+    if (!s->graph || s->graph_K != K || s->graph_v != s->variant || s->graph_grid != s->grid) {
+      if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+      const int64_t launches = s->st_launch;
+      rc = issue_chunk(s, K);
+      s->st_launch = launches;
+      cudaError_t ce = cudaStreamEndCapture(s->stream, &g);
+      if (rc) return rc;
+      CK(ce);
+      CK(cudaGraphInstantiate(&s->graph, g, 0));
+      cudaGraphDestroy(g);
+      s->graph_K = K;
+      s->graph_v = s->variant;
+      s->graph_grid = s->grid;
+    }
+    CK(cudaGraphLaunch(s->graph, s->stream));
+    s->st_launch += K + 1;
+  } else {
+    rc = issue_chunk(s, K);
+    if (rc) return rc;
+  }
+  CK(cudaEventRecord(s->ev1, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
+  s->st_ms += ms;
+  s->st_steps += K;
+  s->st_chunks += 1;
+  if (*s->h_err & kErrTimeout) {
+    s->broken = true;
+    s->err = "a bounded device wait gave up";
+    return SIM_ETIMEOUT;
+  }
+  return SIM_OK;
+}
+
+// Collect results of slots finished on the device (readout already binned).
+int fetch_results(sim_t* s, const std::vector<int>& fin) {
+  if (fin.empty()) return SIM_OK;
+  const int npix = s->sensor.grid_n * s->sensor.grid_n;
+  const bool keep = s->opt.keep_final_xy != 0;
+  std::vector<std::vector<double>> fx(fin.size()), fy(fin.size());
+  std::vector<std::vector<int32_t>> rs(fin.size());
+  for (size_t q = 0; q < fin.size(); ++q) {
+    const int slot = fin[q];
+    CK(cudaMemcpyAsync(s->h_pixels + (int64_t)slot * npix, s->d_pixels + (int64_t)slot * npix,
+                       npix * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(s->h_readout + slot, s->d_readout + slot, sizeof(SlotReadout),
+                       cudaMemcpyDeviceToHost, s->stream));
+    if (keep) {
+      const HostSlot& h = s->slots[slot];
+      const int n = h.rec.cap_h + h.rec.cap_e;
+      fx[q].resize(n);
+      fy[q].resize(n);
+      rs[q].resize(n);
+      if (n) {
+        CK(cudaMemcpyAsync(fx[q].data(), s->A.fx + h.base, n * sizeof(double),
+                           cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(fy[q].data(), s->A.fy + h.base, n * sizeof(double),
+                           cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(rs[q].data(), s->A.rstep + h.base, n * sizeof(int32_t),
+                           cudaMemcpyDeviceToHost, s->stream));
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  const double t = now_ns();
+  std::vector<Done> out;
+  for (size_t q = 0; q < fin.size(); ++q) {
+    const int slot = fin[q];
+    HostSlot& h = s->slots[slot];
+    Done d;
+    d.event_id = h.rec.ev.event_id;
+    d.status = h.status;
+    d.n_carriers = h.rec.cap_h + h.rec.cap_e;
+    d.n_steps = h.n_steps;
+    d.n_collected = s->h_readout[slot].n_collected;
+    d.n_outside = s->h_readout[slot].n_outside;
+    d.n_lost = s->h_readout[slot].n_lost;
+    d.interactions = h.interactions;
+    d.t_submit = h.rec.t_submit;
+    d.t_start = h.t_start;
+    d.t_done = t;
+    d.order = h.rec.order;
+    d.pixels.assign(s->h_pixels + (int64_t)slot * npix, s->h_pixels + (int64_t)(slot + 1) * npix);
+    if (keep) {
+      const int n = d.n_carriers;
+      d.final_xy.resize(2 * (size_t)n);
+      for (int c = 0; c < n; ++c) {
+        d.final_xy[2 * c] = fx[q][c];
+        d.final_xy[2 * c + 1] = fy[q][c];
+      }
+      d.rstep = std::move(rs[q]);
+    }
+    s->st_events += 1;
+    s->st_inter += d.interactions;
+    out.push_back(std::move(d));
+    s->alloc.release(h.base);
+    h = HostSlot{};
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->dmu);
+    for (auto& d : out) s->done.push_back(std::move(d));
+  }
+  s->dcv.notify_all();
+  return SIM_OK;
+}
+
+// One scheduling round: admit, initialise, step one chunk, retire.
+// defer = true keeps finished results on the device (sim_execute).
+int pump(sim_t* s, bool defer, bool* progressed) {
+  *progressed = false;
+  if (s->broken) return SIM_ECUDA;
+  if (s->inject == SIM_ECUDA) {
+    s->broken = true;
+    s->err = "injected CUDA failure";
+    return SIM_ECUDA;
+  }
+  int rc = admit(s);
+  if (rc) return rc;
+  rc = launch_inits(s);
+  if (rc) return rc;
+  bool any = false;
+  for (auto& h : s->slots) any |= h.used && h.running;
+  if (!any) return SIM_OK;
+  rc = run_chunk(s);
+  if (rc) return rc;
+  *progressed = true;
+  const bool inject_numeric = s->inject == SIM_ENUMERIC;
+  if (inject_numeric) s->inject = 0;
+  std::vector<int> fin;
+  for (int k = 0; k < s->S; ++k) {
+    HostSlot& h = s->slots[k];
+    if (!h.used || !h.running) continue;
+    const SlotSummary& m = s->h_summary[k];
+    h.n_h = m.n_h;
+    h.n_e = m.n_e;
+    h.n_steps = m.n_steps;
+    h.interactions = (int64_t)m.interactions;
+    if (m.done || inject_numeric) {
+      h.running = false;
+      h.status = inject_numeric ? SIM_ENUMERIC : m.status;
+      fin.push_back(k);
+    }
+  }
+  if (inject_numeric) {
+    // the device still thinks these slots run: stop them there too
+    for (int k : fin) {
+      const int zero = 0;
+      CK(cudaMemcpyAsync(&s->d_slots[k].running, &zero, sizeof(int), cudaMemcpyHostToDevice,
+                         s->stream));
+      CK(cudaStreamSynchronize(s->stream));
+    }
+  }
+  if (fin.empty()) return SIM_OK;
+  for (size_t q = 0; q < fin.size(); ++q) s->h_list[q] = fin[q];
+  CK(cudaMemcpyAsync(s->d_list, s->h_list, fin.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                     s->stream));
+  CK(launch_bin(s->ph, s->A, s->d_slots, s->d_list, (int)fin.size(), s->d_pixels, s->d_readout,
+                s->stream));
+  s->st_launch += 1;
+  if (defer) {
+    CK(cudaStreamSynchronize(s->stream));
+    for (int k : fin) s->slots[k].finished_on_device = true;
+    return SIM_OK;
+  }
+  return fetch_results(s, fin);
+}
+
+void copy_out(const Done& d, sim_result_t* r, int grid_n) {
+  r->event_id = d.event_id;
+  r->status = d.status;
+  r->n_carriers = d.n_carriers;
+  r->n_steps = d.n_steps;
+  r->n_collected = d.n_collected;
+  r->n_outside = d.n_outside;
+  r->n_lost = d.n_lost;
+  r->interactions = d.interactions;
+  r->t_submit_ns = d.t_submit;
+  r->t_start_ns = d.t_start;
+  r->t_done_ns = d.t_done;
+  if (r->pixels) std::memcpy(r->pixels, d.pixels.data(), (size_t)grid_n * grid_n * sizeof(int32_t));
+  const int64_t n = std::min<int64_t>(r->capacity, d.n_carriers);
+  if (r->final_xy) {
+    for (int64_t c = 0; c < n; ++c) {
+      r->final_xy[2 * c] = d.final_xy.empty() ? NAN : d.final_xy[2 * c];
+      r->final_xy[2 * c + 1] = d.final_xy.empty() ? NAN : d.final_xy[2 * c + 1];
+    }
+  }
+  if (r->retire_step)
+    for (int64_t c = 0; c < n; ++c) r->retire_step[c] = d.rstep.empty() ? -2 : d.rstep[c];
+}
+
+void engine_main(sim_t* s) {
+  cudaSetDevice(s->device);
+  while (!s->stop.load()) {
+    bool progressed = false;
+    int rc;
+    {
+      std::lock_guard<std::mutex> lk(s->drive_mu);
+      rc = pump(s, false, &progressed);
+    }
+    if (rc) {
+      s->dcv.notify_all();
+      std::unique_lock<std::mutex> lk(s->qmu);
+      s->qcv.wait_for(lk, std::chrono::milliseconds(5));
+      continue;
+    }
+    if (!progressed) {
+      std::unique_lock<std::mutex> lk(s->qmu);
+      if (s->queue.empty() && !s->stop.load())
+        s->qcv.wait_for(lk, std::chrono::milliseconds(2));
+    }
+  }
+}
+
+template <typename T>
+int dalloc(sim_t* s, T** p, size_t count) {
+  CK(cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T)));
+  return SIM_OK;
+}
+template <typename T>
+int halloc(sim_t* s, T** p, size_t count) {
+  CK(cudaMallocHost((void**)p, std::max<size_t>(count, 1) * sizeof(T)));
+  std::memset((void*)*p, 0, std::max<size_t>(count, 1) * sizeof(T));
+  return SIM_OK;
+}
+
+int check_device(int device, int* sms) {
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n <= device || device < 0) return SIM_ENODEV;
+  cudaDeviceProp p;
+  if (cudaGetDeviceProperties(&p, device) != cudaSuccess) return SIM_ENODEV;
+  if (p.major != 10 || p.minor != 3) return SIM_ENODEV;  // built for sm_103a only
+  *sms = p.multiProcessorCount;
+  return SIM_OK;
+}
+
+int alloc_all(sim_t* s) {
+  const int64_t C = s->capacity;
+  int rc = 0;
+#define AL(p, n) \
+  if ((rc = dalloc(s, &(p), (size_t)(n))) != 0) return rc
+#define HL(p, n) \
+  if ((rc = halloc(s, &(p), (size_t)(n))) != 0) return rc
+  AL(s->A.px, C);
+  AL(s->A.py, C);
+  AL(s->A.pz, C);
+  AL(s->A.sh[0], C);
+  AL(s->A.sh[1], C);
+  AL(s->A.cid, C);
+  AL(s->A.fx, C);
+  AL(s->A.fy, C);
+  AL(s->A.rstep, C);
+  AL(s->A.cstate, C);
+  s->A.capacity = C;
+  AL(s->d_slots, s->S);
+  AL(s->d_summary, s->S);
+  AL(s->d_readout, s->S);
+  AL(s->d_pixels, (int64_t)s->S * s->sensor.grid_n * s->sensor.grid_n);
+  AL(s->d_units, kMaxUnits);
+  AL(s->d_n_units, 1);
+  AL(s->d_unit_counter, kMaxK);
+  AL(s->d_ret, (int64_t)kMaxK * s->S * 2);
+  AL(s->d_partial, s->partial_cap);
+  AL(s->d_combine, kMaxUnits);
+  AL(s->d_err, 1);
+  AL(s->d_explicit, C);
+  AL(s->d_list, s->S);
+  if (s->opt.mode == CTS_MODE_PLAIN) AL(s->d_field, 3 * C);
+  HL(s->h_summary, s->S);
+  HL(s->h_units, kMaxUnits);
+  HL(s->h_n_units, 1);
+  HL(s->h_list, s->S);
+  HL(s->h_slotdev, s->S);
+  HL(s->h_readout, s->S);
+  HL(s->h_pixels, (int64_t)s->S * s->sensor.grid_n * s->sensor.grid_n);
+  HL(s->h_err, 1);
+#undef AL
+#undef HL
+  CK(cudaMemset(s->d_slots, 0, s->S * sizeof(SlotDev)));
+  CK(cudaMemset(s->d_combine, 0, kMaxUnits * sizeof(int32_t)));
+  CK(cudaMemset(s->d_err, 0, sizeof(int32_t)));
+  CK(cudaEventCreate(&s->ev0));
+  CK(cudaEventCreate(&s->ev1));
+  return SIM_OK;
+}
+
+void free_all(sim_t* s) {
+  if (s->graph) cudaGraphExecDestroy(s->graph);
+  void* dev[] = {s->A.px, s->A.py, s->A.pz, s->A.sh[0], s->A.sh[1], s->A.cid, s->A.fx, s->A.fy,
+                 s->A.rstep, s->A.cstate, s->d_slots, s->d_summary, s->d_readout, s->d_pixels,
+                 s->d_units, s->d_n_units, s->d_unit_counter, s->d_ret, s->d_partial,
+                 s->d_combine, s->d_err, s->d_field, s->d_explicit, s->d_list};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  void* host[] = {s->h_summary, s->h_units, s->h_n_units, s->h_list, s->h_slotdev, s->h_readout,
+                  s->h_pixels, s->h_err};
+  for (void* p : host)
+    if (p) cudaFreeHost(p);
+  if (s->ev0) cudaEventDestroy(s->ev0);
+  if (s->ev1) cudaEventDestroy(s->ev1);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+}
+
+// Pick the pair-kernel variant: explicit option, else the one whose tile
+// keeps the most SMs busy for typical event sizes (nt128_r4).
+int choose_variant(sim_t* s) {
+  if (s->opt.variant >= 1 && s->opt.variant <= variant_count()) return s->opt.variant - 1;
+  return 0;
+}
+
+int set_variant(sim_t* s, int v) {
+  int occ = 0;
+  CK(variant_occupancy(v, &occ));
+  if (occ < 1) occ = 1;
+  s->variant = v;
+  s->grid = s->sm_count * occ;
+  const Variant vi = variant_info(v);
+  s->tile_i = vi.nt * vi.r;
+  return SIM_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+const char* sim_strerror(int code) {
+  switch (code) {
+    case SIM_OK: return "ok";
+    case SIM_EINVAL: return "invalid argument";
+    case SIM_ENOMEM_BUDGET: return "event larger than the device budget";
+    case SIM_EAGAIN: return "admission queue full";
+    case SIM_ETIMEOUT: return "timed out";
+    case SIM_ECUDA: return "CUDA error";
+    case SIM_EMAXSTEPS: return "step cap reached with holes still moving";
+    case SIM_ENUMERIC: return "non-finite field or position";
+    case SIM_ESTATE: return "call not valid in this mode or state";
+    case SIM_ENODEV: return "no sm_103 CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mobility_t* mobility,
+             const sim_options_t* options, sim_t** out) {
+  if (!out) return SIM_EINVAL;
+  *out = nullptr;
+  int rc = validate_params(sensor, field, mobility);
+  if (rc) return rc;
+  sim_options_t opt{};
+  if (options) opt = *options;
+  else opt.mode = CTS_MODE_BATCHED;
+  if (opt.mode < CTS_MODE_PLAIN || opt.mode > CTS_MODE_SERVE) return SIM_EINVAL;
+  if (opt.max_slots < 0 || opt.chunk_steps < 0 || opt.chunk_steps > kMaxK ||
+      opt.max_carriers < 0 || opt.hbm_budget_bytes < 0 || opt.queue_capacity < 0 ||
+      opt.variant < 0 || opt.variant > variant_count())
+    return SIM_EINVAL;
+  int sms = 0;
+  rc = check_device(opt.device, &sms);
+  if (rc) return rc;
+  if (cudaSetDevice(opt.device) != cudaSuccess) return SIM_ENODEV;
+
+  sim_t* s = new sim_t();
+  s->sensor = *sensor;
+  if (!(s->sensor.softening_um > 0)) s->sensor.softening_um = 1e-6;
+  s->field = *field;
+  s->mob = *mobility;
+  s->opt = opt;
+  s->device = opt.device;
+  s->sm_count = sms;
+  s->ph = make_phys(s->sensor, s->field, s->mob);
+  s->S = opt.mode == CTS_MODE_PLAIN ? 1 : (opt.max_slots > 0 ? opt.max_slots : kDefaultSlots);
+  s->K = opt.chunk_steps > 0 ? opt.chunk_steps : kDefaultK;
+  if (s->opt.queue_capacity == 0) s->opt.queue_capacity = kDefaultQueue;
+  const int64_t budget = opt.hbm_budget_bytes > 0 ? opt.hbm_budget_bytes : kDefaultBudget;
+  s->capacity = opt.max_carriers > 0 ? opt.max_carriers : std::max<int64_t>(budget / kBytesPerCarrier, 1024);
+  if (s->capacity > (1ll << 28)) s->capacity = 1ll << 28;
+  s->partial_cap = std::min<int64_t>(3 * 4 * (s->capacity + 4096), 64ll << 20);
+  s->slots.resize(s->S);
+  s->alloc = ArenaAllocator(s->capacity);
+  if (opt.stream) {
+    s->stream = (cudaStream_t)opt.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return SIM_ECUDA;
+    }
+    s->own_stream = true;
+  }
+  rc = alloc_all(s);
+  if (!rc) rc = set_variant(s, choose_variant(s));
+  if (rc) {
+    free_all(s);
+    delete s;
+    return rc;
+  }
+  if (opt.mode == CTS_MODE_SERVE) s->engine = std::thread(engine_main, s);
+  *out = s;
+  return SIM_OK;
+}
+
+int sim_destroy(sim_t* s) {
+  if (!s) return SIM_EINVAL;
+  if (s->engine.joinable()) {
+    s->stop.store(true);
+    s->qcv.notify_all();
+    s->engine.join();
+  }
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  free_all(s);
+  delete s;
+  return SIM_OK;
+}
+
+int sim_submit(sim_t* s, const sim_event_t* ev, int n_ev, int* n_accepted) {
+  if (n_accepted) *n_accepted = 0;
+  if (!s || (!ev && n_ev > 0) || n_ev < 0) return SIM_EINVAL;
+  if (s->broken) return SIM_ECUDA;
+  int acc = 0;
+  int rc = SIM_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->qmu);
+    for (int k = 0; k < n_ev; ++k) {
+      if ((int)s->queue.size() >= s->opt.queue_capacity) {
+        rc = SIM_EAGAIN;
+        break;
+      }
+      EventRec r;
+      rc = prepare_event(s, &ev[k], &r);
+      if (rc) break;
+      r.t_submit = now_ns();
+      r.order = s->order_counter++;
+      s->queue.push_back(std::move(r));
+      ++acc;
+    }
+    if (rc) s->st_rejected += n_ev - acc;
+  }
+  s->qcv.notify_all();
+  if (n_accepted) *n_accepted = acc;
+  return rc;
+}
+
+int sim_poll(sim_t* s, sim_result_t* out, int max_out, int* n_out, int timeout_ms) {
+  if (n_out) *n_out = 0;
+  if (!s || max_out < 0 || (max_out > 0 && !out)) return SIM_EINVAL;
+  if (s->inject == SIM_ETIMEOUT) {
+    s->inject = 0;
+    return SIM_ETIMEOUT;
+  }
+  const double deadline = now_ns() + (timeout_ms < 0 ? 1e30 : timeout_ms * 1e6);
+  cudaSetDevice(s->device);
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> lk(s->dmu);
+      if (!s->done.empty() && max_out > 0) {
+        int n = 0;
+        while (n < max_out && !s->done.empty()) {
+          copy_out(s->done.front(), &out[n], s->sensor.grid_n);
+          s->done.pop_front();
+          ++n;
+        }
+        if (n_out) *n_out = n;
+        return SIM_OK;
+      }
+    }
+    if (s->broken) return SIM_ECUDA;
+    if (s->opt.mode == CTS_MODE_SERVE) {
+      std::unique_lock<std::mutex> lk(s->dmu);
+      if (s->done.empty()) {
+        const double left_ms = (deadline - now_ns()) * 1e-6;
+        if (left_ms <= 0) return SIM_ETIMEOUT;
+        s->dcv.wait_for(lk, std::chrono::microseconds((int64_t)std::min(left_ms, 50.0) * 1000 + 1));
+      }
+      continue;
+    }
+    bool progressed = false;
+    int rc;
+    {
+      std::lock_guard<std::mutex> lk(s->drive_mu);
+      rc = pump(s, false, &progressed);
+    }
+    if (rc) return rc;
+    if (!progressed) {
+      std::lock_guard<std::mutex> lk(s->dmu);
+      if (s->done.empty()) {
+        bool queued;
+        {
+          std::lock_guard<std::mutex> q(s->qmu);
+          queued = !s->queue.empty();
+        }
+        if (!queued || now_ns() > deadline) return SIM_ETIMEOUT;
+      }
+    }
+    if (now_ns() > deadline) {
+      std::lock_guard<std::mutex> lk(s->dmu);
+      if (s->done.empty()) return SIM_ETIMEOUT;
+    }
+  }
+}
+
+int sim_run(sim_t* s, const sim_event_t* ev, int n, sim_result_t* out) {
+  if (!s || n < 0 || (n > 0 && (!ev || !out))) return SIM_EINVAL;
+  int64_t first_order;
+  {
+    std::lock_guard<std::mutex> dl(s->drive_mu);
+    for (auto& h : s->slots)
+      if (h.used) return SIM_ESTATE;
+    std::lock_guard<std::mutex> lk(s->qmu);
+    std::lock_guard<std::mutex> dk(s->dmu);
+    if (!s->queue.empty() || !s->done.empty()) return SIM_ESTATE;
+    first_order = s->order_counter;
+  }
+  int submitted = 0;
+  int got = 0;
+  std::vector<char> have((size_t)n, 0);
+  while (got < n) {
+    if (submitted < n) {
+      int acc = 0;
+      const int rc = sim_submit(s, ev + submitted, n - submitted, &acc);
+      submitted += acc;
+      if (rc && rc != SIM_EAGAIN) return rc;
+    }
+    Done d;
+    bool have_done = false;
+    {
+      std::lock_guard<std::mutex> lk(s->dmu);
+      if (!s->done.empty()) {
+        d = std::move(s->done.front());
+        s->done.pop_front();
+        have_done = true;
+      }
+    }
+    if (have_done) {
+      const int64_t idx = d.order - first_order;
+      if (idx >= 0 && idx < n && !have[idx]) {
+        copy_out(d, &out[idx], s->sensor.grid_n);
+        have[idx] = 1;
+        ++got;
+      }
+      continue;
+    }
+    if (s->opt.mode == CTS_MODE_SERVE) {
+      std::unique_lock<std::mutex> lk(s->dmu);
+      if (s->done.empty()) s->dcv.wait_for(lk, std::chrono::milliseconds(5));
+      if (s->broken) return SIM_ECUDA;
+      continue;
+    }
+    bool progressed = false;
+    int rc;
+    {
+      std::lock_guard<std::mutex> lk(s->drive_mu);
+      rc = pump(s, false, &progressed);
+    }
+    if (rc) return rc;
+    if (!progressed) {
+      std::lock_guard<std::mutex> lk(s->dmu);
+      std::lock_guard<std::mutex> q(s->qmu);
+      if (s->done.empty() && s->queue.empty() && submitted >= n) return SIM_ESTATE;
+    }
+  }
+  return SIM_OK;
+}
+
+int sim_stage(sim_t* s, const sim_event_t* ev, int n) {
+  if (!s || n < 0 || (n > 0 && !ev)) return SIM_EINVAL;
+  if (s->opt.mode != CTS_MODE_BATCHED) return SIM_ESTATE;
+  if (s->broken) return SIM_ECUDA;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  for (auto& h : s->slots)
+    if (h.used) return SIM_ESTATE;
+  if (n > s->S) return SIM_ENOMEM_BUDGET;
+  std::vector<EventRec> recs((size_t)n);
+  int64_t need = 0;
+  for (int k = 0; k < n; ++k) {
+    const int rc = prepare_event(s, &ev[k], &recs[k]);
+    if (rc) return rc;
+    recs[k].t_submit = now_ns();
+    recs[k].order = k;
+    need += std::max<int64_t>((int64_t)recs[k].cap_h + recs[k].cap_e, 1);
+  }
+  if (need > s->capacity) return SIM_ENOMEM_BUDGET;
+  s->staged.clear();
+  for (int k = 0; k < n; ++k) {
+    const int64_t base = s->alloc.alloc(std::max<int64_t>((int64_t)recs[k].cap_h + recs[k].cap_e, 1));
+    if (base < 0) return SIM_ENOMEM_BUDGET;
+    const int rc = place_event(s, k, std::move(recs[k]), base);
+    if (rc) return rc;
+    s->staged.push_back(k);
+  }
+  CK(cudaStreamSynchronize(s->stream));
+  return SIM_OK;
+}
+
+int sim_execute(sim_t* s) {
+  if (!s) return SIM_EINVAL;
+  if (s->opt.mode != CTS_MODE_BATCHED) return SIM_ESTATE;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  for (;;) {
+    bool any = false;
+    for (auto& h : s->slots) any |= h.used && (h.running || h.needs_init);
+    if (!any) break;
+    bool progressed = false;
+    // staged events only: nothing is admitted from the queue meanwhile
+    std::deque<EventRec> parked;
+    {
+      std::lock_guard<std::mutex> lk(s->qmu);
+      parked.swap(s->queue);
+    }
+    const int rc = pump(s, true, &progressed);
+    {
+      std::lock_guard<std::mutex> lk(s->qmu);
+      for (auto it = parked.rbegin(); it != parked.rend(); ++it) s->queue.push_front(std::move(*it));
+    }
+    if (rc) return rc;
+  }
+  return SIM_OK;
+}
+
+int sim_collect(sim_t* s, sim_result_t* out, int max_out, int* n_out) {
+  if (n_out) *n_out = 0;
+  if (!s || max_out < 0 || (max_out > 0 && !out)) return SIM_EINVAL;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  std::vector<int> fin;
+  for (int k : s->staged)
+    if (s->slots[k].used && s->slots[k].finished_on_device) fin.push_back(k);
+  const int rc = fetch_results(s, fin);
+  if (rc) return rc;
+  s->staged.clear();
+  std::vector<Done> all;
+  {
+    std::lock_guard<std::mutex> lk(s->dmu);
+    while (!s->done.empty()) {
+      all.push_back(std::move(s->done.front()));
+      s->done.pop_front();
+    }
+  }
+  std::sort(all.begin(), all.end(), [](const Done& a, const Done& b) { return a.order < b.order; });
+  int n = 0;
+  for (auto& d : all) {
+    if (n < max_out) copy_out(d, &out[n], s->sensor.grid_n);
+    ++n;
+  }
+  if (n_out) *n_out = std::min(n, max_out);
+  return SIM_OK;
+}
+
+int sim_get_stats(sim_t* s, sim_stats_t* o) {
+  if (!s || !o) return SIM_EINVAL;
+  *o = sim_stats_t{};
+  o->events_done = s->st_events;
+  o->interactions = s->st_inter;
+  o->steps_launched = s->st_steps;
+  o->kernel_launches = s->st_launch;
+  o->chunks = s->st_chunks;
+  {
+    std::lock_guard<std::mutex> lk(s->qmu);
+    o->queue_depth = (int64_t)s->queue.size();
+  }
+  o->rejected = s->st_rejected;
+  o->sm_count = s->sm_count;
+  o->variant = s->variant;
+  o->device_ms = s->st_ms;
+  return SIM_OK;
+}
+
+int sim_debug_inject(sim_t* s, int fault) {
+  if (!s) return SIM_EINVAL;
+  if (fault != 0 && fault != SIM_ENUMERIC && fault != SIM_ETIMEOUT && fault != SIM_ECUDA)
+    return SIM_EINVAL;
+  s->inject = fault;
+  return SIM_OK;
+}
+
+// ---- kernel-level entry points --------------------------------------------
+
+int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, int32_t n_h,
+                    int32_t n_e, double* out_E) {
+  if (!s || n_h < 0 || n_e < 0 || (n_h + n_e > 0 && (!x || !y || !z || !out_E)))
+    return SIM_EINVAL;
+  if (n_e > 0 && s->sensor.species != CTS_BOTH) return SIM_EINVAL;
+  const int n = n_h + n_e;
+  if (n == 0) return SIM_OK;
+  if (n_h == 0) return SIM_EINVAL;  // the planner skips events without holes
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  cudaSetDevice(s->device);
+  // a private arena and slot: the handle's resident events are untouched
+  sim_t* t = s;
+  Arena A{};
+  SlotDev* d_slot = nullptr;
+  float* d_field = nullptr;
+  std::vector<float4> sh((size_t)n);
+  for (int c = 0; c < n; ++c) sh[c] = make_float4(x[c], y[c], z[c], 0.0f);
+  std::vector<UnitPlan> plan;
+  int64_t pfl = 0;
+  const int32_t nh = n_h, ne = n_e;
+  if (plan_units(&nh, &ne, 1, t->tile_i, t->grid, t->ph.repulsion != 0, kMaxUnits,
+                 t->partial_cap, &plan, &pfl) != 0)
+    return SIM_EINVAL;
+  int rc = SIM_OK;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = cudaMalloc(&A.sh[0], n * sizeof(float4))) != cudaSuccess) break;
+    A.sh[1] = A.sh[0];
+    A.capacity = n;
+    if ((e = cudaMalloc(&d_slot, sizeof(SlotDev))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&d_field, 3 * (size_t)n * sizeof(float))) != cudaSuccess) break;
+    SlotDev sd{};
+    sd.base = 0;
+    sd.cap_h = n_h;
+    sd.cap_e = n_e;
+    sd.n_h = n_h;
+    sd.n_e = n_e;
+    sd.act_h = n_h;
+    sd.act_e = n_e;
+    sd.n_total = n;
+    sd.running = 1;
+    if ((e = cudaMemcpyAsync(A.sh[0], sh.data(), n * sizeof(float4), cudaMemcpyHostToDevice,
+                             s->stream)) != cudaSuccess)
+      break;
+    if ((e = cudaMemcpyAsync(d_slot, &sd, sizeof(SlotDev), cudaMemcpyHostToDevice, s->stream)) !=
+        cudaSuccess)
+      break;
+    std::memcpy(s->h_units, plan.data(), plan.size() * sizeof(Unit));
+    *s->h_n_units = (int32_t)plan.size();
+    if ((e = cudaMemcpyAsync(s->d_units, s->h_units, plan.size() * sizeof(Unit),
+                             cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+      break;
+    if ((e = cudaMemcpyAsync(s->d_n_units, s->h_n_units, sizeof(int32_t), cudaMemcpyHostToDevice,
+                             s->stream)) != cudaSuccess)
+      break;
+    if ((e = cudaMemsetAsync(s->d_unit_counter, 0, sizeof(int32_t), s->stream)) != cudaSuccess)
+      break;
+    if ((e = cudaMemsetAsync(s->d_ret, 0, 2 * sizeof(int32_t), s->stream)) != cudaSuccess) break;
+    StepArgs a = step_args(s, false);
+    a.A = A;
+    a.slots = d_slot;
+    a.field_out = d_field;
+    a.S = 1;
+    if ((e = launch_step(s->variant, a, 0, s->grid, s->stream)) != cudaSuccess) break;
+    std::vector<float> f(3 * (size_t)n);
+    if ((e = cudaMemcpyAsync(f.data(), d_field, 3 * (size_t)n * sizeof(float),
+                             cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess)
+      break;
+    if ((e = cudaStreamSynchronize(s->stream)) != cudaSuccess) break;
+    for (int c = 0; c < n; ++c) {
+      out_E[3 * c] = f[c];
+      out_E[3 * c + 1] = f[(size_t)n + c];
+      out_E[3 * c + 2] = f[2 * (size_t)n + c];
+    }
+  } while (0);
+  if (e != cudaSuccess) {
+    s->err = cudaGetErrorString(e);
+    rc = SIM_ECUDA;
+  }
+  if (A.sh[0]) cudaFree(A.sh[0]);
+  if (d_slot) cudaFree(d_slot);
+  if (d_field) cudaFree(d_field);
+  return rc;
+}
+
+int sim_debug_bin(sim_t* s, const double* x, const double* y, int64_t n, int32_t* pixels,
+                  int64_t* outside) {
+  if (!s || n < 0 || !pixels || !outside || (n > 0 && (!x || !y))) return SIM_EINVAL;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  cudaSetDevice(s->device);
+  const int npix = s->sensor.grid_n * s->sensor.grid_n;
+  double *dx = nullptr, *dy = nullptr;
+  int32_t* dp = nullptr;
+  long long* dout = nullptr;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = cudaMalloc(&dx, std::max<int64_t>(n, 1) * sizeof(double))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&dy, std::max<int64_t>(n, 1) * sizeof(double))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&dp, npix * sizeof(int32_t))) != cudaSuccess) break;
+    if ((e = cudaMalloc(&dout, sizeof(long long))) != cudaSuccess) break;
+    if (n > 0) {
+      if ((e = cudaMemcpyAsync(dx, x, n * sizeof(double), cudaMemcpyHostToDevice, s->stream))) break;
+      if ((e = cudaMemcpyAsync(dy, y, n * sizeof(double), cudaMemcpyHostToDevice, s->stream))) break;
+    }
+    if ((e = cudaMemsetAsync(dp, 0, npix * sizeof(int32_t), s->stream))) break;
+    if ((e = cudaMemsetAsync(dout, 0, sizeof(long long), s->stream))) break;
+    if ((e = launch_bin_points(s->ph, dx, dy, n, dp, dout, s->stream))) break;
+    long long o = 0;
+    if ((e = cudaMemcpyAsync(pixels, dp, npix * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream))) break;
+    if ((e = cudaMemcpyAsync(&o, dout, sizeof(long long), cudaMemcpyDeviceToHost, s->stream))) break;
+    if ((e = cudaStreamSynchronize(s->stream))) break;
+    *outside = o;
+  } while (0);
+  if (dx) cudaFree(dx);
+  if (dy) cudaFree(dy);
+  if (dp) cudaFree(dp);
+  if (dout) cudaFree(dout);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
+int sim_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                     uint32_t* curand_out) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return SIM_EINVAL;
+  int sms = 0;
+  if (check_device(0, &sms)) return SIM_ENODEV;
+  cudaSetDevice(0);
+  uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr, *dcur = nullptr;
+  cudaError_t e = cudaSuccess;
+  const size_t m = (size_t)std::max<int64_t>(n, 1);
+  do {
+    if ((e = cudaMalloc(&dc, 4 * m * sizeof(uint32_t)))) break;
+    if ((e = cudaMalloc(&dk, 2 * m * sizeof(uint32_t)))) break;
+    if ((e = cudaMalloc(&dout, 4 * m * sizeof(uint32_t)))) break;
+    if (curand_out && (e = cudaMalloc(&dcur, 4 * m * sizeof(uint32_t)))) break;
+    if (n > 0) {
+      if ((e = cudaMemcpy(dc, ctr, 4 * n * sizeof(uint32_t), cudaMemcpyHostToDevice))) break;
+      if ((e = cudaMemcpy(dk, key, 2 * n * sizeof(uint32_t), cudaMemcpyHostToDevice))) break;
+    }
+    if ((e = launch_philox(dc, dk, n, dout, dcur, 0))) break;
+    if ((e = cudaDeviceSynchronize())) break;
+    if (n > 0) {
+      if ((e = cudaMemcpy(out, dout, 4 * n * sizeof(uint32_t), cudaMemcpyDeviceToHost))) break;
+      if (curand_out &&
+          (e = cudaMemcpy(curand_out, dcur, 4 * n * sizeof(uint32_t), cudaMemcpyDeviceToHost)))
+        break;
+    }
+  } while (0);
+  cudaFree(dc);
+  cudaFree(dk);
+  cudaFree(dout);
+  if (dcur) cudaFree(dcur);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
+int sim_debug_normals(const uint64_t* in, int64_t n, double* out) {
+  if (n < 0 || (n > 0 && (!in || !out))) return SIM_EINVAL;
+  int sms = 0;
+  if (check_device(0, &sms)) return SIM_ENODEV;
+  cudaSetDevice(0);
+  unsigned long long* din = nullptr;
+  double* dout = nullptr;
+  cudaError_t e = cudaSuccess;
+  const size_t m = (size_t)std::max<int64_t>(n, 1);
+  do {
+    if ((e = cudaMalloc(&din, 5 * m * sizeof(unsigned long long)))) break;
+    if ((e = cudaMalloc(&dout, 3 * m * sizeof(double)))) break;
+    if (n > 0 && (e = cudaMemcpy(din, in, 5 * n * sizeof(uint64_t), cudaMemcpyHostToDevice))) break;
+    if ((e = launch_normals(din, n, dout, 0))) break;
+    if ((e = cudaDeviceSynchronize())) break;
+    if (n > 0 && (e = cudaMemcpy(out, dout, 3 * n * sizeof(double), cudaMemcpyDeviceToHost))) break;
+  } while (0);
+  cudaFree(din);
+  cudaFree(dout);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
+int sim_debug_trajectory(sim_t* s, const sim_event_t* ev, int64_t n_steps, double* pos_out,
+                         int8_t* state_out, int64_t capacity, int64_t* steps_done) {
+  if (!s || !ev || n_steps < 0 || !pos_out || !state_out || !steps_done) return SIM_EINVAL;
+  if (s->opt.mode != CTS_MODE_BATCHED) return SIM_ESTATE;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  for (auto& h : s->slots)
+    if (h.used) return SIM_ESTATE;
+  {
+    std::lock_guard<std::mutex> lk(s->qmu);
+    if (!s->queue.empty()) return SIM_ESTATE;
+  }
+  cudaSetDevice(s->device);
+  EventRec r;
+  int rc = prepare_event(s, ev, &r);
+  if (rc) return rc;
+  const int n = r.cap_h + r.cap_e;
+  if (capacity < n) return SIM_EINVAL;
+  const int64_t base = s->alloc.alloc(std::max(n, 1));
+  if (base < 0) return SIM_ENOMEM_BUDGET;
+  const Phys saved = s->ph;
+  s->ph.max_steps = std::min<int64_t>(s->ph.max_steps, n_steps);
+  const int savedK = s->K;
+  const int saved_graphs = s->opt.disable_graphs;
+  s->opt.disable_graphs = 1;
+  s->K = (int)std::min<int64_t>(std::max<int64_t>(n_steps, 1), savedK);
+  rc = place_event(s, 0, std::move(r), base);
+  while (!rc) {
+    bool any = s->slots[0].used && (s->slots[0].running || s->slots[0].needs_init);
+    if (!any) break;
+    rc = launch_inits(s);
+    if (rc) break;
+    if (!s->slots[0].running) break;
+    rc = run_chunk(s);
+    if (rc) break;
+    const SlotSummary& m = s->h_summary[0];
+    s->slots[0].n_h = m.n_h;
+    s->slots[0].n_e = m.n_e;
+    s->slots[0].n_steps = m.n_steps;
+    if (m.done) s->slots[0].running = false;
+  }
+  if (!rc) {
+    std::vector<double> px(n), py(n), pz(n), fx(n), fy(n);
+    std::vector<int32_t> cid(n);
+    std::vector<int8_t> cs(n);
+    const int nh = s->slots[0].n_h, ne = s->slots[0].n_e;
+    do {
+      if (n == 0) break;
+      cudaError_t e = cudaSuccess;
+      if ((e = cudaMemcpy(px.data(), s->A.px + base, n * sizeof(double), cudaMemcpyDeviceToHost)) ||
+          (e = cudaMemcpy(py.data(), s->A.py + base, n * sizeof(double), cudaMemcpyDeviceToHost)) ||
+          (e = cudaMemcpy(pz.data(), s->A.pz + base, n * sizeof(double), cudaMemcpyDeviceToHost)) ||
+          (e = cudaMemcpy(fx.data(), s->A.fx + base, n * sizeof(double), cudaMemcpyDeviceToHost)) ||
+          (e = cudaMemcpy(fy.data(), s->A.fy + base, n * sizeof(double), cudaMemcpyDeviceToHost)) ||
+          (e = cudaMemcpy(cid.data(), s->A.cid + base, n * sizeof(int32_t), cudaMemcpyDeviceToHost)) ||
+          (e = cudaMemcpy(cs.data(), s->A.cstate + base, n, cudaMemcpyDeviceToHost))) {
+        s->err = cudaGetErrorString(e);
+        rc = SIM_ECUDA;
+        break;
+      }
+      for (int c = 0; c < n; ++c) {
+        pos_out[3 * c] = pos_out[3 * c + 1] = pos_out[3 * c + 2] = NAN;
+        state_out[c] = (int8_t)(cs[c] & kStateMask);
+        if ((cs[c] & kStateMask) == kStateCollected) {
+          pos_out[3 * c] = fx[c];
+          pos_out[3 * c + 1] = fy[c];
+        }
+      }
+      // active carriers are the compacted prefixes of the two species ranges
+      const int hole_len = s->slots[0].running ? nh : nh;
+      for (int q = 0; q < hole_len + ne; ++q) {
+        const int64_t idx = q < hole_len ? q : s->slots[0].rec.cap_h + (q - hole_len);
+        const int id = cid[idx];
+        if (id < 0 || id >= n) continue;
+        if ((cs[id] & kStateMask) != kStateActive) continue;
+        pos_out[3 * id] = px[idx];
+        pos_out[3 * id + 1] = py[idx];
+        pos_out[3 * id + 2] = pz[idx];
+      }
+    } while (0);
+    *steps_done = s->slots[0].n_steps;
+  }
+  s->ph = saved;
+  s->K = savedK;
+  s->opt.disable_graphs = saved_graphs;
+  s->alloc.release(base);
+  s->slots[0] = HostSlot{};
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,362 @@
+"""GPU parity: the sm_103a kernels, called through the C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (derivations in the design notes):
+  * Philox words, pixel indices, binning counts: bit-exact.
+  * Diffusion normals: FP32 Box-Muller vs FP64 oracle on identical uniforms,
+    |dn| <= 4e-6 (a few FP32 ulps of log/sqrt/cospi at |n| <= 5.8).
+  * Pair field on identical FP32 positions (single-step force error of the
+    method, <= 1e-5): aggregate ||dE|| / ||E|| <= 1e-5 and per carrier
+    |dE_i| <= 1e-5 * max(|E_i|, 1e-3 * S_i), S_i = sum_j |term_ij|.
+  * Whole events: per-pixel collected charge within 1e-3 of the event total.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_09712_gb300 as cts
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2506_09712_gb300 import build
+    build.build()
+    oracle.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def sim_for(name, field=None, mode=cts.CTS_MODE_BATCHED, sensor_over=None, **opt):
+    p = W.preset(name)
+    sensor = dict(p["sensor"], **(sensor_over or {}))
+    return cts.Simulator(sensor, p["mobility"], field, mode=mode, **opt)
+
+
+def oracle_params(name, field=None, sensor_over=None, eps=0.0):
+    p = W.preset(name)
+    sensor = dict(p["sensor"], **(sensor_over or {}))
+    sensor["oracle_softening_um"] = eps
+    return oracle.make_params(sensor, field or W.field_switches(), p["mobility"])
+
+
+# ---------------------------------------------------------------------------
+# Random numbers
+# ---------------------------------------------------------------------------
+def test_philox_device_matches_oracle_and_curand():
+    rng = np.random.default_rng(1)
+    n = 4096
+    ctr = rng.integers(0, 1 << 32, size=(n, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:, 1] &= (1 << 29) - 1           # keep curand's 64-bit offset in range
+    ctr[0] = 0
+    key = rng.integers(0, 1 << 32, size=(n, 2), dtype=np.uint64).astype(np.uint32)
+    dev, cur = cts.sim_debug_philox(ctr, key, with_curand=True)
+    assert np.array_equal(dev, cur)
+    for k in range(0, n, 7):
+        assert list(dev[k]) == oracle.philox4x32_10(ctr[k], key[k])
+
+
+def test_diffusion_normals_device_vs_oracle():
+    rng = np.random.default_rng(2)
+    n = 20000
+    t = np.stack([np.full(n, 20250611), rng.integers(0, 1 << 40, n), rng.integers(0, 2, n),
+                  rng.integers(0, 60000, n), rng.integers(0, 5000, n)], axis=1).astype(np.uint64)
+    dev = cts.sim_debug_normals(t)
+    ref = np.array([oracle.normals3(*map(int, row)) for row in t[:4000]])
+    assert np.max(np.abs(dev[:4000] - ref)) <= 4e-6
+    assert abs(dev.mean()) < 0.02 and abs(dev.std() - 1) < 0.02
+
+
+# ---------------------------------------------------------------------------
+# Pair field (Eq. 4) on identical FP32 positions
+# ---------------------------------------------------------------------------
+def _abs_sum(xyz, sign, rows, eps=1e-6):
+    """S_i = sum_j k |r_ij| / (r_ij^2 + eps^2)^1.5, the scale of the sum's rounding."""
+    kc = oracle.coulomb_k(11.7)
+    out = np.zeros(len(rows))
+    x = xyz.astype(np.float64)
+    for q, i in enumerate(rows):
+        d = x[i] - x
+        r2 = (d * d).sum(axis=1) + eps * eps
+        t = np.sqrt(r2 - eps * eps) / r2 ** 1.5
+        t[i] = 0.0
+        out[q] = kc * t.sum()
+    return out
+
+
+def _field_check(sim, xyz32, n_h, n_e=0, rows=None, tol=FIELD_TOL):
+    E = sim.field(xyz32, n_h, n_e)
+    sign = np.concatenate([np.ones(n_h, np.int8), -np.ones(n_e, np.int8)])
+    rows = np.arange(n_h + n_e) if rows is None else np.asarray(rows)
+    ref = oracle.field(xyz32.astype(np.float64), sign=sign, eps=1e-6, rows=rows)
+    got = E[rows]
+    S = _abs_sum(xyz32, sign, rows)
+    err = np.linalg.norm(got - ref, axis=1)
+    mag = np.linalg.norm(ref, axis=1)
+    per = err / np.maximum(mag, 1e-3 * S)
+    agg = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert np.all(np.isfinite(got))
+    assert agg <= tol, agg
+    assert per.max() <= tol, (per.max(), int(np.argmax(per)))
+    return agg, per.max()
+
+
+@pytest.fixture(scope="module")
+def sim2():
+    s = sim_for("batch_20keV_320um")
+    yield s
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def sim_both():
+    s = sim_for("track_200keV_320um")
+    yield s
+    s.close()
+
+
+@pytest.mark.parametrize("n", [2, 3, 8, 31, 64])
+def test_field_tiny_brute_force(sim2, n):
+    xyz = W.random_cloud(n, 0.3, seed=n).astype(np.float32)
+    _field_check(sim2, xyz, n)
+
+
+@pytest.mark.parametrize("n", [511, 513, 1025, 2049])
+def test_field_ragged_tiles(sim2, n):
+    xyz = W.random_cloud(n, 1.0, seed=n).astype(np.float32)
+    _field_check(sim2, xyz, n)
+
+
+@pytest.mark.parametrize("n,sigma", [(829, 0.5), (5525, 0.83), (6906, 1.23)])
+def test_field_event_sizes(sim2, n, sigma):
+    # A single event: the planner splits the j range, exercising the combine.
+    xyz = W.random_cloud(n, sigma, seed=n).astype(np.float32)
+    _field_check(sim2, xyz, n)
+
+
+def test_field_expanded_cloud(sim2):
+    # late-time geometry: a 20 um wide, 5 um deep flattened cloud
+    rng = np.random.default_rng(9)
+    xyz = (rng.standard_normal((5525, 3)) * np.array([20.0, 20.0, 5.0])).astype(np.float32)
+    _field_check(sim2, xyz, 5525)
+
+
+def test_field_two_species(sim_both):
+    rng = np.random.default_rng(4)
+    h = rng.standard_normal((3000, 3)) * 2.0
+    e = rng.standard_normal((2500, 3)) * 2.0 + np.array([0.5, 0.0, 3.0])
+    xyz = np.concatenate([h, e]).astype(np.float32)
+    _field_check(sim_both, xyz, 3000, 2500)
+
+
+def test_field_max_size_sampled(sim_both):
+    # 2 x 55 250 carriers along a 150 um track (the largest event): the oracle
+    # computes 256 sampled rows one by one.
+    rng = np.random.default_rng(5)
+    n = 55_250
+    s = rng.random(n) * 150.0
+    d = np.array([0.3, 0.2, -0.93]); d /= np.linalg.norm(d)
+    pts = s[:, None] * d[None, :] + 0.5 * rng.standard_normal((n, 3))
+    pts -= pts.mean(axis=0)
+    xyz = np.concatenate([pts, pts + 1e-3 * rng.standard_normal((n, 3))]).astype(np.float32)
+    rows = rng.choice(2 * n, 256, replace=False)
+    _field_check(sim_both, xyz, n, n, rows=rows)
+
+
+def test_field_coincident_and_parked_sources(sim2):
+    # carriers on top of each other give finite fields (softening), never NaN
+    xyz = np.zeros((64, 3), np.float32)
+    xyz[32:] = [[0.1, 0.0, 0.0]]
+    E = sim2.field(xyz, 64)
+    assert np.all(np.isfinite(E))
+    ref = oracle.field(xyz.astype(np.float64), eps=1e-6)
+    assert np.allclose(E, ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max())
+
+
+# ---------------------------------------------------------------------------
+# Readout
+# ---------------------------------------------------------------------------
+def test_binning_bit_exact(sim2):
+    rng = np.random.default_rng(6)
+    n = 200_000
+    x = rng.normal(0, 60, n)
+    y = rng.normal(0, 60, n)
+    x[:2000] = np.round(x[:2000] / 12.5) * 12.5   # exactly on pixel edges
+    y[1000:3000] = np.round(y[1000:3000] / 12.5) * 12.5
+    x[5] = 1e300
+    x[6] = -1e300
+    pix, out = sim2.bin(x, y)
+    P = oracle_params("batch_20keV_320um")
+    rp, ro = oracle.bin_positions(P, x, y)
+    assert np.array_equal(pix, rp) and out == ro
+
+
+# ---------------------------------------------------------------------------
+# Trajectories and whole events
+# ---------------------------------------------------------------------------
+def _ev(name, k=0, **over):
+    e = W.make_events(name, n=k + 1)[k]
+    e.update(over)
+    return e
+
+
+@pytest.mark.parametrize("steps", [1, 10, 60])
+def test_trajectory_parity_3keV(steps):
+    name = "plain_3keV_100um"
+    ev = _ev(name, 3)
+    P = oracle_params(name, sensor_over=dict(max_steps=steps))
+    ref = oracle.run_event(P, ev)
+    with sim_for(name) as sim:
+        pos, st, done = sim.trajectory(dict(ev, n_carriers=829), steps)
+    assert done == ref.n_steps
+    assert np.array_equal(st, ref.state)
+    act = ref.state == oracle.ACTIVE
+    col = ref.state == oracle.COLLECTED
+    dpos = np.abs(pos[act] - ref.pos[act]).max() if act.any() else 0.0
+    dcol = np.abs(pos[col, :2] - ref.final_xy[col]).max() if col.any() else 0.0
+    # FP32 displacements around FP64 positions: ~1e-7 relative per step
+    assert dpos <= 2e-5 * steps ** 0.5 + 1e-6, dpos
+    assert dcol <= 2e-5 * steps ** 0.5 + 1e-6, dcol
+
+
+def _compare_events(gpu, ref, n_carriers):
+    assert gpu["status"] == ref.status == 0
+    assert gpu["n_collected"] == ref.n_collected
+    assert abs(gpu["n_steps"] - ref.n_steps) <= 1
+    tol = math.floor(1e-3 * n_carriers)
+    assert np.abs(gpu["pixels"] - ref.pixels).max() <= tol
+    assert gpu["pixels"].sum() + gpu["n_outside"] == ref.n_collected
+    assert gpu["interactions"] == pytest.approx(ref.interactions, rel=2e-3)
+
+
+def test_events_parity_3keV_all_eight():
+    name = "plain_3keV_100um"
+    evs = W.make_events(name)
+    P = oracle_params(name)
+    refs = oracle.run_events(P, evs)
+    with sim_for(name) as sim:
+        res = sim.run(evs)
+    for g, r in zip(res, refs):
+        _compare_events(g, r, 829)
+
+
+def test_events_parity_20keV_two_events():
+    name = "batch_20keV_320um"
+    evs = W.make_events(name, n=2)
+    P = oracle_params(name)
+    refs = oracle.run_events(P, evs)
+    with sim_for(name) as sim:
+        res = sim.run(evs)
+    for g, r in zip(res, refs):
+        _compare_events(g, r, 5525)
+
+
+def test_modes_and_mixes_agree():
+    # PLAIN (two launches per step), BATCHED with and without graphs, SERVE;
+    # an event alone and in a mix with others gives the same result.
+    name = "plain_3keV_100um"
+    evs = W.make_events(name, n=4)
+    outs = []
+    for mode, opts in [(cts.CTS_MODE_PLAIN, {}), (cts.CTS_MODE_BATCHED, {}),
+                       (cts.CTS_MODE_BATCHED, dict(disable_graphs=1)),
+                       (cts.CTS_MODE_SERVE, {})]:
+        with sim_for(name, mode=mode, **opts) as sim:
+            outs.append(sim.run(evs))
+    with sim_for(name) as sim:
+        alone = sim.run([evs[2]])[0]
+        mix = sim.run(W.make_events(name, n=8, first_id=100)[:5] + [evs[2]])[-1]
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert abs(a["n_steps"] - b["n_steps"]) <= 1
+            assert np.abs(a["pixels"] - b["pixels"]).max() <= 0
+    assert np.abs(alone["pixels"] - mix["pixels"]).max() <= 0
+    assert abs(alone["n_steps"] - mix["n_steps"]) <= 1
+
+
+def test_stage_execute_collect_matches_run():
+    name = "plain_3keV_100um"
+    evs = W.make_events(name)
+    with sim_for(name) as sim:
+        a = sim.run(evs)
+        sim.stage(evs)
+        sim.execute()
+        b = sim.collect(len(evs))
+    assert [x["event_id"] for x in b] == [e["event_id"] for e in evs]
+    for x, y in zip(a, b):
+        assert np.array_equal(x["pixels"], y["pixels"]) and x["n_steps"] == y["n_steps"]
+
+
+# ---------------------------------------------------------------------------
+# Edge cases and failure paths (host-side injection; no GPU fault)
+# ---------------------------------------------------------------------------
+def test_edge_cases():
+    name = "plain_3keV_100um"
+    H = 100.0
+    with sim_for(name, keep_final_xy=1) as sim:
+        evs = [
+            dict(_ev(name), energy_keV=0.001),                      # zero carriers
+            dict(_ev(name), depth_um=H),                            # absorbed at the readout
+            W.explicit_event([[3.0, 4.0, 50.0]]),                   # one carrier
+            W.explicit_event(np.tile([[1.0, 1.0, 30.0]], (50, 1))), # coincident carriers
+        ]
+        res = sim.run(evs, keep_xy_capacity=1000)
+    assert res[0]["n_carriers"] == 0 and res[0]["n_steps"] == 0 and res[0]["pixels"].sum() == 0
+    assert res[1]["n_collected"] == 829 and res[1]["status"] == 0
+    assert res[2]["n_collected"] == 1 and res[2]["pixels"].sum() == 1
+    assert res[3]["n_collected"] == 50 and np.all(np.isfinite(res[3]["final_xy"]))
+    P = oracle_params(name)
+    for k in (1, 2, 3):
+        r = oracle.run_event(P, evs[k])
+        assert abs(r.n_steps - res[k]["n_steps"]) <= 1
+        assert np.abs(r.pixels - res[k]["pixels"]).max() <= 0
+
+
+def test_max_steps_status():
+    name = "batch_20keV_320um"
+    with sim_for(name, sensor_over=dict(max_steps=50)) as sim:
+        r = sim.run([_ev(name)])[0]
+    assert r["status"] == cts.SIM_EMAXSTEPS and r["n_steps"] == 50
+
+
+def test_submit_errors():
+    name = "plain_3keV_100um"
+    with sim_for(name, max_carriers=2048, queue_capacity=3) as sim:
+        rc, acc = sim.submit([dict(_ev(name), energy_keV=50.0)])   # 13 812 > 2048 carriers
+        assert rc == cts.SIM_ENOMEM_BUDGET and acc == 0
+        rc, acc = sim.submit([dict(_ev(name), depth_um=-1.0)])
+        assert rc == cts.SIM_EINVAL and acc == 0
+        rc, acc = sim.submit(W.make_events(name, n=5))
+        assert rc == cts.SIM_EAGAIN and acc == 3
+        got = []
+        while len(got) < 3:
+            got += sim.poll(8, 10_000)
+        assert sorted(r["event_id"] for r in got) == [0, 1, 2]
+        assert sim.stats()["rejected"] >= 4
+
+
+def test_injected_faults():
+    name = "plain_3keV_100um"
+    with sim_for(name) as sim:
+        sim.submit(W.make_events(name, n=2))
+        assert sim.inject(cts.SIM_ENUMERIC) == 0
+        got = []
+        while len(got) < 2:
+            got += sim.poll(4, 10_000)
+        assert all(r["status"] == cts.SIM_ENUMERIC for r in got)
+        assert sim.inject(cts.SIM_ETIMEOUT) == 0
+        assert sim.poll(4, 10) == []                 # reported as a timeout once
+        r = sim.run(W.make_events(name, n=1))[0]     # the handle still works
+        assert r["status"] == 0
+        assert sim.inject(cts.SIM_ECUDA) == 0
+        sim.submit(W.make_events(name, n=1))
+        with pytest.raises(cts.SimError) as e:
+            sim.poll(4, 1000)
+        assert e.value.code == cts.SIM_ECUDA

@@ -1,0 +1,197 @@
+"""CPU-side checks of the C-ABI library: it loads without a GPU, exports every
+symbol the public headers declare, validates parameters before touching a
+device, and its host scheduling logic (unit planner, arena allocator, drift
+time estimate) is correct.  No kernel is launched here."""
+import glob
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2506_09712_gb300 as cts
+from paper_2506_09712_gb300 import build as cts_build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cts_build.build()
+    return cts.load()
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:int|double|const\s+char\s*\*)\s+(\w+)\s*\(", text, re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_symbols()
+    assert {"sim_init", "sim_submit", "sim_poll", "sim_destroy", "cts_plan_units"} <= declared
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert declared == set(cts.EXPORTED)
+
+
+def test_strerror_names_every_code(lib):
+    for code in range(-9, 1):
+        assert cts.strerror(code) != "unknown status"
+    assert cts.strerror(-99) == "unknown status"
+
+
+def _good():
+    s = cts.make_sensor(dict(thickness_um=320.0, bias_V=150.0, depletion_V=60.0, dt_ps=10.0))
+    f = cts.make_field()
+    m = cts.make_mobility(dict(mu0_h=480.0, vsat_h=0.95e7, beta_h=1.2))
+    return s, f, m
+
+
+@pytest.mark.parametrize("field,value", [
+    ("thickness_um", 0.0), ("dt_ps", -1.0), ("temperature_K", 0.0), ("grid_n", 0),
+    ("species", 2), ("max_steps", 0), ("bias_V", 10.0), ("pitch_um", float("nan")),
+])
+def test_init_rejects_bad_sensor(lib, field, value):
+    s, f, m = _good()
+    setattr(s, field, value)
+    rc, h = cts.sim_init(s, f, m, None)
+    assert rc == cts.SIM_EINVAL and not h.value
+
+
+def test_init_rejects_bad_mobility(lib):
+    s, f, m = _good()
+    m.beta_h = 0.0
+    assert cts.sim_init(s, f, m, None)[0] == cts.SIM_EINVAL
+    s, f, m = _good()
+    s.species = cts.CTS_BOTH          # electrons need their own parameters
+    assert cts.sim_init(s, f, m, None)[0] == cts.SIM_EINVAL
+
+
+def test_init_without_device_reports_enodev(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    s, f, m = _good()
+    rc, h = cts.sim_init(s, f, m, None)
+    assert rc == cts.SIM_ENODEV and not h.value
+
+
+def test_kernel_hooks_without_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(cts.SimError) as e:
+        cts.sim_debug_philox([[0, 0, 0, 0]], [[0, 0]])
+    assert e.value.code == cts.SIM_ENODEV
+
+
+def _check_cover(units, n_h, n_e):
+    """Every ordered pair (i, j) of a slot is covered exactly once: per slot and
+    species the i-tiles partition the carriers, and per i-tile the j ranges
+    partition the slot's concatenated source list."""
+    tiles = {}
+    for (slot, spec, i0, ni, j0, j1, split, nsplit, iblock, pbase) in units:
+        tiles.setdefault((slot, spec, i0, ni), []).append((j0, j1))
+    per_species = {}
+    for (slot, spec, i0, ni), js in tiles.items():
+        js.sort()
+        n = n_h[slot] + n_e[slot]
+        assert js[0][0] == 0 and js[-1][1] == n, (slot, js)
+        for (a0, a1), (b0, b1) in zip(js, js[1:]):
+            assert a1 == b0 and a0 < a1
+        per_species.setdefault((slot, spec), []).append((i0, i0 + ni))
+    for slot in range(len(n_h)):
+        if n_h[slot] <= 0:
+            continue
+        for spec, cnt in ((0, n_h[slot]), (1, n_e[slot])):
+            iv = sorted(per_species.get((slot, spec), []))
+            if cnt == 0:
+                assert not iv
+                continue
+            assert iv[0][0] == 0 and iv[-1][1] == cnt
+            for (a0, a1), (b0, b1) in zip(iv, iv[1:]):
+                assert a1 == b0
+    return True
+
+
+@pytest.mark.parametrize("n_h,n_e,tile,grid", [
+    ([5525] * 64, [0] * 64, 512, 456),
+    ([5525], [0], 512, 456),
+    ([829, 0, 1381, 6906, 3], [0, 0, 0, 0, 0], 512, 456),
+    ([3000, 17], [3000, 5], 256, 300),
+    ([1], [0], 512, 456),
+])
+def test_planner_covers_every_pair_once(lib, n_h, n_e, tile, grid):
+    rc, units, pfl = cts.cts_plan_units(n_h, n_e, tile, grid)
+    assert rc == 0
+    assert _check_cover(units, n_h, n_e)
+    # idle slots get no units
+    assert all(n_h[u[0]] > 0 for u in units)
+    # decreasing cost order
+    cost = units[:, 3] * (units[:, 5] - units[:, 4])
+    assert np.all(np.diff(cost) <= 0)
+    # split i-blocks: consistent metadata, disjoint partial regions
+    blocks = {}
+    for u in units:
+        if u[7] > 1:
+            blocks.setdefault(u[8], []).append(u)
+    ends = []
+    for b, us in blocks.items():
+        assert sorted(x[6] for x in us) == list(range(us[0][7]))
+        assert len({(x[0], x[1], x[2], x[9]) for x in us}) == 1
+        ends.append((us[0][9], us[0][9] + us[0][7] * 3 * tile))
+    ends.sort()
+    for (a0, a1), (b0, b1) in zip(ends, ends[1:]):
+        assert a1 <= b0
+    if ends:
+        assert ends[-1][1] <= pfl
+
+
+def test_planner_splits_when_few_events(lib):
+    # One 5525-carrier event on 456 CTAs: tiles alone would leave most CTAs idle.
+    rc, units, _ = cts.cts_plan_units([5525], [0], 512, 456)
+    assert rc == 0 and units.shape[0] > 11
+    # Many events: whole tiles already fill the grid, no splits needed.
+    rc, units, pfl = cts.cts_plan_units([5525] * 256, [0] * 256, 512, 456)
+    assert rc == 0 and pfl == 0 and np.all(units[:, 7] == 1)
+    # No splitting allowed
+    rc, units, pfl = cts.cts_plan_units([5525], [0], 512, 456, allow_split=0)
+    assert rc == 0 and pfl == 0 and units.shape[0] == 11
+
+
+def test_planner_respects_budgets(lib):
+    rc, units, pfl = cts.cts_plan_units([5525] * 4, [0] * 4, 512, 456, partial_cap=3 * 512 * 4)
+    assert rc == 0 and pfl <= 3 * 512 * 4
+    assert _check_cover(units, [5525] * 4, [0] * 4)
+    rc, _, _ = cts.cts_plan_units([5525] * 64, [0] * 64, 512, 456, max_units=100)
+    assert rc == -2
+
+
+def test_arena_first_fit_and_coalescing(lib):
+    # allocate 3 blocks, free the middle, reuse it; free all, whole capacity again
+    ops = [100, 200, 300, -2, 150, -1, -3, -5, 1000]
+    rc, res = cts.cts_arena_replay(1024, ops)
+    assert rc == 0
+    a, b, c = res[0], res[1], res[2]
+    assert (a, b, c) == (0, 128, 352)            # rounded to multiples of 32
+    assert res[4] == 128                         # the freed middle block is reused
+    assert res[8] == 0                           # everything coalesced
+    rc, res = cts.cts_arena_replay(256, [200, 100])
+    assert res[1] == -1                          # no room
+
+
+def test_estimate_steps_matches_eq9(lib):
+    # beta = 1: Eq. 9 closed form, t = (1/(mu0 k)) ln(E(0)/E(z0)) + z0 / vsat.
+    H, Vb, Vd, mu0, vsat = 320.0, 150.0, 60.0, 480.0, 0.95e7
+    for depth in (10.0, 120.0, 300.0):
+        z0 = H - depth
+        E = lambda z: (Vb - Vd) / H + 2 * Vd * (H - z) / H ** 2
+        t = 1 / (mu0 * 0.1 * 2 * Vd / H ** 2) * math.log(E(0) / E(z0)) + z0 / (vsat * 1e-5)
+        est = cts.cts_estimate_steps(H, Vb, Vd, mu0, vsat, 1.0, 10.0, depth)
+        assert est == pytest.approx(t / 0.01, rel=1e-4)
