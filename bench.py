@@ -1,0 +1,435 @@
+#!/usr/bin/env python
+"""Benchmark of the brute-force charge-transport Monte Carlo on GB300.
+
+One step = one whole simulation of a batch of synthetic events (event
+initialisation, every time step of the O(N^2) field + drift/diffusion update
+until each hole is collected, pixel readout): by default the 64 photons of
+20 keV in a 320 um sensor (5525 carriers each, dt = 10 ps, 9x9 pixels).
+
+  value   pair interactions/s over the timed steps, the descriptors already
+          resident on the device (sim_stage before, sim_execute timed with
+          CUDA events on the library's stream, L2 flushed between steps)
+  e2e     the same metric through sim_run with host buffers: descriptor
+          upload and result download inside the timed region
+  roofline  the fused step kernel against the FP32 ALU peak
+          (SMs x 128 lanes x 2 flop x clock), 16 algorithmic flops per pair
+  cpu_baseline  the FP64 oracle on a bounded sample, on the host cores
+
+`--impl reference` times the oracle alone on the same workload and metric.
+Under torchrun every rank simulates its own batch (weak scaling, no
+data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("pair interactions/s (% FP32 peak) and events/s at 20 keV/320um; "
+          "p50/p99 event latency")
+UNIT = "pair interactions/s"
+FLOPS_PER_PAIR = 16          # 3 sub, 3 mul + 3 add (r^2 + eps^2), 2 mul (r^-3), 3 fma
+FP32_LANES_PER_SM = 128
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="batch_20keV_320um")
+    ap.add_argument("--events", type=int, default=0, help="events per rank (0: preset)")
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-extras", action="store_true", help="skip plain/serving/oracle legs")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, pw, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+                pw.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# The oracle leg (bounded sample on the host cores)
+# ---------------------------------------------------------------------------
+def oracle_rate(workload: str, seconds: float, steps: int = 0):
+    """Interactions/s of the FP64 oracle on the first time steps of one event
+    (the number of steps is sized to about `seconds` unless given)."""
+    import oracle
+    import workloads as W
+    oracle.build()
+    p = W.preset(workload)
+    ev = W.make_events(workload, n=1)[0]
+    if not steps:
+        probe = 8
+        P = oracle.make_params(dict(p["sensor"], max_steps=probe), W.field_switches(),
+                               p["mobility"])
+        t0 = time.perf_counter()
+        r = oracle.run_event(P, ev)
+        per_step = (time.perf_counter() - t0) / max(r.n_steps, 1)
+        steps = max(probe, int(seconds / max(per_step, 1e-9)))
+    P = oracle.make_params(dict(p["sensor"], max_steps=steps), W.field_switches(),
+                           p["mobility"])
+    t0 = time.perf_counter()
+    r = oracle.run_event(P, ev)
+    dt = time.perf_counter() - t0
+    return {"value": r.interactions / dt, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle", "seconds": dt, "interactions": r.interactions, "steps": steps,
+            "sample": f"event 0 of {workload}: its first {r.n_steps} time steps "
+                      f"({r.interactions} pair interactions), FP64, OpenMP over carriers"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(args.steps + args.warmup, 1)))
+    rates, secs, steps, r = [], [], 0, None
+    for k in range(args.warmup + args.steps):
+        r = oracle_rate(args.workload, per_step, steps)
+        steps = r["steps"]
+        if k >= args.warmup:
+            rates.append(r["value"])
+            secs.append(r["seconds"])
+    total_s = sum(secs)
+    value = sum(r_ * s_ for r_, s_ in zip(rates, secs)) / total_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / max(len(secs), 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload,
+                       "reference": "FP64 CPU oracle on the host cores (no GPU)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"],
+                             "kind": "oracle", "sample": r["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("cts_kernels.cu", "cts_internal.h"):
+        with open(os.path.join(ROOT, "paper_2506_09712_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if the
+    kernel source is unchanged since that capture (else None)."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def serving_leg(cts, W, torch, device):
+    """Continuous batching under Poisson arrivals of the serving mix: saturation
+    throughput first, then p50/p99 latency at 0.7x of it, then the literal
+    2 kHz offer with a bounded queue."""
+    name = "serve_mix_320um"
+    p = W.preset(name)
+    out = {"workload": name}
+    with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_SERVE, device=device,
+                       max_slots=256) as sim:
+        evs = W.make_events(name, n=192, first_id=10_000)
+        t0 = time.perf_counter()
+        res = sim.run(evs)
+        sat = len(res) / (time.perf_counter() - t0)
+        out["saturation_events_per_s"] = sat
+
+        out["at_0p7_saturation"] = _offered(sim, W, name, 0.7 * sat, 160)
+    with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_SERVE, device=device,
+                       max_slots=256, queue_capacity=64) as sim:
+        out["at_2kHz_bounded_queue"] = _offered(sim, W, name, p["rate_hz"], 400)
+    return out
+
+
+def _offered(sim, W, name, rate, n):
+    """Open-loop Poisson arrivals at `rate`; latency = completion - submission."""
+    arr = W.poisson_arrivals(rate, n, seed=7)
+    evs = W.make_events(name, n=n, first_id=20_000)
+    got, rejected, k = [], 0, 0
+    start = time.perf_counter()
+    while len(got) + rejected < n:
+        now = time.perf_counter() - start
+        while k < n and arr[k] <= now:
+            rc, _ = sim.submit([evs[k]])
+            rejected += rc != 0
+            k += 1
+        got += sim.poll(64, 1)
+    wall = time.perf_counter() - start
+    lat = sorted((r["t_done_ns"] - r["t_submit_ns"]) * 1e-6 for r in got)
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
+    return {"offered_hz": rate, "events": n, "completed": len(got), "rejected": rejected,
+            "events_per_s": len(got) / wall, "p50_ms": q(0.5), "p99_ms": q(0.99)}
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import paper_2506_09712_gb300 as cts
+    import workloads as W
+    from paper_2506_09712_gb300 import build as cts_build
+
+    cts_build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    p = W.preset(args.workload)
+    n_ev = args.events or p["n_events"]
+    events = W.make_events(args.workload, n=n_ev, first_id=rank * n_ev)
+    stream = torch.cuda.Stream()
+    opts = dict(device=local, max_slots=max(256, n_ev), time_launches=1,
+                stream=stream.cuda_stream, variant=args.variant, chunk_steps=args.chunk)
+    sim = cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_BATCHED, **opts)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def one_step():
+        sim.stage(events)
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        s0 = sim.stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.execute()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s1 = sim.stats()
+        res = sim.collect(n_ev)
+        inter = sum(r["interactions"] for r in res)
+        return e0.elapsed_time(e1), inter, s0, s1, res
+
+    for _ in range(args.warmup):
+        one_step()
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "") or "")
+    gpu_id = (uuid if uuid.startswith("GPU-") else "GPU-" + uuid) if uuid else str(local)
+    sampler = ClockSampler(gpu_id)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ms, inter, kms, kl, launches = [], 0, 0.0, 0, 0
+    statuses = []
+    for _ in range(args.steps):
+        t, i, s0, s1, res = one_step()
+        ms.append(t)
+        inter += i
+        kms += s1["step_kernel_ms"] - s0["step_kernel_ms"]
+        kl += s1["step_kernel_launches"] - s0["step_kernel_launches"]
+        launches += s1["kernel_launches"] - s0["kernel_launches"]
+        statuses += [r["status"] for r in res]
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        c = torch.tensor([float(inter), float(n_ev * args.steps)], device="cuda",
+                         dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        inter_all, events_all = int(c[0].item()), int(c[1].item())
+    else:
+        inter_all, events_all = inter, n_ev * args.steps
+    value = inter_all / (total_ms * 1e-3)
+    events_per_s = events_all / (total_ms * 1e-3)
+
+    # end to end through sim_run with host buffers
+    sim.run(events)
+    torch.cuda.synchronize()
+    s0 = sim.stats()
+    t0 = time.perf_counter()
+    e2e_inter = 0
+    for _ in range(args.steps):
+        res = sim.run(events)
+        e2e_inter += sum(r["interactions"] for r in res)
+    e2e_s = time.perf_counter() - t0
+    s1 = sim.stats()
+    if dist:
+        t = torch.tensor([e2e_s, float(e2e_inter)], device="cuda", dtype=torch.float64)
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ti = t[1:].clone()
+        dist.all_reduce(ti, op=dist.ReduceOp.SUM)
+        e2e_s, e2e_inter = float(tm.item()), int(ti.item())
+    e2e = {"value": e2e_inter / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // args.steps,
+           "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.steps,
+           "api": "sim_run (host descriptors in, host results out)"}
+    st = sim.stats()
+    sim.close()
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return 0
+
+    sm_count = st["sm_count"]
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except (OSError, ValueError):
+        pass
+    sm_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    achieved = FLOPS_PER_PAIR * inter / (kms * 1e-3) / 1e12 if kms > 0 else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+            "frac": achieved / peak_tflops if achieved else None,
+            "traffic": profiled_traffic(),
+            "kernel": "step_kernel (fused pair field + update)",
+            "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "
+                          f"(max SM clock); measured-clock frac in frac_at_measured_clock",
+            "flops_per_pair": FLOPS_PER_PAIR,
+            "step_kernel_ms": kms, "step_kernel_launches": kl,
+            "kernel_share_of_timed": kms / (sum(ms)) if ms else None}
+    if achieved and clocks.get("sm_mhz"):
+        roof["frac_at_measured_clock"] = achieved / (
+            sm_count * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "events_per_gpu": n_ev,
+                       "energy_keV": p.get("energies", [[None]])[0][0],
+                       "thickness_um": p["sensor"]["thickness_um"],
+                       "bias_V": p["sensor"]["bias_V"], "dt_ps": p["sensor"]["dt_ps"],
+                       "grid": f'{p["sensor"]["grid_n"]}x{p["sensor"]["grid_n"]}',
+                       "positions": "f64", "pair_field": "f32 + Kahan",
+                       "l2": "flushed (256 MiB write) before every timed step",
+                       "parallelism": f"event-sharded x{world}",
+                       "variant": st["variant"]},
+            "events_per_s": events_per_s,
+            "roofline": roof, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+            "statuses_ok": all(s == 0 for s in statuses)}
+    if p.get("energies") and len(p["energies"]) == 1:
+        line["config"]["carriers_per_event"] = int(round(p["energies"][0][0] * 1000 / 3.62))
+
+    if not args.no_extras and world == 1:
+        # the plain one-event-per-launch path on the same GPU (>= 5x target)
+        with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_PLAIN,
+                           device=local) as plain:
+            sample = events[:2]
+            plain.run(sample[:1])
+            t0 = time.perf_counter()
+            plain.run(sample)
+            plain_eps = len(sample) / (time.perf_counter() - t0)
+        line["plain"] = {"events_per_s": plain_eps, "sample": "2 events, PLAIN mode",
+                         "batched_over_plain": events_per_s / plain_eps}
+        try:
+            line["serving"] = serving_leg(cts, W, torch, local)
+        except Exception as e:  # reported, never fatal for the bench line
+            line["serving"] = {"error": repr(e)}
+        line["cpu_baseline"] = oracle_rate(args.workload, args.cpu_seconds)
+        line["cpu_baseline"]["value_ratio_gpu_over_cpu"] = value / line["cpu_baseline"]["value"]
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -109,6 +109,7 @@ typedef struct sim_options_t {
   int32_t variant;         /* pair-kernel variant + 1; 0 = default choice */
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
   int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */
+  int32_t time_launches;   /* 1 = time every step-kernel launch with CUDA events */
   void* stream;            /* cudaStream_t to launch on; NULL = own stream */
 } sim_options_t;
 
@@ -166,6 +167,10 @@ typedef struct sim_stats_t {
   int32_t sm_count;
   int32_t variant;          /* pair-kernel variant in use */
   double device_ms;         /* device time of executed chunks (CUDA events) */
+  double step_kernel_ms;    /* summed step-kernel launch times (time_launches) */
+  int64_t step_kernel_launches; /* launches timed into step_kernel_ms */
+  int64_t h2d_bytes;        /* bytes copied host -> device by the library */
+  int64_t d2h_bytes;        /* bytes copied device -> host by the library */
 } sim_stats_t;
 
 typedef struct sim_t sim_t;
@@ -235,6 +240,12 @@ int sim_debug_normals(const uint64_t* in, int64_t n, double* out);
 int sim_debug_trajectory(sim_t* sim, const sim_event_t* ev, int64_t n_steps,
                          double* pos_out, int8_t* state_out, int64_t capacity,
                          int64_t* steps_done);
+
+/* One step of the pair kernel (field only: the staged events do not move)
+ * on the events admitted by sim_stage, with a per-CTA trace: out[4g..4g+3] =
+ * (SM id, start ns, end ns, pairs) of CTA g, for up to max_ctas CTAs;
+ * *n_ctas receives the grid size.  For load-balance studies. */
+int sim_debug_trace_step(sim_t* sim, uint64_t* out, int32_t max_ctas, int32_t* n_ctas);
 
 /* Host-side fault injection for the failure-path tests: the next chunk (or
  * poll) reports the given code as if the device or queue had raised it

@@ -19,22 +19,28 @@ extern "C" {
  * electrons) of slot `slot`, against sources [j0, j1) of the slot's
  * concatenated [holes | electrons] list.  Units of one i-block share iblock
  * and are split into nsplit j ranges (split = 0 .. nsplit - 1); pbase is the
- * float offset of the i-block's partial sums (nsplit > 1 only). */
+ * offset (FP64 entries) of the tile's 3 x tile_i accumulators (nsplit > 1). */
 typedef struct cts_unit_t {
   int32_t slot, spec, i0, ni, j0, j1, split, nsplit, iblock, pbase;
 } cts_unit_t;
 
 /* Plan the units of one step for n_slots resident events with n_h[s] holes
- * and n_e[s] electrons (negative or zero counts: slot idle).  tile_i = i's per
- * unit (threads x i's per thread of the pair kernel), grid = persistent CTAs,
- * allow_split = 0 forbids j splits (then every unit covers all sources).
- * Units are written to out (capacity max_units) in decreasing cost order;
- * *n_out their count, *partial_floats the partial-sum floats they need.
- * Returns 0, SIM_EINVAL (-1) for bad sizes, or -2 if max_units or
- * partial_cap is too small even without splits. */
+ * and n_e[s] electrons (slots with n_h <= 0 are finished and get no work).
+ * tile_i = i's per tile (threads x i's per thread of the pair kernel); grid =
+ * persistent CTAs.  allow_split = 1: the total pair work is cut into `grid`
+ * equal contiguous shares (tiles cut at j multiples of 4, segments of a tile
+ * share iblock/pbase for their partial sums), grouped by CTA: CTA g runs
+ * units [cta_begin[g], cta_begin[g+1]).  allow_split = 2: guided pieces for a
+ * dynamic queue (largest first; pieces shrink over the last 30 % of the work)
+ * that CTAs pull from; cta_begin[grid] = number of units, the rest 0.
+ * allow_split = 0: whole tiles dealt out longest first.  Units are written to
+ * out (capacity max_units); cta_begin has grid + 1 entries.  *n_out = units,
+ * *partial_floats = FP64 partial-sum entries needed (limit partial_cap).
+ * Returns 0, -1 for bad arguments, -2 if max_units is too small. */
 int cts_plan_units(const int32_t* n_h, const int32_t* n_e, int32_t n_slots, int32_t tile_i,
                    int32_t grid, int32_t allow_split, int32_t max_units, int64_t partial_cap,
-                   cts_unit_t* out, int32_t* n_out, int64_t* partial_floats);
+                   cts_unit_t* out, int32_t* n_out, int32_t* cta_begin,
+                   int64_t* partial_floats);
 
 /* First-fit carrier arena of the scheduler, for tests: replays n_ops
  * operations (size > 0: allocate size entries and write the offset, or -1 if

@@ -49,7 +49,8 @@ class sim_options_t(C.Structure):
                 ("chunk_steps", C.c_int32), ("max_carriers", C.c_int64),
                 ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32),
                 ("variant", C.c_int32), ("disable_graphs", C.c_int32),
-                ("keep_final_xy", C.c_int32), ("stream", C.c_void_p)]
+                ("keep_final_xy", C.c_int32), ("time_launches", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class sim_event_t(C.Structure):
@@ -75,7 +76,9 @@ class sim_stats_t(C.Structure):
     _fields_ = [("events_done", C.c_int64), ("interactions", C.c_int64),
                 ("steps_launched", C.c_int64), ("kernel_launches", C.c_int64),
                 ("chunks", C.c_int64), ("queue_depth", C.c_int64), ("rejected", C.c_int64),
-                ("sm_count", C.c_int32), ("variant", C.c_int32), ("device_ms", C.c_double)]
+                ("sm_count", C.c_int32), ("variant", C.c_int32), ("device_ms", C.c_double),
+                ("step_kernel_ms", C.c_double), ("step_kernel_launches", C.c_int64),
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
 
 
 class cts_unit_t(C.Structure):
@@ -87,7 +90,8 @@ class cts_unit_t(C.Structure):
 EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_execute",
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
-            "sim_debug_inject", "cts_plan_units", "cts_arena_replay", "cts_estimate_steps"]
+            "sim_debug_inject", "sim_debug_trace_step", "cts_plan_units", "cts_arena_replay",
+            "cts_estimate_steps"]
 
 _lib = None
 
@@ -131,8 +135,9 @@ def load(build_if_missing: bool = True):
         "sim_debug_trajectory": [C.c_void_p, P(sim_event_t), i64, P(d), P(C.c_int8), i64,
                                  P(i64)],
         "sim_debug_inject": [C.c_void_p, C.c_int],
+        "sim_debug_trace_step": [C.c_void_p, P(u64), i32, P(i32)],
         "cts_plan_units": [P(i32), P(i32), i32, i32, i32, i32, i32, i64, P(cts_unit_t), P(i32),
-                           P(i64)],
+                           P(i32), P(i64)],
         "cts_arena_replay": [i64, P(i64), i32, P(i64)],
         "cts_estimate_steps": [d, d, d, d, d, d, d, d],
     }
@@ -269,20 +274,30 @@ def sim_debug_inject(h, fault):
     return load().sim_debug_inject(h, int(fault))
 
 
+def sim_debug_trace_step(h, max_ctas=8192):
+    """Per-CTA (smid, t_start_ns, t_end_ns, pairs) of one field-only step."""
+    out = np.zeros((max_ctas, 4), dtype=np.uint64)
+    n = C.c_int32(0)
+    _check(load().sim_debug_trace_step(h, _ptr(out, C.c_uint64), max_ctas, C.byref(n)),
+           "sim_debug_trace_step")
+    return out[:n.value]
+
+
 def cts_plan_units(n_h, n_e, tile_i, grid, allow_split=1, max_units=65536,
                    partial_cap=1 << 26):
+    """Returns (rc, units[n, 10], cta_begin[grid + 1], partial_floats)."""
     n_h = np.ascontiguousarray(n_h, dtype=np.int32); n_e = np.ascontiguousarray(n_e, dtype=np.int32)
     out = (cts_unit_t * max_units)()
+    begin = np.zeros(grid + 1, dtype=np.int32)
     n = C.c_int32(0)
     pf = C.c_int64(0)
     rc = load().cts_plan_units(_ptr(n_h, C.c_int32), _ptr(n_e, C.c_int32), n_h.size, tile_i,
                                grid, allow_split, max_units, partial_cap, out, C.byref(n),
-                               C.byref(pf))
+                               _ptr(begin, C.c_int32), C.byref(pf))
     if rc != 0:
-        return rc, None, 0
-    arr = np.array([[getattr(out[k], f) for f, _ in cts_unit_t._fields_] for k in range(n.value)],
-                   dtype=np.int64).reshape(-1, 10)
-    return rc, arr, pf.value
+        return rc, None, None, 0
+    raw = np.frombuffer(out, dtype=np.int32, count=n.value * 10).reshape(-1, 10)
+    return rc, raw.astype(np.int64), begin, pf.value
 
 
 def cts_arena_replay(capacity, ops):

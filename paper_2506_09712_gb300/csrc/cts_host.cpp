@@ -13,75 +13,174 @@
 namespace cts {
 
 // ---------------------------------------------------------------------------
-// Unit planner.  Each slot's i's are cut into tiles of tile_i; a tile is cut
-// into nsplit j ranges when the step has too little work to fill the GPU with
-// whole tiles (few or small events), so every CTA still gets a unit of about
-// `target` pairs.  Units are sorted by cost, largest first (LPT order for the
-// dynamic per-step work counter).
+// Unit planner (a stream-K style partition).  The pair work of one step is
+// the sequence of i-tiles (tile_i carriers of one species of one slot, each
+// against all n sources of its slot); its total cost W = sum ni * n is cut
+// into G equal contiguous shares, one per persistent CTA, at j granularity
+// (rounded to multiples of 4 sources).  A tile cut by a share boundary is
+// computed in several segments whose partial sums are combined by the CTA
+// that finishes last, so every CTA gets the same number of pairs (to within
+// 4 * tile_i) and no dynamic queue is needed.
 // ---------------------------------------------------------------------------
+namespace {
+struct Tile {
+  int32_t slot, spec, i0, ni, n;
+  double c0;  // cumulative cost before the tile
+};
+}  // namespace
+
 int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, int grid,
                bool allow_split, int max_units, int64_t partial_cap, std::vector<UnitPlan>* out,
-               int64_t* partial_floats) {
+               std::vector<int32_t>* cta_begin, int64_t* partial_floats, bool dynamic) {
   out->clear();
+  cta_begin->assign((size_t)std::max(grid, 0) + 1, 0);
   *partial_floats = 0;
   if (tile_i <= 0 || grid <= 0 || n_slots < 0 || max_units <= 0) return -1;
-  double total = 0.0;
-  int64_t tiles = 0;
-  for (int s = 0; s < n_slots; ++s) {
-    const int64_t nh = std::max(n_h[s], 0), ne = std::max(n_e[s], 0);
-    if (nh <= 0) continue;  // an event with no hole is finished
-    const double n = (double)(nh + ne);
-    total += n * n;
-    tiles += (nh + tile_i - 1) / tile_i + (ne + tile_i - 1) / tile_i;
-  }
-  if (tiles > max_units) return -2;
-  // Aim for >= 4 units per CTA, each at least one shared-memory stage deep.
-  const double target = std::max(total / (4.0 * grid), (double)tile_i * (double)kPlanMinJ);
-  int64_t units_left = max_units - tiles;  // budget for extra split units
-  int iblock = 0;
-  int64_t pfl = 0;
+  std::vector<Tile> tiles;
+  double W = 0.0;
   for (int s = 0; s < n_slots; ++s) {
     const int nh = std::max(n_h[s], 0), ne = std::max(n_e[s], 0);
-    if (nh <= 0) continue;
+    if (nh <= 0) continue;  // an event with no hole is finished
     const int n = nh + ne;
     for (int spec = 0; spec < 2; ++spec) {
       const int ni_tot = spec ? ne : nh;
       for (int i0 = 0; i0 < ni_tot; i0 += tile_i) {
         const int ni = std::min(tile_i, ni_tot - i0);
-        int ns = 1;
-        if (allow_split) {
-          const double want = std::floor((double)ni * (double)n / target + 0.5);
-          ns = (int)std::max(1.0, std::min(want, (double)kPlanMaxSplit));
-          ns = std::min(ns, std::max(1, n / kPlanMinJ));
-          if (ns > 1 && (int64_t)(ns - 1) > units_left) ns = (int)std::max<int64_t>(1, units_left + 1);
-          if (ns > 1 && pfl + (int64_t)ns * 3 * tile_i > partial_cap) ns = 1;
-        }
-        const int pbase = ns > 1 ? (int)pfl : 0;
-        for (int sp = 0; sp < ns; ++sp) {
-          UnitPlan u;
-          u.slot = s;
-          u.spec = spec;
-          u.i0 = i0;
-          u.ni = ni;
-          u.j0 = (int)((int64_t)n * sp / ns);
-          u.j1 = (int)((int64_t)n * (sp + 1) / ns);
-          u.split = sp;
-          u.nsplit = ns;
-          u.iblock = ns > 1 ? iblock : -1;
-          u.pbase = pbase;
-          out->push_back(u);
-        }
-        if (ns > 1) {
-          units_left -= ns - 1;
-          pfl += (int64_t)ns * 3 * tile_i;
-          ++iblock;
-        }
+        tiles.push_back(Tile{s, spec, i0, ni, n, W});
+        W += (double)ni * (double)n;
       }
     }
   }
-  std::stable_sort(out->begin(), out->end(), [](const UnitPlan& a, const UnitPlan& b) {
-    return (int64_t)a.ni * (a.j1 - a.j0) > (int64_t)b.ni * (b.j1 - b.j0);
-  });
+  if ((int64_t)tiles.size() > max_units) return -2;
+  if (tiles.empty()) return 0;
+  auto emit = [&](const Tile& t, int j0, int j1, int split, int nsplit, int iblock, int pbase) {
+    UnitPlan u;
+    u.slot = t.slot;
+    u.spec = t.spec;
+    u.i0 = t.i0;
+    u.ni = t.ni;
+    u.j0 = j0;
+    u.j1 = j1;
+    u.split = split;
+    u.nsplit = nsplit;
+    u.iblock = iblock;
+    u.pbase = pbase;
+    out->push_back(u);
+  };
+  // CTAs that get work: enough that each share holds >= kPlanMinPairs pairs.
+  const int g_eff = allow_split ? (int)std::max(1.0, std::min((double)grid,
+                                                             std::floor(W / (kPlanMinJ * (double)tile_i))))
+                                : grid;
+  if (dynamic && !allow_split) dynamic = false;
+  if (!dynamic && (!allow_split || g_eff == 1)) {
+    // whole tiles, longest-processing-time first onto the least loaded CTA
+    std::vector<int> order(tiles.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return (double)tiles[a].ni * tiles[a].n > (double)tiles[b].ni * tiles[b].n;
+    });
+    std::vector<double> load((size_t)grid, 0.0);
+    std::vector<std::vector<int>> per((size_t)grid);
+    for (int t : order) {
+      const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      load[g] += (double)tiles[t].ni * tiles[t].n;
+      per[g].push_back(t);
+    }
+    for (int g = 0; g < grid; ++g) {
+      (*cta_begin)[g] = (int32_t)out->size();
+      for (int t : per[g]) emit(tiles[t], 0, tiles[t].n, 0, 1, -1, 0);
+    }
+    (*cta_begin)[grid] = (int32_t)out->size();
+    return 0;
+  }
+  if (dynamic) {
+    // Guided pieces for a dynamic queue: most work in large pieces, the last
+    // fraction in pieces that shrink toward the end, all sorted largest
+    // first; CTAs that run faster simply take more of them.
+    const double w = W / grid;
+    int iblock = 0;
+    int64_t pfl = 0;
+    struct Piece { int t, j0, j1, k, ns; };
+    std::vector<Piece> pieces;
+    for (size_t ti = 0; ti < tiles.size(); ++ti) {
+      const Tile& t = tiles[ti];
+      const double f = t.c0 / W;
+      const double target = f < 0.70 ? 0.5 * w : f < 0.92 ? 0.125 * w : w / 32.0;
+      int ns = (int)std::max(1.0, std::ceil((double)t.ni * t.n / target));
+      ns = std::min({ns, std::max(1, t.n / kPlanMinJ), kPlanMaxPieces});
+      if (ns > 1 && pfl + (int64_t)3 * tile_i > partial_cap) ns = 1;
+      for (int k = 0; k < ns; ++k) {
+        int j0 = (int)((int64_t)t.n * k / ns) & ~3, j1 = k + 1 == ns ? t.n : (int)((int64_t)t.n * (k + 1) / ns) & ~3;
+        if (k > 0) j0 = pieces.back().j1;
+        pieces.push_back(Piece{(int)ti, j0, j1, k, ns});
+      }
+      if (ns > 1) {
+        for (int k = 0; k < ns; ++k) pieces[pieces.size() - ns + k].ns = ns;
+      }
+    }
+    // partial-sum regions per split tile
+    std::vector<int> pb(tiles.size(), 0), ib(tiles.size(), -1);
+    for (const Piece& pc : pieces)
+      if (pc.ns > 1 && pc.k == 0) {
+        pb[pc.t] = (int)pfl;
+        ib[pc.t] = iblock++;
+        pfl += (int64_t)3 * tile_i;
+      }
+    std::stable_sort(pieces.begin(), pieces.end(), [&](const Piece& a, const Piece& b) {
+      return (double)tiles[a.t].ni * (a.j1 - a.j0) > (double)tiles[b.t].ni * (b.j1 - b.j0);
+    });
+    if ((int64_t)pieces.size() > max_units) return -2;
+    for (const Piece& pc : pieces)
+      emit(tiles[pc.t], pc.j0, pc.j1, pc.k, pc.ns, ib[pc.t], pb[pc.t]);
+    for (int g = 0; g <= grid; ++g) (*cta_begin)[g] = g == grid ? (int32_t)out->size() : 0;
+    *partial_floats = pfl;
+    return 0;
+  }
+  const double share = W / g_eff;
+  // j boundary inside tile t for cumulative cost x (multiple of 4, clamped)
+  auto bnd = [&](const Tile& t, double x) -> int {
+    const double j = std::ceil((x - t.c0) / t.ni - 1e-9);
+    int jj = (int)std::max(0.0, std::min((double)t.n, j));
+    jj = (jj + 3) & ~3;
+    return std::min(jj, t.n);
+  };
+  int iblock = 0;
+  int64_t pfl = 0;
+  int next_cta = 0;
+  for (const Tile& t : tiles) {
+    const double c1 = t.c0 + (double)t.ni * t.n;
+    int g_first = (int)std::floor(t.c0 / share);
+    int g_last = (int)std::floor((c1 - 1e-6) / share);
+    g_first = std::min(std::max(g_first, 0), g_eff - 1);
+    g_last = std::min(std::max(g_last, g_first), g_eff - 1);
+    // segments [bnd(g*share), bnd((g+1)*share)) for g in [g_first, g_last]
+    std::vector<std::pair<int, std::pair<int, int>>> segs;
+    for (int g = g_first; g <= g_last; ++g) {
+      const int j0 = g == g_first ? 0 : bnd(t, g * share);
+      const int j1 = g == g_last ? t.n : bnd(t, (g + 1) * share);
+      if (j1 > j0) segs.push_back({g, {j0, j1}});
+    }
+    const int ns = (int)segs.size();
+    int pbase = 0, ib = -1;
+    if (ns > 1) {
+      if (pfl + (int64_t)3 * tile_i > partial_cap) {
+        // no room for partial sums: run the tile whole on its first CTA
+        segs.assign(1, {segs.front().first, {0, t.n}});
+      } else {
+        pbase = (int)pfl;
+        ib = iblock++;
+        pfl += (int64_t)3 * tile_i;
+      }
+    }
+    const int nsf = (int)segs.size();
+    for (int k = 0; k < nsf; ++k) {
+      const int g = segs[k].first;
+      while (next_cta <= g) (*cta_begin)[next_cta++] = (int32_t)out->size();
+      emit(t, segs[k].second.first, segs[k].second.second, k, nsf, ib, pbase);
+    }
+  }
+  while (next_cta <= grid) (*cta_begin)[next_cta++] = (int32_t)out->size();
+  if ((int64_t)out->size() > max_units) return -2;
   *partial_floats = pfl;
   return 0;
 }
@@ -162,17 +261,20 @@ extern "C" {
 
 int cts_plan_units(const int32_t* n_h, const int32_t* n_e, int32_t n_slots, int32_t tile_i,
                    int32_t grid, int32_t allow_split, int32_t max_units, int64_t partial_cap,
-                   cts_unit_t* out, int32_t* n_out, int64_t* partial_floats) {
-  if (!n_h || !n_e || !out || !n_out || !partial_floats) return -1;
+                   cts_unit_t* out, int32_t* n_out, int32_t* cta_begin,
+                   int64_t* partial_floats) {
+  if (!n_h || !n_e || !out || !n_out || !partial_floats || !cta_begin) return -1;
   std::vector<cts::UnitPlan> units;
+  std::vector<int32_t> begin;
   const int rc = cts::plan_units(n_h, n_e, n_slots, tile_i, grid, allow_split != 0, max_units,
-                                 partial_cap, &units, partial_floats);
+                                 partial_cap, &units, &begin, partial_floats, allow_split == 2);
   if (rc != 0) return rc;
   for (size_t k = 0; k < units.size(); ++k) {
     const cts::UnitPlan& u = units[k];
     out[k] = cts_unit_t{u.slot, u.spec, u.i0, u.ni, u.j0, u.j1, u.split, u.nsplit, u.iblock,
                         u.pbase};
   }
+  for (size_t g = 0; g < begin.size(); ++g) cta_begin[g] = begin[g];
   *n_out = (int32_t)units.size();
   return 0;
 }

@@ -6,17 +6,21 @@
 
 namespace cts {
 
-constexpr int kPlanMinJ = 1024;     // smallest j range of a split (one smem stage)
-constexpr int kPlanMaxSplit = 16;   // most j splits of one i tile
+constexpr int kPlanMinJ = 256;       // shortest j range of a tile piece
+constexpr int kPlanMaxPieces = 32;   // most pieces one tile is cut into
 constexpr int64_t kArenaAlign = 32; // arena entries are handed out in multiples of this
 
 struct UnitPlan {
   int32_t slot, spec, i0, ni, j0, j1, split, nsplit, iblock, pbase;
 };
 
+// Static mode: cta_begin receives grid + 1 offsets, CTA g runs units
+// [begin[g], begin[g+1]).  Dynamic mode: units form one queue (largest first)
+// that CTAs pull from with an atomic counter; cta_begin is all zeros except
+// begin[grid] = number of units.
 int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, int grid,
                bool allow_split, int max_units, int64_t partial_cap, std::vector<UnitPlan>* out,
-               int64_t* partial_floats);
+               std::vector<int32_t>* cta_begin, int64_t* partial_floats, bool dynamic);
 
 class ArenaAllocator {
  public:

@@ -30,7 +30,9 @@ constexpr int kErrBounds = 4;     // index outside its slot (checked build)
 
 constexpr float kParked = 1.0e18f;  // shadow coordinate of retired carriers
 constexpr int kChunkJ = 1024;       // j entries per shared-memory stage
+constexpr int kFoldJ = 256;         // sources summed in plain FP32 before a Kahan fold
 constexpr int kMaxK = 256;          // largest chunk (steps per host check)
+constexpr int kMaxGrid = 8192;      // largest persistent grid
 
 // Derived physical constants (all in um, ns, V).
 struct Phys {
@@ -124,13 +126,15 @@ struct StepArgs {
   Arena A;
   SlotDev* slots;
   const Unit* units;
-  const int32_t* n_units;
-  int32_t* unit_counter;     // [K]
+  const int32_t* cta_begin;  // [grid + 1]: CTA g runs units [cta_begin[g], cta_begin[g+1])
+  int32_t* unit_counter;     // [K]: dynamic queue position per step (dynamic plans)
+  int32_t dynamic;           // 1: pull units from unit_counter instead of cta_begin
   int32_t* ret;              // [K][S][2]
-  float* partial;            // j-split partial sums
+  double* partial;           // FP64 accumulators of split tiles (3 x tile_i each, kept zero)
   int32_t* combine_count;    // per i-block
   float* field_out;          // FIELD_ONLY output, SoA [3][capacity]
   int32_t* err;              // global error bits
+  unsigned long long* trace; // optional: per CTA {smid, t_start, t_end, pairs} (ns)
   Phys ph;
   int32_t S;                 // slot count
   int32_t fused;             // 1: update positions; 0: write field_out
@@ -141,6 +145,8 @@ struct Variant {
   int nt;       // threads per CTA
   int r;        // i's per thread
   const char* name;
+  int ctas_per_sm;  // 0: as many as fit; else a fixed count
+  int dynamic;      // 1: guided dynamic queue; 0: static equal shares
 };
 int variant_count();
 Variant variant_info(int v);

@@ -90,14 +90,13 @@ __device__ __forceinline__ double mobility_d(const Phys& ph, int spec, double E)
 }
 
 // Frame anchor of a species for the next step: the drift-only motion of the
-// cloud centre.  One body (noinline, explicit rounding) so every CTA that
-// evaluates it for a slot gets the same bits.
+// cloud centre (its displacement in FP32, accumulated in FP64).  One body
+// (noinline) so every CTA that evaluates it for a slot gets the same bits.
 __device__ __noinline__ double anchor_next(const Phys& ph, int spec, double z) {
   if (!ph.drift) return z;
-  const double E = __dsub_rn(ph.ea, __dmul_rn(ph.eb, z));
-  const double v = __dmul_rn(mobility_d(ph, spec, E), E);
-  const double dz = __dmul_rn(v, ph.dt);
-  const double zn = spec == 0 ? __dsub_rn(z, dz) : __dadd_rn(z, dz);
+  const float E = ph.f_ea - ph.f_eb * (float)z;
+  const float dz = mobility_f(ph, spec, E) * E * ph.f_dt;
+  const double zn = spec == 0 ? __dsub_rn(z, (double)dz) : __dadd_rn(z, (double)dz);
   return fmin(fmax(zn, 0.0), ph.H);
 }
 
@@ -149,17 +148,18 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
+
 // The pair loop over n staged sources: acc_i += (r_i - r_j) / (|r_i - r_j|^2 +
 // eps^2)^(3/2), or the reversed difference for sources of the opposite sign.
-template <int R, bool NEG>
+template <int R, bool NEG, int JU>
 __device__ __forceinline__ void pair_chunk(const float4* __restrict__ sj, int n,
                                            const float (&xi)[R], const float (&yi)[R],
                                            const float (&zi)[R], float (&ax)[R], float (&ay)[R],
                                            float (&az)[R], float eps2) {
   int j = 0;
-  for (; j + 2 <= n; j += 2) {
+  for (; j + JU <= n; j += JU) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < JU; ++h) {
       const float4 q = sj[j + h];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -188,6 +188,41 @@ __device__ __forceinline__ void pair_chunk(const float4* __restrict__ sj, int n,
       ax[r] = fmaf(dx, w, ax[r]);
       ay[r] = fmaf(dy, w, ay[r]);
       az[r] = fmaf(dz, w, az[r]);
+    }
+  }
+}
+
+// The same pair loop on packed FP32 pairs (two i's per 64-bit register pair,
+// Blackwell's two-wide FMA/ADD/MUL): half the FP32 instruction issues.
+// Differences come from one rounding of x_j * (-1) + x_i, i.e. exactly the
+// rounded x_i - x_j of the scalar loop.
+template <int P, bool NEG, int JU>
+__device__ __forceinline__ void pair_chunk_packed(const float4* __restrict__ sj, int n,
+                                                  const float2 (&xi)[P], const float2 (&yi)[P],
+                                                  const float2 (&zi)[P], float2 (&ax)[P],
+                                                  float2 (&ay)[P], float2 (&az)[P],
+                                                  float eps2s) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 eps2 = make_float2(eps2s, eps2s);
+#pragma unroll JU
+  for (int j = 0; j < n; ++j) {
+    const float4 q = sj[j];
+    const float2 qx = make_float2(q.x, q.x);
+    const float2 qy = make_float2(q.y, q.y);
+    const float2 qz = make_float2(q.z, q.z);
+#pragma unroll
+    for (int r = 0; r < P; ++r) {
+      const float2 dx = NEG ? __ffma2_rn(xi[r], m1, qx) : __ffma2_rn(qx, m1, xi[r]);
+      const float2 dy = NEG ? __ffma2_rn(yi[r], m1, qy) : __ffma2_rn(qy, m1, yi[r]);
+      const float2 dz = NEG ? __ffma2_rn(zi[r], m1, qz) : __ffma2_rn(qz, m1, zi[r]);
+      float2 r2 = __ffma2_rn(dz, dz, eps2);
+      r2 = __ffma2_rn(dy, dy, r2);
+      r2 = __ffma2_rn(dx, dx, r2);
+      const float2 rs = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+      const float2 w = __fmul2_rn(__fmul2_rn(rs, rs), rs);
+      ax[r] = __ffma2_rn(dx, w, ax[r]);
+      ay[r] = __ffma2_rn(dy, w, ay[r]);
+      az[r] = __ffma2_rn(dz, w, az[r]);
     }
   }
 }
@@ -282,13 +317,14 @@ __device__ __forceinline__ void active_counts(const StepArgs& a, const SlotDev* 
 // ---------------------------------------------------------------------------
 // The step kernel.
 // ---------------------------------------------------------------------------
-template <int NT, int R>
-__global__ void __launch_bounds__(NT) step_kernel(StepArgs a, int k) {
+template <int NT, int R, bool PACKED, int JU, int MINB>
+__global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
   constexpr int TI = NT * R;
+  static_assert(!PACKED || R % 2 == 0, "packed variants pair i's two by two");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float4* stage = reinterpret_cast<float4*>(smem_raw);  // [2][kChunkJ]
   __shared__ __align__(8) uint64_t bar[2];
-  __shared__ int s_u, s_skip, s_last, s_nah, s_nae, s_step;
+  __shared__ int s_skip, s_last, s_nah, s_nae, s_step;
   __shared__ double s_azn[2];
   __shared__ float s_off;
 
@@ -301,15 +337,24 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a, int k) {
   __syncthreads();
   uint32_t uses[2] = {0u, 0u};
   bool failed = false;
-  const int n_units = *a.n_units;
   const float eps2 = a.ph.f_eps2;
-
+  unsigned long long t_start = 0, pairs_done = 0;
+  if (a.trace && tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+  // this CTA's share of the step's pair work: a static equal-cost range, or
+  // pieces pulled from the step's queue
+  __shared__ int s_u;
+  const int u_begin = a.dynamic ? 0 : a.cta_begin[blockIdx.x];
+  const int u_end = a.dynamic ? a.cta_begin[gridDim.x] : a.cta_begin[blockIdx.x + 1];
+  int u = u_begin;
   for (;;) {
-    if (tid == 0) s_u = atomicAdd(&a.unit_counter[k], 1);
-    __syncthreads();
-    const int u = s_u;
-    if (u >= n_units) break;
+    if (a.dynamic) {
+      if (tid == 0) s_u = atomicAdd(&a.unit_counter[k], 1);
+      __syncthreads();
+      u = s_u;
+    }
+    if (u >= u_end) break;
     const Unit U = a.units[u];
+    if (!a.dynamic) ++u;
     SlotDev* S = a.slots + U.slot;
     if (tid == 0) {
       int nah, nae;
@@ -338,6 +383,7 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a, int k) {
     const float4* __restrict__ shin = a.A.sh[p];
     const int64_t ibase = S->base + (U.spec ? S->cap_h : 0);
     const int nh = S->n_h, ne = S->n_e;
+    pairs_done += (unsigned long long)U.ni * (unsigned long long)(U.j1 - U.j0);
 
     float xi[R], yi[R], zi[R];
 #pragma unroll
@@ -405,19 +451,47 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a, int k) {
             zi[r] = U.spec ? zq : zq - s_off;
           }
         }
-        float tx[R], ty[R], tz[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) tx[r] = ty[r] = tz[r] = 0.0f;
         const float4* sj = stage + st * kChunkJ;
-        if (c < nch_h)
-          pair_chunk<R, false>(sj, cnt, xi, yi, zi, tx, ty, tz, eps2);
-        else
-          pair_chunk<R, true>(sj, cnt, xi, yi, zi, tx, ty, tz, eps2);
+        // plain FP32 sums over at most kFoldJ sources, then a Kahan fold
+        for (int sub = 0; sub < cnt; sub += kFoldJ) {
+          const int m = min(kFoldJ, cnt - sub);
+          float tx[R], ty[R], tz[R];
+          if constexpr (PACKED) {
+            constexpr int P = R / 2;
+            float2 px2[P], py2[P], pz2[P], ax2[P], ay2[P], az2[P];
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          kahan_add(sx[r], cx[r], tx[r]);
-          kahan_add(sy[r], cy[r], ty[r]);
-          kahan_add(sz[r], cz[r], tz[r]);
+            for (int q = 0; q < P; ++q) {
+              px2[q] = make_float2(xi[2 * q], xi[2 * q + 1]);
+              py2[q] = make_float2(yi[2 * q], yi[2 * q + 1]);
+              pz2[q] = make_float2(zi[2 * q], zi[2 * q + 1]);
+              ax2[q] = ay2[q] = az2[q] = make_float2(0.0f, 0.0f);
+            }
+            if (c < nch_h)
+              pair_chunk_packed<P, false, JU>(sj + sub, m, px2, py2, pz2, ax2, ay2, az2,
+                                                   eps2);
+            else
+              pair_chunk_packed<P, true, JU>(sj + sub, m, px2, py2, pz2, ax2, ay2, az2,
+                                                  eps2);
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+              tx[2 * q] = ax2[q].x; tx[2 * q + 1] = ax2[q].y;
+              ty[2 * q] = ay2[q].x; ty[2 * q + 1] = ay2[q].y;
+              tz[2 * q] = az2[q].x; tz[2 * q + 1] = az2[q].y;
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) tx[r] = ty[r] = tz[r] = 0.0f;
+            if (c < nch_h)
+              pair_chunk<R, false, JU>(sj + sub, m, xi, yi, zi, tx, ty, tz, eps2);
+            else
+              pair_chunk<R, true, JU>(sj + sub, m, xi, yi, zi, tx, ty, tz, eps2);
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            kahan_add(sx[r], cx[r], tx[r]);
+            kahan_add(sy[r], cy[r], ty[r]);
+            kahan_add(sz[r], cz[r], tz[r]);
+          }
         }
         __syncthreads();
       }
@@ -432,13 +506,19 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a, int k) {
     }
 
     if (U.nsplit > 1) {
-      float* part = a.partial + U.pbase + (int64_t)U.split * 3 * TI;
+      // Add the piece's compensated sum (S - c of two FP32 values is exact in
+      // FP64) into the tile's FP64 accumulators; the CTA finishing the tile's
+      // last piece reads them once, clears them for the next step and goes on
+      // to the update.
+      double* acc = a.partial + U.pbase;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int li = r * NT + tid;
-        part[li] = vx[r];
-        part[TI + li] = vy[r];
-        part[2 * TI + li] = vz[r];
+        if (li < U.ni) {
+          atomicAdd(acc + li, (double)sx[r] - (double)cx[r]);
+          atomicAdd(acc + TI + li, (double)sy[r] - (double)cy[r]);
+          atomicAdd(acc + 2 * TI + li, (double)sz[r] - (double)cz[r]);
+        }
       }
       __threadfence();
       __syncthreads();
@@ -456,16 +536,14 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a, int k) {
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int li = r * NT + tid;
-        double bx = 0.0, by = 0.0, bz = 0.0;
-        for (int s = 0; s < U.nsplit; ++s) {
-          const float* q = a.partial + U.pbase + (int64_t)s * 3 * TI;
-          bx += (double)__ldcg(q + li);
-          by += (double)__ldcg(q + TI + li);
-          bz += (double)__ldcg(q + 2 * TI + li);
+        if (li < U.ni) {
+          vx[r] = (float)__ldcg(acc + li);
+          vy[r] = (float)__ldcg(acc + TI + li);
+          vz[r] = (float)__ldcg(acc + 2 * TI + li);
+          acc[li] = 0.0;
+          acc[TI + li] = 0.0;
+          acc[2 * TI + li] = 0.0;
         }
-        vx[r] = (float)bx;
-        vy[r] = (float)by;
-        vz[r] = (float)bz;
       }
     }
 
@@ -492,6 +570,17 @@ __global__ void __launch_bounds__(NT) step_kernel(StepArgs a, int k) {
       }
     }
     __syncthreads();
+  }
+  if (a.trace && tid == 0) {
+    unsigned long long t_end;
+    unsigned smid;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    unsigned long long* t = a.trace + 4 * (size_t)blockIdx.x;
+    t[0] = smid;
+    t[1] = t_start;
+    t[2] = t_end;
+    t[3] = pairs_done;
   }
 }
 
@@ -851,15 +940,25 @@ struct VariantEntry {
   int nt, r;
   const char* name;
   void (*fn)(StepArgs, int);
+  int ctas_per_sm, dynamic;
 };
 
+// (threads, i's per thread, packed f32x2, j unroll, min CTAs per SM [register
+// cap], CTAs per SM launched [0 = all that fit], dynamic queue).  Entry 0 is
+// the default: packed FP32 pairs, 512-carrier tiles, guided dynamic queue.
+#define CTS_V(NT, R, PK, JU, MB, CPS, DYN, NAME) \
+  {NT, R, NAME, step_kernel<NT, R, PK, JU, MB>, CPS, DYN}
 const VariantEntry kVariants[] = {
-    {128, 4, "nt128_r4", step_kernel<128, 4>},
-    {256, 4, "nt256_r4", step_kernel<256, 4>},
-    {128, 8, "nt128_r8", step_kernel<128, 8>},
-    {256, 2, "nt256_r2", step_kernel<256, 2>},
-    {64, 8, "nt64_r8", step_kernel<64, 8>},
+    CTS_V(128, 4, true, 4, 4, 0, 1, "nt128_r4_f32x2_u4_dyn"),
+    CTS_V(128, 2, true, 4, 6, 0, 1, "nt128_r2_f32x2_u4_dyn"),
+    CTS_V(256, 2, true, 4, 3, 0, 1, "nt256_r2_f32x2_u4_dyn"),
+    CTS_V(128, 4, true, 4, 4, 0, 0, "nt128_r4_f32x2_u4_static"),
+    CTS_V(512, 2, true, 4, 1, 1, 0, "nt512_r2_f32x2_u4_1sm_static"),
+    CTS_V(128, 4, false, 2, 6, 0, 1, "nt128_r4_scalar_dyn"),
+    CTS_V(256, 2, false, 4, 3, 0, 1, "nt256_r2_scalar_u4_dyn"),
+    CTS_V(256, 2, false, 2, 4, 0, 0, "nt256_r2_scalar_static"),
 };
+#undef CTS_V
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr size_t kStageBytes = 2 * kChunkJ * sizeof(float4);
 
@@ -869,7 +968,7 @@ int variant_count() { return kNumVariants; }
 
 Variant variant_info(int v) {
   const VariantEntry& e = kVariants[v];
-  return Variant{e.nt, e.r, e.name};
+  return Variant{e.nt, e.r, e.name, e.ctas_per_sm, e.dynamic};
 }
 
 size_t variant_smem(int) { return kStageBytes; }

@@ -37,8 +37,8 @@ constexpr int64_t kDefaultBudget = 1ll << 30;
 constexpr int kMaxUnits = 1 << 16;
 constexpr int kDefaultQueue = 1 << 16;
 // arena (positions, two shadows, id, collection point, step, state), explicit
-// staging, j-split partial sums (12 floats) and the PLAIN field buffer
-constexpr int64_t kBytesPerCarrier = 24 + 32 + 4 + 16 + 4 + 1 + 32 + 48 + 12;
+// staging, split-tile accumulators (3 doubles) and the PLAIN field buffer
+constexpr int64_t kBytesPerCarrier = 24 + 32 + 4 + 16 + 4 + 1 + 32 + 24 + 12;
 
 struct EventRec {
   sim_event_t ev{};
@@ -85,7 +85,7 @@ struct sim_t {
   int device = 0, sm_count = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  int S = 0, K = 0, variant = 0, grid = 0, tile_i = 0;
+  int S = 0, K = 0, variant = 0, grid = 0, tile_i = 0, dynamic = 0;
   int64_t capacity = 0, partial_cap = 0;
   bool broken = false;
   std::string err;
@@ -97,10 +97,10 @@ struct sim_t {
   SlotReadout* d_readout = nullptr;
   int32_t* d_pixels = nullptr;
   Unit* d_units = nullptr;
-  int32_t* d_n_units = nullptr;
+  int32_t* d_cta_begin = nullptr;
   int32_t* d_unit_counter = nullptr;
   int32_t* d_ret = nullptr;
-  float* d_partial = nullptr;
+  double* d_partial = nullptr;
   int32_t* d_combine = nullptr;
   int32_t* d_err = nullptr;
   float* d_field = nullptr;
@@ -109,18 +109,20 @@ struct sim_t {
   // pinned host staging
   SlotSummary* h_summary = nullptr;
   Unit* h_units = nullptr;
-  int32_t* h_n_units = nullptr;
+  int32_t* h_cta_begin = nullptr;
   int32_t* h_list = nullptr;
   SlotDev* h_slotdev = nullptr;
   SlotReadout* h_readout = nullptr;
   int32_t* h_pixels = nullptr;
   int32_t* h_err = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> lev;  // per-launch events (time_launches): K + 1
 
   // host state
   std::vector<HostSlot> slots;
   ArenaAllocator alloc;
   std::vector<UnitPlan> plan;
+  std::vector<int32_t> plan_begin;
   std::mutex qmu;
   std::condition_variable qcv;
   std::deque<EventRec> queue;
@@ -141,7 +143,8 @@ struct sim_t {
   // stats
   int64_t st_events = 0, st_inter = 0, st_steps = 0, st_launch = 0, st_chunks = 0,
           st_rejected = 0;
-  double st_ms = 0.0;
+  double st_ms = 0.0, st_kernel_ms = 0.0;
+  int64_t st_kernel_launches = 0, st_h2d = 0, st_d2h = 0;
 };
 
 namespace {
@@ -155,6 +158,16 @@ namespace {
       return SIM_ECUDA;                                                            \
     }                                                                              \
   } while (0)
+
+// Host<->device copies of the library, counted for the statistics.
+cudaError_t h2d(sim_t* s, void* dst, const void* src, size_t bytes) {
+  s->st_h2d += (int64_t)bytes;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s->stream);
+}
+cudaError_t d2h(sim_t* s, void* dst, const void* src, size_t bytes) {
+  s->st_d2h += (int64_t)bytes;
+  return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream);
+}
 
 bool finite_all(std::initializer_list<double> v) {
   for (double x : v)
@@ -331,13 +344,12 @@ int place_event(sim_t* s, int slot, EventRec&& r, int64_t base) {
       d.depth_um = s->sensor.thickness_um - cz / r.n_pairs;
     }
     if (!rec.empty())
-      CK(cudaMemcpyAsync(s->d_explicit + base, rec.data(), rec.size() * sizeof(ExplicitRec),
-                         cudaMemcpyHostToDevice, s->stream));
+      CK(h2d(s, s->d_explicit + base, rec.data(), rec.size() * sizeof(ExplicitRec)));
     // keep the staging alive until the copy is done
     CK(cudaStreamSynchronize(s->stream));
   }
   h.rec = std::move(r);
-  CK(cudaMemcpyAsync(s->d_slots + slot, &d, sizeof(SlotDev), cudaMemcpyHostToDevice, s->stream));
+  CK(h2d(s, s->d_slots + slot, &d, sizeof(SlotDev)));
   return SIM_OK;
 }
 
@@ -368,8 +380,7 @@ int launch_inits(sim_t* s) {
       s->slots[k].needs_init = false;
     }
   if (!n) return SIM_OK;
-  CK(cudaMemcpyAsync(s->d_list, s->h_list, n * sizeof(int32_t), cudaMemcpyHostToDevice,
-                     s->stream));
+  CK(h2d(s, s->d_list, s->h_list, n * sizeof(int32_t)));
   CK(launch_init(s->ph, s->A, s->d_slots, s->d_list, n, s->d_explicit, s->stream));
   // keep h_list stable until the copy has been consumed
   CK(cudaStreamSynchronize(s->stream));
@@ -377,13 +388,20 @@ int launch_inits(sim_t* s) {
   return SIM_OK;
 }
 
+bool capturing(sim_t* s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s->stream, &st);
+  return st == cudaStreamCaptureStatusActive;
+}
+
 StepArgs step_args(sim_t* s, bool fused) {
   StepArgs a{};
   a.A = s->A;
   a.slots = s->d_slots;
   a.units = s->d_units;
-  a.n_units = s->d_n_units;
+  a.cta_begin = s->d_cta_begin;
   a.unit_counter = s->d_unit_counter;
+  a.dynamic = s->dynamic;
   a.ret = s->d_ret;
   a.partial = s->d_partial;
   a.combine_count = s->d_combine;
@@ -404,9 +422,10 @@ int upload_units(sim_t* s, bool allow_split) {
       ne[k] = s->slots[k].n_e;
     }
   int64_t pfl = 0;
-  const int rc = plan_units(nh.data(), ne.data(), s->S, s->tile_i, s->grid,
-                            allow_split && s->ph.repulsion, kMaxUnits, s->partial_cap, &s->plan,
-                            &pfl);
+  const bool split = allow_split && s->ph.repulsion;
+  const int rc = plan_units(nh.data(), ne.data(), s->S, s->tile_i, s->grid, split, kMaxUnits,
+                            s->partial_cap, &s->plan, &s->plan_begin, &pfl,
+                            split && s->dynamic);
   if (rc != 0) {
     s->err = "unit plan does not fit the unit buffer";
     return SIM_EINVAL;
@@ -414,11 +433,9 @@ int upload_units(sim_t* s, bool allow_split) {
   const int n = (int)s->plan.size();
   static_assert(sizeof(UnitPlan) == sizeof(Unit), "unit layout");
   std::memcpy(s->h_units, s->plan.data(), n * sizeof(Unit));
-  *s->h_n_units = n;
-  CK(cudaMemcpyAsync(s->d_units, s->h_units, std::max(n, 1) * sizeof(Unit),
-                     cudaMemcpyHostToDevice, s->stream));
-  CK(cudaMemcpyAsync(s->d_n_units, s->h_n_units, sizeof(int32_t), cudaMemcpyHostToDevice,
-                     s->stream));
+  std::memcpy(s->h_cta_begin, s->plan_begin.data(), (s->grid + 1) * sizeof(int32_t));
+  CK(h2d(s, s->d_units, s->h_units, std::max(n, 1) * sizeof(Unit)));
+  CK(h2d(s, s->d_cta_begin, s->h_cta_begin, (s->grid + 1) * sizeof(int32_t)));
   return SIM_OK;
 }
 
@@ -435,15 +452,21 @@ int issue_chunk(sim_t* s, int K) {
     s->st_launch += 2;
   } else {
     const StepArgs a = step_args(s, true);
-    for (int k = 0; k < K; ++k) CK(launch_step(s->variant, a, k, s->grid, s->stream));
+    const bool timed = s->opt.time_launches != 0;
+    // inside a stream capture the events become external event-record nodes
+    const unsigned evflag = capturing(s) ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (timed) CK(cudaEventRecordWithFlags(s->lev[0], s->stream, evflag));
+    for (int k = 0; k < K; ++k) {
+      CK(launch_step(s->variant, a, k, s->grid, s->stream));
+      if (timed) CK(cudaEventRecordWithFlags(s->lev[k + 1], s->stream, evflag));
+    }
     s->st_launch += K;
   }
   CK(launch_close(s->ph, s->A, s->d_slots, nullptr, s->S, s->d_ret, s->S, K, s->d_summary,
                   s->stream));
   s->st_launch += 1;
-  CK(cudaMemcpyAsync(s->h_summary, s->d_summary, s->S * sizeof(SlotSummary),
-                     cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaMemcpyAsync(s->h_err, s->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  CK(d2h(s, s->h_summary, s->d_summary, s->S * sizeof(SlotSummary)));
+  CK(d2h(s, s->h_err, s->d_err, sizeof(int32_t)));
   return SIM_OK;
 }
 
@@ -455,8 +478,7 @@ int run_chunk(sim_t* s) {
     int n = 0;
     for (int k = 0; k < s->S; ++k)
       if (s->slots[k].used && s->slots[k].running) s->h_list[n++] = k;
-    CK(cudaMemcpyAsync(s->d_list, s->h_list, std::max(n, 1) * sizeof(int32_t),
-                       cudaMemcpyHostToDevice, s->stream));
+    CK(h2d(s, s->d_list, s->h_list, std::max(n, 1) * sizeof(int32_t)));
   }
   int rc = upload_units(s, !plain);
   if (rc) return rc;
@@ -469,9 +491,11 @@ int run_chunk(sim_t* s) {
       }
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-      const int64_t launches = s->st_launch;
+      const int64_t launches = s->st_launch, hb = s->st_h2d, db = s->st_d2h;
       rc = issue_chunk(s, K);
       s->st_launch = launches;
+      s->st_h2d = hb;
+      s->st_d2h = db;
       cudaError_t ce = cudaStreamEndCapture(s->stream, &g);
       if (rc) return rc;
       CK(ce);
@@ -483,6 +507,7 @@ int run_chunk(sim_t* s) {
     }
     CK(cudaGraphLaunch(s->graph, s->stream));
     s->st_launch += K + 1;
+    s->st_d2h += (int64_t)s->S * sizeof(SlotSummary) + sizeof(int32_t);
   } else {
     rc = issue_chunk(s, K);
     if (rc) return rc;
@@ -492,6 +517,14 @@ int run_chunk(sim_t* s) {
   float ms = 0.f;
   CK(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
   s->st_ms += ms;
+  if (s->opt.time_launches && !plain) {
+    for (int k = 0; k < K; ++k) {
+      float lm = 0.f;
+      CK(cudaEventElapsedTime(&lm, s->lev[k], s->lev[k + 1]));
+      s->st_kernel_ms += lm;
+    }
+    s->st_kernel_launches += K;
+  }
   s->st_steps += K;
   s->st_chunks += 1;
   if (*s->h_err & kErrTimeout) {
@@ -511,10 +544,9 @@ int fetch_results(sim_t* s, const std::vector<int>& fin) {
   std::vector<std::vector<int32_t>> rs(fin.size());
   for (size_t q = 0; q < fin.size(); ++q) {
     const int slot = fin[q];
-    CK(cudaMemcpyAsync(s->h_pixels + (int64_t)slot * npix, s->d_pixels + (int64_t)slot * npix,
-                       npix * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaMemcpyAsync(s->h_readout + slot, s->d_readout + slot, sizeof(SlotReadout),
-                       cudaMemcpyDeviceToHost, s->stream));
+    CK(d2h(s, s->h_pixels + (int64_t)slot * npix, s->d_pixels + (int64_t)slot * npix,
+           npix * sizeof(int32_t)));
+    CK(d2h(s, s->h_readout + slot, s->d_readout + slot, sizeof(SlotReadout)));
     if (keep) {
       const HostSlot& h = s->slots[slot];
       const int n = h.rec.cap_h + h.rec.cap_e;
@@ -522,12 +554,9 @@ int fetch_results(sim_t* s, const std::vector<int>& fin) {
       fy[q].resize(n);
       rs[q].resize(n);
       if (n) {
-        CK(cudaMemcpyAsync(fx[q].data(), s->A.fx + h.base, n * sizeof(double),
-                           cudaMemcpyDeviceToHost, s->stream));
-        CK(cudaMemcpyAsync(fy[q].data(), s->A.fy + h.base, n * sizeof(double),
-                           cudaMemcpyDeviceToHost, s->stream));
-        CK(cudaMemcpyAsync(rs[q].data(), s->A.rstep + h.base, n * sizeof(int32_t),
-                           cudaMemcpyDeviceToHost, s->stream));
+        CK(d2h(s, fx[q].data(), s->A.fx + h.base, n * sizeof(double)));
+        CK(d2h(s, fy[q].data(), s->A.fy + h.base, n * sizeof(double)));
+        CK(d2h(s, rs[q].data(), s->A.rstep + h.base, n * sizeof(int32_t)));
       }
     }
   }
@@ -622,8 +651,7 @@ int pump(sim_t* s, bool defer, bool* progressed) {
   }
   if (fin.empty()) return SIM_OK;
   for (size_t q = 0; q < fin.size(); ++q) s->h_list[q] = fin[q];
-  CK(cudaMemcpyAsync(s->d_list, s->h_list, fin.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
-                     s->stream));
+  CK(h2d(s, s->d_list, s->h_list, fin.size() * sizeof(int32_t)));
   CK(launch_bin(s->ph, s->A, s->d_slots, s->d_list, (int)fin.size(), s->d_pixels, s->d_readout,
                 s->stream));
   s->st_launch += 1;
@@ -727,7 +755,7 @@ int alloc_all(sim_t* s) {
   AL(s->d_readout, s->S);
   AL(s->d_pixels, (int64_t)s->S * s->sensor.grid_n * s->sensor.grid_n);
   AL(s->d_units, kMaxUnits);
-  AL(s->d_n_units, 1);
+  AL(s->d_cta_begin, kMaxGrid + 1);
   AL(s->d_unit_counter, kMaxK);
   AL(s->d_ret, (int64_t)kMaxK * s->S * 2);
   AL(s->d_partial, s->partial_cap);
@@ -738,7 +766,7 @@ int alloc_all(sim_t* s) {
   if (s->opt.mode == CTS_MODE_PLAIN) AL(s->d_field, 3 * C);
   HL(s->h_summary, s->S);
   HL(s->h_units, kMaxUnits);
-  HL(s->h_n_units, 1);
+  HL(s->h_cta_begin, kMaxGrid + 1);
   HL(s->h_list, s->S);
   HL(s->h_slotdev, s->S);
   HL(s->h_readout, s->S);
@@ -748,9 +776,12 @@ int alloc_all(sim_t* s) {
 #undef HL
   CK(cudaMemset(s->d_slots, 0, s->S * sizeof(SlotDev)));
   CK(cudaMemset(s->d_combine, 0, kMaxUnits * sizeof(int32_t)));
+  CK(cudaMemset(s->d_partial, 0, std::max<int64_t>(s->partial_cap, 1) * sizeof(double)));
   CK(cudaMemset(s->d_err, 0, sizeof(int32_t)));
   CK(cudaEventCreate(&s->ev0));
   CK(cudaEventCreate(&s->ev1));
+  s->lev.assign(kMaxK + 1, nullptr);
+  for (auto& e : s->lev) CK(cudaEventCreate(&e));
   return SIM_OK;
 }
 
@@ -758,16 +789,18 @@ void free_all(sim_t* s) {
   if (s->graph) cudaGraphExecDestroy(s->graph);
   void* dev[] = {s->A.px, s->A.py, s->A.pz, s->A.sh[0], s->A.sh[1], s->A.cid, s->A.fx, s->A.fy,
                  s->A.rstep, s->A.cstate, s->d_slots, s->d_summary, s->d_readout, s->d_pixels,
-                 s->d_units, s->d_n_units, s->d_unit_counter, s->d_ret, s->d_partial,
+                 s->d_units, s->d_cta_begin, s->d_unit_counter, s->d_ret, s->d_partial,
                  s->d_combine, s->d_err, s->d_field, s->d_explicit, s->d_list};
   for (void* p : dev)
     if (p) cudaFree(p);
-  void* host[] = {s->h_summary, s->h_units, s->h_n_units, s->h_list, s->h_slotdev, s->h_readout,
+  void* host[] = {s->h_summary, s->h_units, s->h_cta_begin, s->h_list, s->h_slotdev, s->h_readout,
                   s->h_pixels, s->h_err};
   for (void* p : host)
     if (p) cudaFreeHost(p);
   if (s->ev0) cudaEventDestroy(s->ev0);
   if (s->ev1) cudaEventDestroy(s->ev1);
+  for (auto e : s->lev)
+    if (e) cudaEventDestroy(e);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -782,10 +815,12 @@ int set_variant(sim_t* s, int v) {
   int occ = 0;
   CK(variant_occupancy(v, &occ));
   if (occ < 1) occ = 1;
-  s->variant = v;
-  s->grid = s->sm_count * occ;
   const Variant vi = variant_info(v);
+  if (vi.ctas_per_sm > 0) occ = std::min(occ, vi.ctas_per_sm);
+  s->variant = v;
+  s->grid = std::min(s->sm_count * occ, kMaxGrid);
   s->tile_i = vi.nt * vi.r;
+  s->dynamic = vi.dynamic;
   return SIM_OK;
 }
 
@@ -846,7 +881,7 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
   const int64_t budget = opt.hbm_budget_bytes > 0 ? opt.hbm_budget_bytes : kDefaultBudget;
   s->capacity = opt.max_carriers > 0 ? opt.max_carriers : std::max<int64_t>(budget / kBytesPerCarrier, 1024);
   if (s->capacity > (1ll << 28)) s->capacity = 1ll << 28;
-  s->partial_cap = std::min<int64_t>(3 * 4 * (s->capacity + 4096), 64ll << 20);
+  s->partial_cap = std::min<int64_t>(3 * (s->capacity + 64 * 4096), 64ll << 20);
   s->slots.resize(s->S);
   s->alloc = ArenaAllocator(s->capacity);
   if (opt.stream) {
@@ -1132,6 +1167,10 @@ int sim_get_stats(sim_t* s, sim_stats_t* o) {
   o->sm_count = s->sm_count;
   o->variant = s->variant;
   o->device_ms = s->st_ms;
+  o->step_kernel_ms = s->st_kernel_ms;
+  o->step_kernel_launches = s->st_kernel_launches;
+  o->h2d_bytes = s->st_h2d;
+  o->d2h_bytes = s->st_d2h;
   return SIM_OK;
 }
 
@@ -1163,10 +1202,11 @@ int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, in
   std::vector<float4> sh((size_t)n);
   for (int c = 0; c < n; ++c) sh[c] = make_float4(x[c], y[c], z[c], 0.0f);
   std::vector<UnitPlan> plan;
+  std::vector<int32_t> begin;
   int64_t pfl = 0;
   const int32_t nh = n_h, ne = n_e;
   if (plan_units(&nh, &ne, 1, t->tile_i, t->grid, t->ph.repulsion != 0, kMaxUnits,
-                 t->partial_cap, &plan, &pfl) != 0)
+                 t->partial_cap, &plan, &begin, &pfl, t->ph.repulsion != 0 && t->dynamic) != 0)
     return SIM_EINVAL;
   int rc = SIM_OK;
   cudaError_t e = cudaSuccess;
@@ -1193,12 +1233,12 @@ int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, in
         cudaSuccess)
       break;
     std::memcpy(s->h_units, plan.data(), plan.size() * sizeof(Unit));
-    *s->h_n_units = (int32_t)plan.size();
-    if ((e = cudaMemcpyAsync(s->d_units, s->h_units, plan.size() * sizeof(Unit),
+    std::memcpy(s->h_cta_begin, begin.data(), begin.size() * sizeof(int32_t));
+    if ((e = cudaMemcpyAsync(s->d_units, s->h_units, std::max<size_t>(plan.size(), 1) * sizeof(Unit),
                              cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
       break;
-    if ((e = cudaMemcpyAsync(s->d_n_units, s->h_n_units, sizeof(int32_t), cudaMemcpyHostToDevice,
-                             s->stream)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(s->d_cta_begin, s->h_cta_begin, begin.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
       break;
     if ((e = cudaMemsetAsync(s->d_unit_counter, 0, sizeof(int32_t), s->stream)) != cudaSuccess)
       break;
@@ -1228,6 +1268,50 @@ int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, in
   if (d_slot) cudaFree(d_slot);
   if (d_field) cudaFree(d_field);
   return rc;
+}
+
+int sim_debug_trace_step(sim_t* s, uint64_t* out, int32_t max_ctas, int32_t* n_ctas) {
+  if (!s || !out || !n_ctas || max_ctas < 0) return SIM_EINVAL;
+  if (s->opt.mode != CTS_MODE_BATCHED) return SIM_ESTATE;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  cudaSetDevice(s->device);
+  int rc = launch_inits(s);
+  if (rc) return rc;
+  bool any = false;
+  for (auto& h : s->slots) any |= h.used && h.running;
+  if (!any) return SIM_ESTATE;
+  rc = upload_units(s, true);
+  if (rc) return rc;
+  float* d_field = nullptr;
+  unsigned long long* d_trace = nullptr;
+  cudaError_t e = cudaSuccess;
+  std::vector<unsigned long long> h((size_t)4 * s->grid);
+  do {
+    if ((e = cudaMalloc(&d_field, 3 * (size_t)s->capacity * sizeof(float)))) break;
+    if ((e = cudaMalloc(&d_trace, h.size() * sizeof(unsigned long long)))) break;
+    if ((e = cudaMemsetAsync(d_trace, 0, h.size() * sizeof(unsigned long long), s->stream))) break;
+    if ((e = cudaMemsetAsync(s->d_ret, 0, (size_t)s->S * 2 * sizeof(int32_t), s->stream))) break;
+    if ((e = cudaMemsetAsync(s->d_unit_counter, 0, sizeof(int32_t), s->stream))) break;
+    StepArgs a = step_args(s, false);
+    a.field_out = d_field;
+    a.trace = d_trace;
+    if ((e = launch_step(s->variant, a, 0, s->grid, s->stream))) break;
+    if ((e = cudaMemcpyAsync(h.data(), d_trace, h.size() * sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, s->stream)))
+      break;
+    if ((e = cudaStreamSynchronize(s->stream))) break;
+  } while (0);
+  if (d_field) cudaFree(d_field);
+  if (d_trace) cudaFree(d_trace);
+  if (e != cudaSuccess) {
+    s->err = cudaGetErrorString(e);
+    return SIM_ECUDA;
+  }
+  const int n = std::min(max_ctas, s->grid);
+  for (int g = 0; g < n; ++g)
+    for (int q = 0; q < 4; ++q) out[4 * g + q] = h[4 * (size_t)g + q];
+  *n_ctas = n;
+  return SIM_OK;
 }
 
 int sim_debug_bin(sim_t* s, const double* x, const double* y, int64_t n, int32_t* pixels,

@@ -360,3 +360,44 @@ def test_injected_faults():
         with pytest.raises(cts.SimError) as e:
             sim.poll(4, 1000)
         assert e.value.code == cts.SIM_ECUDA
+
+
+def _variants():
+    """Every compiled pair-kernel variant (sim_init rejects indices past the last)."""
+    out = []
+    p = W.preset("track_200keV_320um")
+    for v in range(1, 64):
+        rc, h = cts.sim_init(cts.make_sensor(p["sensor"]), cts.make_field(),
+                             cts.make_mobility(p["mobility"]), cts.make_options(variant=v))
+        if rc != 0:
+            break
+        cts.sim_destroy(h)
+        out.append(v)
+    return out
+
+
+def test_every_kernel_variant_matches_the_oracle():
+    vs = _variants()
+    assert len(vs) >= 2
+    rng = np.random.default_rng(12)
+    one = W.random_cloud(5525, 0.83, seed=3).astype(np.float32)
+    h = rng.standard_normal((2000, 3)) * 2.0
+    e = rng.standard_normal((1500, 3)) * 2.0 + np.array([0.3, 0.0, 2.0])
+    two = np.concatenate([h, e]).astype(np.float32)
+    bad = []
+    for v in vs:
+        with sim_for("track_200keV_320um", variant=v) as sim:
+            assert sim.stats()["variant"] == v - 1
+            for xyz, nh, ne in ((one, 5525, 0), (two, 2000, 1500)):
+                try:
+                    _field_check(sim, xyz, nh, ne)
+                except AssertionError as err:
+                    bad.append((v, nh, ne, str(err).splitlines()[0]))
+    assert not bad, bad
+    # and one whole event per variant agrees with the oracle
+    name = "plain_3keV_100um"
+    ev = W.make_events(name, n=1)
+    ref = oracle.run_events(oracle_params(name), ev)[0]
+    for v in vs:
+        with sim_for(name, variant=v) as sim:
+            _compare_events(sim.run(ev)[0], ref, 829)

@@ -121,22 +121,34 @@ def _check_cover(units, n_h, n_e):
 
 
 @pytest.mark.parametrize("n_h,n_e,tile,grid", [
-    ([5525] * 64, [0] * 64, 512, 456),
+    ([5525] * 64, [0] * 64, 512, 912),
+    ([5525] * 16, [0] * 16, 512, 912),
     ([5525], [0], 512, 456),
     ([829, 0, 1381, 6906, 3], [0, 0, 0, 0, 0], 512, 456),
     ([3000, 17], [3000, 5], 256, 300),
+    ([55250] * 2, [55250] * 2, 512, 912),
     ([1], [0], 512, 456),
 ])
-def test_planner_covers_every_pair_once(lib, n_h, n_e, tile, grid):
-    rc, units, pfl = cts.cts_plan_units(n_h, n_e, tile, grid)
+def test_planner_covers_every_pair_once_and_balances(lib, n_h, n_e, tile, grid):
+    rc, units, begin, pfl = cts.cts_plan_units(n_h, n_e, tile, grid)
     assert rc == 0
     assert _check_cover(units, n_h, n_e)
-    # idle slots get no units
-    assert all(n_h[u[0]] > 0 for u in units)
-    # decreasing cost order
+    assert all(n_h[u[0]] > 0 for u in units)          # idle slots get no units
+    # CTA ranges: monotone, cover all units
+    assert begin[0] == 0 and begin[-1] == len(units) and np.all(np.diff(begin) >= 0)
+    # j boundaries of split segments are multiples of 4 (16-byte aligned copies)
+    n_of = {s: n_h[s] + n_e[s] for s in range(len(n_h))}
+    for u in units:
+        assert u[4] % 4 == 0 and (u[5] % 4 == 0 or u[5] == n_of[u[0]])
+    # equal shares: every working CTA gets the same pair count within 4 tiles' j step
     cost = units[:, 3] * (units[:, 5] - units[:, 4])
-    assert np.all(np.diff(cost) <= 0)
-    # split i-blocks: consistent metadata, disjoint partial regions
+    per_cta = np.array([cost[begin[g]:begin[g + 1]].sum() for g in range(grid)])
+    busy = per_cta[per_cta > 0]
+    total = sum((n_h[s] + n_e[s]) ** 2 for s in range(len(n_h)) if n_h[s] > 0)
+    assert per_cta.sum() == total
+    if len(busy) > 1:
+        assert busy.max() - busy.min() <= 2 * 4 * tile + 1, (busy.min(), busy.max())
+    # split tiles: consistent metadata, disjoint partial regions inside pfl
     blocks = {}
     for u in units:
         if u[7] > 1:
@@ -145,7 +157,7 @@ def test_planner_covers_every_pair_once(lib, n_h, n_e, tile, grid):
     for b, us in blocks.items():
         assert sorted(x[6] for x in us) == list(range(us[0][7]))
         assert len({(x[0], x[1], x[2], x[9]) for x in us}) == 1
-        ends.append((us[0][9], us[0][9] + us[0][7] * 3 * tile))
+        ends.append((us[0][9], us[0][9] + 3 * tile))
     ends.sort()
     for (a0, a1), (b0, b1) in zip(ends, ends[1:]):
         assert a1 <= b0
@@ -153,23 +165,22 @@ def test_planner_covers_every_pair_once(lib, n_h, n_e, tile, grid):
         assert ends[-1][1] <= pfl
 
 
-def test_planner_splits_when_few_events(lib):
-    # One 5525-carrier event on 456 CTAs: tiles alone would leave most CTAs idle.
-    rc, units, _ = cts.cts_plan_units([5525], [0], 512, 456)
-    assert rc == 0 and units.shape[0] > 11
-    # Many events: whole tiles already fill the grid, no splits needed.
-    rc, units, pfl = cts.cts_plan_units([5525] * 256, [0] * 256, 512, 456)
-    assert rc == 0 and pfl == 0 and np.all(units[:, 7] == 1)
-    # No splitting allowed
-    rc, units, pfl = cts.cts_plan_units([5525], [0], 512, 456, allow_split=0)
-    assert rc == 0 and pfl == 0 and units.shape[0] == 11
+def test_planner_small_work_uses_fewer_ctas(lib):
+    # 829^2 pairs: shares of >= 65536 pairs -> at most 10 CTAs get work
+    rc, units, begin, _ = cts.cts_plan_units([829], [0], 512, 456)
+    busy = np.count_nonzero(np.diff(begin))
+    assert rc == 0 and 1 <= busy <= 10
+    # no splitting allowed: whole tiles, dealt longest first
+    rc, units, begin, pfl = cts.cts_plan_units([5525], [0], 512, 456, allow_split=0)
+    assert rc == 0 and pfl == 0 and units.shape[0] == 11 and np.all(units[:, 7] == 1)
 
 
 def test_planner_respects_budgets(lib):
-    rc, units, pfl = cts.cts_plan_units([5525] * 4, [0] * 4, 512, 456, partial_cap=3 * 512 * 4)
-    assert rc == 0 and pfl <= 3 * 512 * 4
+    rc, units, begin, pfl = cts.cts_plan_units([5525] * 4, [0] * 4, 512, 456,
+                                               partial_cap=3 * 512 * 4)
+    assert rc == 0 and pfl <= 3 * 512 * 4 and np.count_nonzero(units[:, 7] > 1) > 0
     assert _check_cover(units, [5525] * 4, [0] * 4)
-    rc, _, _ = cts.cts_plan_units([5525] * 64, [0] * 64, 512, 456, max_units=100)
+    rc, _, _, _ = cts.cts_plan_units([5525] * 64, [0] * 64, 512, 456, max_units=100)
     assert rc == -2
 
 
@@ -195,3 +206,18 @@ def test_estimate_steps_matches_eq9(lib):
         t = 1 / (mu0 * 0.1 * 2 * Vd / H ** 2) * math.log(E(0) / E(z0)) + z0 / (vsat * 1e-5)
         est = cts.cts_estimate_steps(H, Vb, Vd, mu0, vsat, 1.0, 10.0, depth)
         assert est == pytest.approx(t / 0.01, rel=1e-4)
+
+
+@pytest.mark.parametrize("n_h,n_e", [([5525] * 64, [0] * 64), ([5525] * 3, [0] * 3),
+                                     ([3000, 900], [2000, 10]), ([829], [0])])
+def test_guided_dynamic_plan(lib, n_h, n_e):
+    # allow_split = 2: one queue of pieces, largest first, shrinking at the end
+    rc, units, begin, pfl = cts.cts_plan_units(n_h, n_e, 512, 608, allow_split=2)
+    assert rc == 0
+    assert _check_cover(units, n_h, n_e)
+    assert begin[-1] == len(units) and np.all(begin[:-1] == 0)
+    cost = units[:, 3] * (units[:, 5] - units[:, 4])
+    assert np.all(np.diff(cost) <= 0)
+    # the smallest pieces are much smaller than the largest when there is enough work
+    if cost.sum() > 608 * 512 * 4096:
+        assert cost[-1] * 8 <= cost[0]
