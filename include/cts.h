@@ -247,6 +247,31 @@ int sim_debug_trajectory(sim_t* sim, const sim_event_t* ev, int64_t n_steps,
  * *n_ctas receives the grid size.  For load-balance studies. */
 int sim_debug_trace_step(sim_t* sim, uint64_t* out, int32_t max_ctas, int32_t* n_ctas);
 
+/* Allocation-free pair field, for callers that cannot allocate device
+ * memory (they work inside another framework's memory pool or under a fixed
+ * device budget, or must avoid the device-wide synchronisation of cudaMalloc
+ * and cudaFree).  The paper has no counterpart: it is a packaging of the
+ * Eq. 4 field kernel.  Inputs dev_x, dev_y, dev_z: n_h holes followed by n_e
+ * electrons, FP32 positions in um, caller-owned device memory.  Output
+ * dev_E: 3 * (n_h + n_e) floats, Ex of every carrier, then Ey, then Ez
+ * (V/um), caller-owned device memory.  eps_r: relative permittivity;
+ * softening_um: Plummer length (0 selects 1e-6 um).  Work is queued on
+ * `stream` (a cudaStream_t, NULL = legacy default) and the call returns
+ * without waiting for it.
+ * It allocates nothing: its working storage is one fixed array compiled into
+ * the library (about 3 MB of device memory on every GPU that loads the
+ * library, held until the process exits), so at most 131072 carriers are
+ * accepted; larger inputs return SIM_ENOMEM_BUDGET before anything runs.
+ * The first call on a device looks up that array's device address (set-up,
+ * once per device, with the device current); make that first call before any
+ * stream capture.  Every call uses the same array and leaves it for the next
+ * call: calls that overlap on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller.  Returns SIM_OK, SIM_EINVAL,
+ * SIM_ENOMEM_BUDGET, SIM_ENODEV (no sm_103 device current) or SIM_ECUDA. */
+int cts_field_noalloc(const float* dev_x, const float* dev_y, const float* dev_z,
+                      int32_t n_h, int32_t n_e, double eps_r, double softening_um,
+                      float* dev_E, void* stream);
+
 /* Host-side fault injection for the failure-path tests: the next chunk (or
  * poll) reports the given code as if the device or queue had raised it
  * (SIM_ENUMERIC, SIM_ETIMEOUT, SIM_ECUDA); 0 clears. */

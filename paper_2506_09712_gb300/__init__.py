@@ -90,8 +90,8 @@ class cts_unit_t(C.Structure):
 EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_execute",
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
-            "sim_debug_inject", "sim_debug_trace_step", "cts_plan_units", "cts_arena_replay",
-            "cts_estimate_steps"]
+            "sim_debug_inject", "sim_debug_trace_step", "cts_field_noalloc", "cts_plan_units",
+            "cts_arena_replay", "cts_estimate_steps"]
 
 _lib = None
 
@@ -136,6 +136,8 @@ def load(build_if_missing: bool = True):
                                  P(i64)],
         "sim_debug_inject": [C.c_void_p, C.c_int],
         "sim_debug_trace_step": [C.c_void_p, P(u64), i32, P(i32)],
+        "cts_field_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, i32, i32, d, d, C.c_void_p,
+                              C.c_void_p],
         "cts_plan_units": [P(i32), P(i32), i32, i32, i32, i32, i32, i64, P(cts_unit_t), P(i32),
                            P(i32), P(i64)],
         "cts_arena_replay": [i64, P(i64), i32, P(i64)],
@@ -281,6 +283,12 @@ def sim_debug_trace_step(h, max_ctas=8192):
     _check(load().sim_debug_trace_step(h, _ptr(out, C.c_uint64), max_ctas, C.byref(n)),
            "sim_debug_trace_step")
     return out[:n.value]
+
+
+def cts_field_noalloc(dev_x, dev_y, dev_z, n_h, n_e, eps_r, softening_um, dev_E, stream=None):
+    """Allocation-free field: device pointers (ints) in and out; returns the status code."""
+    return load().cts_field_noalloc(dev_x, dev_y, dev_z, int(n_h), int(n_e), float(eps_r),
+                                    float(softening_um), dev_E, stream)
 
 
 def cts_plan_units(n_h, n_e, tile_i, grid, allow_split=1, max_units=65536,

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcts.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["cts_kernels.cu", "cts_runtime.cu", "cts_host.cpp"]
+SOURCES = ["cts_kernels.cu", "cts_runtime.cu", "cts_host.cpp", "cts_noalloc.cu"]
 HEADERS = ["cts_internal.h", "cts_host_impl.h"]
 
 
