@@ -184,6 +184,27 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# Event sharding across ranks (weak scaling) and the cross-rank timing rule
+# ---------------------------------------------------------------------------
+def shard_events(workload: str, n_per_rank: int, rank: int):
+    """Rank r simulates its own batch: event ids [r * n, (r + 1) * n)."""
+    import workloads as W
+    return W.make_events(workload, n=n_per_rank, first_id=rank * n_per_rank)
+
+
+def aggregate(dist, device, elapsed_ms: float, *counts: float):
+    """Whole-job numbers: the slowest rank's time and the sum of the counts."""
+    if dist is None:
+        return (elapsed_ms, *counts)
+    import torch
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor(list(counts), dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return (float(t.item()), *[float(v) for v in c.tolist()])
+
+
+# ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
 def kernel_source_hash() -> str:
@@ -267,7 +288,7 @@ def run_ours(args, rank, world, local):
 
     p = W.preset(args.workload)
     n_ev = args.events or p["n_events"]
-    events = W.make_events(args.workload, n=n_ev, first_id=rank * n_ev)
+    events = shard_events(args.workload, n_ev, rank)
     stream = torch.cuda.Stream()
     opts = dict(device=local, max_slots=max(256, n_ev), time_launches=1,
                 stream=stream.cuda_stream, variant=args.variant, chunk_steps=args.chunk)
@@ -312,17 +333,8 @@ def run_ours(args, rank, world, local):
         statuses += [r["status"] for r in res]
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        c = torch.tensor([float(inter), float(n_ev * args.steps)], device="cuda",
-                         dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        inter_all, events_all = int(c[0].item()), int(c[1].item())
-    else:
-        inter_all, events_all = inter, n_ev * args.steps
+    total_ms, inter_all, events_all = aggregate(dist, "cuda", sum(ms), float(inter),
+                                                float(n_ev * args.steps))
     value = inter_all / (total_ms * 1e-3)
     events_per_s = events_all / (total_ms * 1e-3)
 
@@ -337,13 +349,7 @@ def run_ours(args, rank, world, local):
         e2e_inter += sum(r["interactions"] for r in res)
     e2e_s = time.perf_counter() - t0
     s1 = sim.stats()
-    if dist:
-        t = torch.tensor([e2e_s, float(e2e_inter)], device="cuda", dtype=torch.float64)
-        tm = t[:1].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ti = t[1:].clone()
-        dist.all_reduce(ti, op=dist.ReduceOp.SUM)
-        e2e_s, e2e_inter = float(tm.item()), int(ti.item())
+    e2e_s, e2e_inter = aggregate(dist, "cuda", e2e_s, float(e2e_inter))
     e2e = {"value": e2e_inter / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": (s1["h2d_bytes"] - s0["h2d_bytes"]) // args.steps,
            "d2h_bytes_per_step": (s1["d2h_bytes"] - s0["d2h_bytes"]) // args.steps,

@@ -750,7 +750,10 @@ __global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, Slo
   const double ux = sin(th) * cos(phi), uy = sin(th) * sin(phi), uz = -cos(th);
   const double axv = cos(th) * cos(phi), ayv = cos(th) * sin(phi), azv = sin(th);
   const double bxv = -sin(phi), byv = cos(phi);
-  const double az0 = fmin(fmax(S->kind == 1 ? H - 0.5 * S->track_len_um * cos(th) : z_entry, 0.0), H);
+  // frame anchor: the absorption point, or the midpoint of a track
+  const double half = S->kind == 1 ? 0.5 * S->track_len_um : 0.0;
+  const double ax0 = S->x0 + half * ux, ay0 = S->y0 + half * uy;
+  const double az0 = fmin(fmax(S->kind == 1 ? H + half * uz : z_entry, 0.0), H);
   const int total_entries = S->cap_h + S->cap_e;
 
   for (int e = threadIdx.x; e < total_entries; e += blockDim.x) {
@@ -798,14 +801,14 @@ __global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, Slo
       atomicAdd(spec ? &ret_e : &ret_h, 1);
       A.sh[0][idx] = make_float4(kParked, kParked, kParked, 0.0f);
     } else {
-      A.sh[0][idx] = make_float4((float)(x - S->x0), (float)(y - S->y0), (float)(z - az0), 0.0f);
+      A.sh[0][idx] = make_float4((float)(x - ax0), (float)(y - ay0), (float)(z - az0), 0.0f);
     }
   }
   (void)n_tot;
   __syncthreads();
   if (threadIdx.x == 0) {
-    S->ax = S->x0;
-    S->ay = S->y0;
+    S->ax = ax0;
+    S->ay = ay0;
     S->az[0][0] = S->az[0][1] = az0;
     S->az[1][0] = S->az[1][1] = az0;
     S->n_h = S->cap_h;
