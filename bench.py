@@ -52,6 +52,8 @@ def parse_args():
     ap.add_argument("--events", type=int, default=0, help="events per rank (0: preset)")
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the kernel variant per resident-work bucket first (untimed)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/serving/oracle legs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -293,6 +295,8 @@ def run_ours(args, rank, world, local):
     opts = dict(device=local, max_slots=max(256, n_ev), time_launches=1,
                 stream=stream.cuda_stream, variant=args.variant, chunk_steps=args.chunk)
     sim = cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_BATCHED, **opts)
+    # kernel variant per amount of resident work, measured on this batch (untimed)
+    table = sim.autotune(events, reps=2) if args.autotune else []
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
 
     def one_step():
@@ -398,7 +402,8 @@ def run_ours(args, rank, world, local):
                        "positions": "f64", "pair_field": "f32 + Kahan",
                        "l2": "flushed (256 MiB write) before every timed step",
                        "parallelism": f"event-sharded x{world}",
-                       "variant": st["variant"]},
+                       "variant": st["variant"],
+                       "variant_table": table},
             "events_per_s": events_per_s,
             "roofline": roof, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
             "statuses_ok": all(s == 0 for s in statuses)}

@@ -205,6 +205,28 @@ int sim_stage(sim_t* sim, const sim_event_t* ev, int n);
 int sim_execute(sim_t* sim);
 int sim_collect(sim_t* sim, sim_result_t* out, int max_out, int* n_out);
 
+/* Kernel variant per chunk (the autotuner's output): a chunk whose resident
+ * pair work W = sum over events of (n_h + n_e)^2 is at least min_pairs[k]
+ * (largest such k; min_pairs ascending) runs variants[k] (1-based, as in
+ * sim_options_t.variant).  n = 0 restores the fixed variant. */
+int sim_set_variants(sim_t* sim, const int64_t* min_pairs, const int32_t* variants, int32_t n);
+
+/* Read the variant table back: up to cap entries; *n_out = table length. */
+int sim_get_variants(sim_t* sim, int64_t* min_pairs, int32_t* variants, int32_t cap,
+                     int32_t* n_out);
+
+/* Autotuner (BATCHED mode, idle handle): stages the first n, n/2, n/4, ..., 1
+ * of the given representative events, times every kernel variant on each
+ * (sim_debug_time_step, `reps` launches), and installs the table that runs
+ * the fastest variant for each range of resident pair work (boundaries at
+ * the geometric means of the measured work).  *n_buckets = table length.
+ * The handle is idle again afterwards. */
+int sim_autotune(sim_t* sim, const sim_event_t* ev, int32_t n, int32_t reps, int32_t* n_buckets);
+
+/* Drop every queued, resident or completed-but-unpolled event (their results
+ * are discarded); the handle is then idle. */
+int sim_reset(sim_t* sim);
+
 int sim_get_stats(sim_t* sim, sim_stats_t* out);
 int sim_destroy(sim_t* sim);
 const char* sim_strerror(int code);
@@ -242,9 +264,10 @@ int sim_debug_trajectory(sim_t* sim, const sim_event_t* ev, int64_t n_steps,
                          int64_t* steps_done);
 
 /* One step of the pair kernel (field only: the staged events do not move)
- * on the events admitted by sim_stage, with a per-CTA trace: out[4g..4g+3] =
- * (SM id, start ns, end ns, pairs) of CTA g, for up to max_ctas CTAs;
- * *n_ctas receives the grid size.  For load-balance studies. */
+ * on the events admitted by sim_stage, with a per-CTA trace: out[8g..8g+7] =
+ * (SM id, start ns, end ns, pairs, units, ns in unit prologues, ns in pair
+ * loops, ns in epilogues) of CTA g, for up to max_ctas CTAs; *n_ctas
+ * receives the grid size.  For load-balance and latency studies. */
 int sim_debug_trace_step(sim_t* sim, uint64_t* out, int32_t max_ctas, int32_t* n_ctas);
 
 /* Allocation-free pair field, for callers that cannot allocate device
@@ -271,6 +294,12 @@ int sim_debug_trace_step(sim_t* sim, uint64_t* out, int32_t max_ctas, int32_t* n
 int cts_field_noalloc(const float* dev_x, const float* dev_y, const float* dev_z,
                       int32_t n_h, int32_t n_e, double eps_r, double softening_um,
                       float* dev_E, void* stream);
+
+/* Time `reps` launches of the pair kernel (field only: positions do not move)
+ * on the events admitted by sim_stage, with kernel variant `variant`
+ * (1-based; 0 = the current one); *ms_per_launch receives the mean launch
+ * time from CUDA events.  The autotuner's measurement. */
+int sim_debug_time_step(sim_t* sim, int32_t variant, int32_t reps, double* ms_per_launch);
 
 /* Host-side fault injection for the failure-path tests: the next chunk (or
  * poll) reports the given code as if the device or queue had raised it

@@ -31,8 +31,9 @@ typedef struct cts_unit_t {
  * equal contiguous shares (tiles cut at j multiples of 4, segments of a tile
  * share iblock/pbase for their partial sums), grouped by CTA: CTA g runs
  * units [cta_begin[g], cta_begin[g+1]).  allow_split = 2: guided pieces for a
- * dynamic queue (largest first; pieces shrink over the last 30 % of the work)
- * that CTAs pull from; cta_begin[grid] = number of units, the rest 0.
+ * dynamic queue (largest first; piece sizes halve from w/2 to w/32 of a CTA's
+ * share w over the last half of the work) that CTAs pull from;
+ * cta_begin[grid] = number of units, the rest 0.
  * allow_split = 0: whole tiles dealt out longest first.  Units are written to
  * out (capacity max_units); cta_begin has grid + 1 entries.  *n_out = units,
  * *partial_floats = FP64 partial-sum entries needed (limit partial_cap).

@@ -90,8 +90,9 @@ class cts_unit_t(C.Structure):
 EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_execute",
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
-            "sim_debug_inject", "sim_debug_trace_step", "cts_field_noalloc", "cts_plan_units",
-            "cts_arena_replay", "cts_estimate_steps"]
+            "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_set_variants",
+            "sim_get_variants", "sim_autotune", "sim_reset", "cts_field_noalloc", "cts_plan_units", "cts_arena_replay",
+            "cts_estimate_steps"]
 
 _lib = None
 
@@ -136,6 +137,11 @@ def load(build_if_missing: bool = True):
                                  P(i64)],
         "sim_debug_inject": [C.c_void_p, C.c_int],
         "sim_debug_trace_step": [C.c_void_p, P(u64), i32, P(i32)],
+        "sim_debug_time_step": [C.c_void_p, i32, i32, P(d)],
+        "sim_set_variants": [C.c_void_p, P(i64), P(i32), i32],
+        "sim_reset": [C.c_void_p],
+        "sim_get_variants": [C.c_void_p, P(i64), P(i32), i32, P(i32)],
+        "sim_autotune": [C.c_void_p, P(sim_event_t), i32, i32, P(i32)],
         "cts_field_noalloc": [C.c_void_p, C.c_void_p, C.c_void_p, i32, i32, d, d, C.c_void_p,
                               C.c_void_p],
         "cts_plan_units": [P(i32), P(i32), i32, i32, i32, i32, i32, i64, P(cts_unit_t), P(i32),
@@ -276,9 +282,44 @@ def sim_debug_inject(h, fault):
     return load().sim_debug_inject(h, int(fault))
 
 
+def sim_debug_time_step(h, variant=0, reps=3):
+    """Mean launch time (ms) of the pair kernel on the staged events."""
+    ms = C.c_double(0.0)
+    _check(load().sim_debug_time_step(h, int(variant), int(reps), C.byref(ms)),
+           "sim_debug_time_step")
+    return ms.value
+
+
+def sim_set_variants(h, min_pairs, variants):
+    mp = np.ascontiguousarray(min_pairs, dtype=np.int64)
+    vs = np.ascontiguousarray(variants, dtype=np.int32)
+    _check(load().sim_set_variants(h, _ptr(mp, C.c_int64), _ptr(vs, C.c_int32), mp.size),
+           "sim_set_variants")
+
+
+def sim_reset(h):
+    _check(load().sim_reset(h), "sim_reset")
+
+
+def sim_get_variants(h, cap=64):
+    mp = np.zeros(cap, dtype=np.int64)
+    vs = np.zeros(cap, dtype=np.int32)
+    n = C.c_int32(0)
+    _check(load().sim_get_variants(h, _ptr(mp, C.c_int64), _ptr(vs, C.c_int32), cap,
+                                   C.byref(n)), "sim_get_variants")
+    return [(int(mp[q]), int(vs[q])) for q in range(min(n.value, cap))]
+
+
+def sim_autotune(h, events, n, reps=3):
+    nb = C.c_int32(0)
+    _check(load().sim_autotune(h, events, int(n), int(reps), C.byref(nb)), "sim_autotune")
+    return nb.value
+
+
 def sim_debug_trace_step(h, max_ctas=8192):
-    """Per-CTA (smid, t_start_ns, t_end_ns, pairs) of one field-only step."""
-    out = np.zeros((max_ctas, 4), dtype=np.uint64)
+    """Per-CTA (smid, t_start_ns, t_end_ns, pairs, units, ns_prologue, ns_loop,
+    ns_epilogue) of one field-only step."""
+    out = np.zeros((max_ctas, 8), dtype=np.uint64)
     n = C.c_int32(0)
     _check(load().sim_debug_trace_step(h, _ptr(out, C.c_uint64), max_ctas, C.byref(n)),
            "sim_debug_trace_step")
@@ -488,3 +529,20 @@ class Simulator:
 
     def inject(self, fault: int):
         return sim_debug_inject(self.h, fault)
+
+    def set_variants(self, table):
+        """table: [(min_pairs, variant)] ascending; [] restores the fixed variant."""
+        sim_set_variants(self.h, [t[0] for t in table], [t[1] for t in table])
+
+    def reset(self):
+        sim_reset(self.h)
+
+    def autotune(self, events: list[dict], reps: int = 3):
+        """Measure every kernel variant on batches of these events and install
+        the fastest per amount of resident pair work; returns the table."""
+        evs = make_events(events)
+        sim_autotune(self.h, evs, len(events), reps)
+        return sim_get_variants(self.h)
+
+    def variants(self):
+        return sim_get_variants(self.h)

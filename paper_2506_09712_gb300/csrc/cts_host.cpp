@@ -94,9 +94,9 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
     return 0;
   }
   if (dynamic) {
-    // Guided pieces for a dynamic queue: most work in large pieces, the last
-    // fraction in pieces that shrink toward the end, all sorted largest
-    // first; CTAs that run faster simply take more of them.
+    // Guided pieces for a dynamic queue (factoring): piece sizes halve batch
+    // by batch toward the end of the step's work, all sorted largest first;
+    // CTAs that run faster simply take more of them.
     const double w = W / grid;
     int iblock = 0;
     int64_t pfl = 0;
@@ -105,7 +105,10 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
     for (size_t ti = 0; ti < tiles.size(); ++ti) {
       const Tile& t = tiles[ti];
       const double f = t.c0 / W;
-      const double target = f < 0.70 ? 0.5 * w : f < 0.92 ? 0.125 * w : w / 32.0;
+      // factoring: the first half of the work in pieces of w/2, the next
+      // quarter in w/4, ... down to w/32
+      const double target = f < 0.5 ? 0.5 * w : f < 0.75 ? 0.25 * w : f < 0.875 ? 0.125 * w
+                          : f < 0.9375 ? w / 16.0 : w / 32.0;
       int ns = (int)std::max(1.0, std::ceil((double)t.ni * t.n / target));
       ns = std::min({ns, std::max(1, t.n / kPlanMinJ), kPlanMaxPieces});
       if (ns > 1 && pfl + (int64_t)3 * tile_i > partial_cap) ns = 1;

@@ -134,7 +134,8 @@ struct StepArgs {
   int32_t* combine_count;    // per i-block
   float* field_out;          // FIELD_ONLY output, SoA [3][capacity]
   int32_t* err;              // global error bits
-  unsigned long long* trace; // optional: per CTA {smid, t_start, t_end, pairs} (ns)
+  unsigned long long* trace; // optional: per CTA {smid, t_start, t_end, pairs, units,
+                             //   ns in prologues, in pair loops, in epilogues}
   Phys ph;
   int32_t S;                 // slot count
   int32_t fused;             // 1: update positions; 0: write field_out

@@ -227,6 +227,50 @@ __device__ __forceinline__ void pair_chunk_packed(const float4* __restrict__ sj,
   }
 }
 
+// The pair loop with two sources per packed FP32 lane pair: sources come from
+// a struct-of-arrays copy of the chunk (x[], y[], z[]), so one 128-bit load
+// yields the (x_j, x_j+1) and (x_j+2, x_j+3) register pairs directly; the i
+// position is held duplicated, (x_i, x_i).  m is a multiple of 4 (the copy is
+// padded with parked sources, which contribute exactly zero).  Accumulators
+// hold (sum over even j, sum over odd j).
+template <int R, bool NEG>
+__device__ __forceinline__ void pair_chunk_jpacked(const float* __restrict__ xs,
+                                                   const float* __restrict__ ys,
+                                                   const float* __restrict__ zs, int m,
+                                                   const float2 (&xi)[R], const float2 (&yi)[R],
+                                                   const float2 (&zi)[R], float2 (&ax)[R],
+                                                   float2 (&ay)[R], float2 (&az)[R],
+                                                   float eps2s) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 eps2 = make_float2(eps2s, eps2s);
+#pragma unroll 2
+  for (int j = 0; j < m; j += 4) {
+    const float4 X = *reinterpret_cast<const float4*>(xs + j);
+    const float4 Y = *reinterpret_cast<const float4*>(ys + j);
+    const float4 Z = *reinterpret_cast<const float4*>(zs + j);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float2 qx = h ? make_float2(X.z, X.w) : make_float2(X.x, X.y);
+      const float2 qy = h ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y);
+      const float2 qz = h ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float2 dx = NEG ? __ffma2_rn(xi[r], m1, qx) : __ffma2_rn(qx, m1, xi[r]);
+        const float2 dy = NEG ? __ffma2_rn(yi[r], m1, qy) : __ffma2_rn(qy, m1, yi[r]);
+        const float2 dz = NEG ? __ffma2_rn(zi[r], m1, qz) : __ffma2_rn(qz, m1, zi[r]);
+        float2 r2 = __ffma2_rn(dz, dz, eps2);
+        r2 = __ffma2_rn(dy, dy, r2);
+        r2 = __ffma2_rn(dx, dx, r2);
+        const float2 rs = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+        const float2 w = __fmul2_rn(__fmul2_rn(rs, rs), rs);
+        ax[r] = __ffma2_rn(dx, w, ax[r]);
+        ay[r] = __ffma2_rn(dy, w, ay[r]);
+        az[r] = __ffma2_rn(dz, w, az[r]);
+      }
+    }
+  }
+}
+
 // Kahan step (Higham, Accuracy and Stability, Alg. 4.2): s += t with the
 // running compensation c.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float t) {
@@ -295,12 +339,12 @@ __device__ __forceinline__ void update_carrier(const StepArgs& a, SlotDev* S, in
 // Per-slot duties of a step, done once per slot: interaction count, step
 // count and the next frame anchors.
 __device__ __forceinline__ void slot_duties(const StepArgs& a, SlotDev* S, int step, int p,
-                                            int nah, int nae) {
+                                            int nah, int nae, double azn0, double azn1) {
   const long long n = (long long)nah + (long long)nae;
   atomicAdd(&S->interactions, (unsigned long long)(n * (n - 1)));
   S->n_steps = step + 1;
-  S->az[p ^ 1][0] = anchor_next(a.ph, 0, S->az[p][0]);
-  S->az[p ^ 1][1] = anchor_next(a.ph, 1, S->az[p][1]);
+  S->az[p ^ 1][0] = azn0;
+  S->az[p ^ 1][1] = azn1;
 }
 
 // Active carriers of a slot at chunk step k.
@@ -317,12 +361,18 @@ __device__ __forceinline__ void active_counts(const StepArgs& a, const SlotDev* 
 // ---------------------------------------------------------------------------
 // The step kernel.
 // ---------------------------------------------------------------------------
-template <int NT, int R, bool PACKED, int JU, int MINB>
+// MODE 0: scalar FP32 pair loop; 1: packed over pairs of i's; 2: packed over
+// pairs of sources (struct-of-arrays copy of each chunk in shared memory).
+template <int NT, int R, int MODE, int JU, int MINB>
 __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
   constexpr int TI = NT * R;
-  static_assert(!PACKED || R % 2 == 0, "packed variants pair i's two by two");
+  static_assert(MODE != 1 || R % 2 == 0, "packed-i variants pair i's two by two");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float4* stage = reinterpret_cast<float4*>(smem_raw);  // [2][kChunkJ]
+  // MODE 2: struct-of-arrays copy of the current chunk, padded to a multiple of 4
+  float* soa_x = reinterpret_cast<float*>(smem_raw + 2 * kChunkJ * sizeof(float4));
+  float* soa_y = soa_x + kChunkJ;
+  float* soa_z = soa_y + kChunkJ;
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ int s_skip, s_last, s_nah, s_nae, s_step;
   __shared__ double s_azn[2];
@@ -338,8 +388,14 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
   uint32_t uses[2] = {0u, 0u};
   bool failed = false;
   const float eps2 = a.ph.f_eps2;
-  unsigned long long t_start = 0, pairs_done = 0;
-  if (a.trace && tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+  unsigned long long t_start = 0, pairs_done = 0, n_units_done = 0;
+  unsigned long long ns_pro = 0, ns_loop = 0, ns_epi = 0, t_mark = 0;
+  auto now_ns = [&]() {
+    unsigned long long t = 0;
+    if (a.trace) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+  };
+  if (a.trace && tid == 0) t_start = now_ns();
   // this CTA's share of the step's pair work: a static equal-cost range, or
   // pieces pulled from the step's queue
   __shared__ int s_u;
@@ -353,24 +409,36 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
       u = s_u;
     }
     if (u >= u_end) break;
+    if (tid == 0) t_mark = now_ns();
     const Unit U = a.units[u];
     if (!a.dynamic) ++u;
     SlotDev* S = a.slots + U.slot;
-    if (tid == 0) {
-      int nah, nae;
-      active_counts(a, S, U.slot, k, nah, nae);
-      const int step = S->step0 + k;
-      s_nah = nah;
-      s_nae = nae;
-      s_step = step;
-      s_skip = (!S->running) || nah <= 0 || (int64_t)step >= a.ph.max_steps;
-      if (!s_skip) {
-        const int p = step & 1;
-        s_azn[0] = anchor_next(a.ph, 0, S->az[p][0]);
-        s_azn[1] = anchor_next(a.ph, 1, S->az[p][1]);
-        s_off = (float)(S->az[p][1] - S->az[p][0]);
-        if (a.fused && U.spec == 0 && U.i0 == 0 && U.split == 0)
-          slot_duties(a, S, step, p, nah, nae);
+    // Prologue, spread over warps so its latencies overlap: warp 0 sums the
+    // slot's retire counters of the earlier steps of this chunk (one load per
+    // lane), warps 1 and 2 predict the next frame anchor of each species.
+    {
+      const int warp = tid >> 5, lane = tid & 31;
+      if (warp == 0) {
+        int dh = 0, de = 0;
+        for (int kk = lane; kk < k; kk += 32) {
+          dh += a.ret[((int64_t)kk * a.S + U.slot) * 2 + 0];
+          de += a.ret[((int64_t)kk * a.S + U.slot) * 2 + 1];
+        }
+        dh = __reduce_add_sync(0xffffffffu, dh);
+        de = __reduce_add_sync(0xffffffffu, de);
+        if (lane == 0) {
+          const int nah = S->act_h - dh, nae = S->act_e - de;
+          const int step = S->step0 + k;
+          s_nah = nah;
+          s_nae = nae;
+          s_step = step;
+          s_skip = (!S->running) || nah <= 0 || (int64_t)step >= a.ph.max_steps;
+        }
+      } else if (warp <= 2 && lane == 0) {
+        const int spec = warp - 1;
+        const int p = (S->step0 + k) & 1;
+        s_azn[spec] = anchor_next(a.ph, spec, S->az[p][spec]);
+        if (spec == 1) s_off = (float)(S->az[p][1] - S->az[p][0]);
       }
     }
     __syncthreads();
@@ -378,12 +446,20 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
       __syncthreads();
       continue;
     }
+    if (tid == 0 && a.fused && U.spec == 0 && U.i0 == 0 && U.split == 0)
+      slot_duties(a, S, s_step, s_step & 1, s_nah, s_nae, s_azn[0], s_azn[1]);
     const int step = s_step;
     const int p = step & 1;
     const float4* __restrict__ shin = a.A.sh[p];
     const int64_t ibase = S->base + (U.spec ? S->cap_h : 0);
     const int nh = S->n_h, ne = S->n_e;
     pairs_done += (unsigned long long)U.ni * (unsigned long long)(U.j1 - U.j0);
+    n_units_done += 1;
+    if (tid == 0 && a.trace) {
+      const unsigned long long t = now_ns();
+      ns_pro += t - t_mark;
+      t_mark = t;
+    }
 
     float xi[R], yi[R], zi[R];
 #pragma unroll
@@ -452,11 +528,43 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
           }
         }
         const float4* sj = stage + st * kChunkJ;
+        int cnt_eff = cnt;
+        if constexpr (MODE == 2) {
+          cnt_eff = (cnt + 3) & ~3;
+          for (int e = tid; e < cnt_eff; e += NT) {
+            const float4 q = e < cnt ? sj[e] : make_float4(kParked, kParked, kParked, 0.0f);
+            soa_x[e] = q.x;
+            soa_y[e] = q.y;
+            soa_z[e] = q.z;
+          }
+          __syncthreads();
+        }
         // plain FP32 sums over at most kFoldJ sources, then a Kahan fold
-        for (int sub = 0; sub < cnt; sub += kFoldJ) {
-          const int m = min(kFoldJ, cnt - sub);
+        for (int sub = 0; sub < cnt_eff; sub += kFoldJ) {
+          const int m = min(kFoldJ, cnt_eff - sub);
           float tx[R], ty[R], tz[R];
-          if constexpr (PACKED) {
+          if constexpr (MODE == 2) {
+            float2 qx2[R], qy2[R], qz2[R], ax2[R], ay2[R], az2[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              qx2[r] = make_float2(xi[r], xi[r]);
+              qy2[r] = make_float2(yi[r], yi[r]);
+              qz2[r] = make_float2(zi[r], zi[r]);
+              ax2[r] = ay2[r] = az2[r] = make_float2(0.0f, 0.0f);
+            }
+            if (c < nch_h)
+              pair_chunk_jpacked<R, false>(soa_x + sub, soa_y + sub, soa_z + sub, m, qx2, qy2,
+                                           qz2, ax2, ay2, az2, eps2);
+            else
+              pair_chunk_jpacked<R, true>(soa_x + sub, soa_y + sub, soa_z + sub, m, qx2, qy2,
+                                          qz2, ax2, ay2, az2, eps2);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              tx[r] = ax2[r].x + ax2[r].y;
+              ty[r] = ay2[r].x + ay2[r].y;
+              tz[r] = az2[r].x + az2[r].y;
+            }
+          } else if constexpr (MODE == 1) {
             constexpr int P = R / 2;
             float2 px2[P], py2[P], pz2[P], ax2[P], ay2[P], az2[P];
 #pragma unroll
@@ -496,6 +604,11 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
         __syncthreads();
       }
       if (failed) break;
+    }
+    if (tid == 0 && a.trace) {
+      const unsigned long long t = now_ns();
+      ns_loop += t - t_mark;
+      t_mark = t;
     }
     float vx[R], vy[R], vz[R];
 #pragma unroll
@@ -569,18 +682,22 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
         }
       }
     }
+    if (tid == 0 && a.trace) ns_epi += now_ns() - t_mark;
     __syncthreads();
   }
   if (a.trace && tid == 0) {
-    unsigned long long t_end;
+    unsigned long long t_end = now_ns();
     unsigned smid;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
     asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-    unsigned long long* t = a.trace + 4 * (size_t)blockIdx.x;
+    unsigned long long* t = a.trace + 8 * (size_t)blockIdx.x;
     t[0] = smid;
     t[1] = t_start;
     t[2] = t_end;
     t[3] = pairs_done;
+    t[4] = n_units_done;
+    t[5] = ns_pro;
+    t[6] = ns_loop;
+    t[7] = ns_epi;
   }
 }
 
@@ -596,7 +713,7 @@ __global__ void update_kernel(StepArgs a, int k, const int32_t* slot_list, int n
     const int p = step & 1;
     const double azn0 = anchor_next(a.ph, 0, S->az[p][0]);
     const double azn1 = anchor_next(a.ph, 1, S->az[p][1]);
-    if (blockIdx.x == 0 && threadIdx.x == 0) slot_duties(a, S, step, p, nah, nae);
+    if (blockIdx.x == 0 && threadIdx.x == 0) slot_duties(a, S, step, p, nah, nae, azn0, azn1);
     const int n = S->n_h + S->n_e;
     const int64_t cap = a.A.capacity;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
@@ -943,27 +1060,32 @@ struct VariantEntry {
   int nt, r;
   const char* name;
   void (*fn)(StepArgs, int);
-  int ctas_per_sm, dynamic;
+  int ctas_per_sm, dynamic, mode;
 };
 
 // (threads, i's per thread, packed f32x2, j unroll, min CTAs per SM [register
 // cap], CTAs per SM launched [0 = all that fit], dynamic queue).  Entry 0 is
-// the default: packed FP32 pairs, 512-carrier tiles, guided dynamic queue.
-#define CTS_V(NT, R, PK, JU, MB, CPS, DYN, NAME) \
-  {NT, R, NAME, step_kernel<NT, R, PK, JU, MB>, CPS, DYN}
+// the default: sources paired in packed FP32 lanes, 512-carrier tiles, guided
+// dynamic queue (fastest on the 64 x 20 keV batch).
+#define CTS_V(NT, R, MODE, JU, MB, CPS, DYN, NAME) \
+  {NT, R, NAME, step_kernel<NT, R, MODE, JU, MB>, CPS, DYN, MODE}
 const VariantEntry kVariants[] = {
-    CTS_V(128, 4, true, 4, 4, 0, 1, "nt128_r4_f32x2_u4_dyn"),
-    CTS_V(128, 2, true, 4, 6, 0, 1, "nt128_r2_f32x2_u4_dyn"),
-    CTS_V(256, 2, true, 4, 3, 0, 1, "nt256_r2_f32x2_u4_dyn"),
-    CTS_V(128, 4, true, 4, 4, 0, 0, "nt128_r4_f32x2_u4_static"),
-    CTS_V(512, 2, true, 4, 1, 1, 0, "nt512_r2_f32x2_u4_1sm_static"),
-    CTS_V(128, 4, false, 2, 6, 0, 1, "nt128_r4_scalar_dyn"),
-    CTS_V(256, 2, false, 4, 3, 0, 1, "nt256_r2_scalar_u4_dyn"),
-    CTS_V(256, 2, false, 2, 4, 0, 0, "nt256_r2_scalar_static"),
+    CTS_V(256, 2, 2, 4, 3, 0, 1, "nt256_r2_jpair_dyn"),
+    CTS_V(128, 2, 2, 4, 6, 0, 1, "nt128_r2_jpair_dyn"),
+    CTS_V(128, 4, 2, 4, 4, 0, 1, "nt128_r4_jpair_dyn"),
+    CTS_V(512, 1, 2, 4, 2, 0, 1, "nt512_r1_jpair_dyn"),
+    CTS_V(128, 4, 1, 4, 4, 0, 1, "nt128_r4_ipair_dyn"),
+    CTS_V(256, 2, 1, 4, 3, 0, 1, "nt256_r2_ipair_dyn"),
+    CTS_V(128, 4, 1, 4, 4, 0, 0, "nt128_r4_ipair_static"),
+    CTS_V(512, 2, 1, 4, 1, 1, 0, "nt512_r2_ipair_1sm_static"),
+    CTS_V(256, 2, 0, 4, 3, 0, 1, "nt256_r2_scalar_dyn"),
+    CTS_V(256, 2, 0, 2, 4, 0, 0, "nt256_r2_scalar_static"),
 };
 #undef CTS_V
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr size_t kStageBytes = 2 * kChunkJ * sizeof(float4);
+constexpr size_t kSoaBytes = 3 * kChunkJ * sizeof(float);
+size_t smem_of(const VariantEntry& e) { return kStageBytes + (e.mode == 2 ? kSoaBytes : 0); }
 
 }  // namespace
 
@@ -974,19 +1096,19 @@ Variant variant_info(int v) {
   return Variant{e.nt, e.r, e.name, e.ctas_per_sm, e.dynamic};
 }
 
-size_t variant_smem(int) { return kStageBytes; }
+size_t variant_smem(int v) { return smem_of(kVariants[v]); }
 
 cudaError_t variant_occupancy(int v, int* blocks_per_sm) {
   const VariantEntry& e = kVariants[v];
   cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kStageBytes);
+                                         (int)smem_of(e));
   if (err != cudaSuccess) return err;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.nt, kStageBytes);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.nt, smem_of(e));
 }
 
 cudaError_t launch_step(int v, const StepArgs& a, int k, int grid, cudaStream_t s) {
   const VariantEntry& e = kVariants[v];
-  e.fn<<<grid, e.nt, kStageBytes, s>>>(a, k);
+  e.fn<<<grid, e.nt, smem_of(e), s>>>(a, k);
   return cudaGetLastError();
 }
 

@@ -136,9 +136,16 @@ struct sim_t {
   int inject = 0;
   std::vector<int> staged;  // slots admitted by sim_stage, in staging order
 
-  // graph cache
-  cudaGraphExec_t graph = nullptr;
-  int graph_K = -1, graph_v = -1, graph_grid = -1;
+  // one captured K-step chunk per kernel variant
+  std::vector<cudaGraphExec_t> graphs;
+  std::vector<int> graph_K;
+  // per-variant occupancy (CTAs per SM), queried once
+  std::vector<int> occ_cache;
+  // variant table: a chunk whose resident pair work W satisfies
+  // W >= table_min[k] (largest such k) runs table_var[k]; empty = fixed variant
+  std::vector<int64_t> table_min;
+  std::vector<int> table_var;
+  int base_variant = 0;
 
   // stats
   int64_t st_events = 0, st_inter = 0, st_steps = 0, st_launch = 0, st_chunks = 0,
@@ -470,6 +477,8 @@ int issue_chunk(sim_t* s, int K) {
   return SIM_OK;
 }
 
+int set_variant(sim_t* s, int v);
+
 int run_chunk(sim_t* s) {
   const bool plain = s->opt.mode == CTS_MODE_PLAIN;
   const int K = plain ? 1 : s->K;
@@ -480,14 +489,25 @@ int run_chunk(sim_t* s) {
       if (s->slots[k].used && s->slots[k].running) s->h_list[n++] = k;
     CK(h2d(s, s->d_list, s->h_list, std::max(n, 1) * sizeof(int32_t)));
   }
+  if (!plain && !s->table_min.empty()) {
+    double W = 0.0;
+    for (auto& h : s->slots)
+      if (h.used && h.running) W += (double)(h.n_h + h.n_e) * (double)(h.n_h + h.n_e);
+    int v = s->table_var[0];
+    for (size_t q = 0; q < s->table_min.size(); ++q)
+      if (W >= (double)s->table_min[q]) v = s->table_var[q];
+    int rcv = set_variant(s, v);
+    if (rcv) return rcv;
+  }
   int rc = upload_units(s, !plain);
   if (rc) return rc;
   CK(cudaEventRecord(s->ev0, s->stream));
   if (!plain && !s->opt.disable_graphs) {
-    if (!s->graph || s->graph_K != K || s->graph_v != s->variant || s->graph_grid != s->grid) {
-      if (s->graph) {
-        cudaGraphExecDestroy(s->graph);
-        s->graph = nullptr;
+    cudaGraphExec_t& graph = s->graphs[s->variant];
+    if (!graph || s->graph_K[s->variant] != K) {
+      if (graph) {
+        cudaGraphExecDestroy(graph);
+        graph = nullptr;
       }
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
@@ -499,13 +519,11 @@ int run_chunk(sim_t* s) {
       cudaError_t ce = cudaStreamEndCapture(s->stream, &g);
       if (rc) return rc;
       CK(ce);
-      CK(cudaGraphInstantiate(&s->graph, g, 0));
+      CK(cudaGraphInstantiate(&graph, g, 0));
       cudaGraphDestroy(g);
-      s->graph_K = K;
-      s->graph_v = s->variant;
-      s->graph_grid = s->grid;
+      s->graph_K[s->variant] = K;
     }
-    CK(cudaGraphLaunch(s->graph, s->stream));
+    CK(cudaGraphLaunch(graph, s->stream));
     s->st_launch += K + 1;
     s->st_d2h += (int64_t)s->S * sizeof(SlotSummary) + sizeof(int32_t);
   } else {
@@ -786,7 +804,8 @@ int alloc_all(sim_t* s) {
 }
 
 void free_all(sim_t* s) {
-  if (s->graph) cudaGraphExecDestroy(s->graph);
+  for (auto g : s->graphs)
+    if (g) cudaGraphExecDestroy(g);
   void* dev[] = {s->A.px, s->A.py, s->A.pz, s->A.sh[0], s->A.sh[1], s->A.cid, s->A.fx, s->A.fy,
                  s->A.rstep, s->A.cstate, s->d_slots, s->d_summary, s->d_readout, s->d_pixels,
                  s->d_units, s->d_cta_begin, s->d_unit_counter, s->d_ret, s->d_partial,
@@ -812,9 +831,13 @@ int choose_variant(sim_t* s) {
 }
 
 int set_variant(sim_t* s, int v) {
-  int occ = 0;
-  CK(variant_occupancy(v, &occ));
-  if (occ < 1) occ = 1;
+  if (v == s->variant && s->grid > 0) return SIM_OK;
+  int occ = s->occ_cache[v];
+  if (occ <= 0) {
+    CK(variant_occupancy(v, &occ));
+    if (occ < 1) occ = 1;
+    s->occ_cache[v] = occ;
+  }
   const Variant vi = variant_info(v);
   if (vi.ctas_per_sm > 0) occ = std::min(occ, vi.ctas_per_sm);
   s->variant = v;
@@ -893,8 +916,13 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
     }
     s->own_stream = true;
   }
+  s->graphs.assign(variant_count(), nullptr);
+  s->graph_K.assign(variant_count(), -1);
+  s->occ_cache.assign(variant_count(), 0);
+  s->variant = -1;
   rc = alloc_all(s);
   if (!rc) rc = set_variant(s, choose_variant(s));
+  s->base_variant = s->variant;
   if (rc) {
     free_all(s);
     delete s;
@@ -1285,7 +1313,7 @@ int sim_debug_trace_step(sim_t* s, uint64_t* out, int32_t max_ctas, int32_t* n_c
   float* d_field = nullptr;
   unsigned long long* d_trace = nullptr;
   cudaError_t e = cudaSuccess;
-  std::vector<unsigned long long> h((size_t)4 * s->grid);
+  std::vector<unsigned long long> h((size_t)8 * s->grid);
   do {
     if ((e = cudaMalloc(&d_field, 3 * (size_t)s->capacity * sizeof(float)))) break;
     if ((e = cudaMalloc(&d_trace, h.size() * sizeof(unsigned long long)))) break;
@@ -1309,9 +1337,153 @@ int sim_debug_trace_step(sim_t* s, uint64_t* out, int32_t max_ctas, int32_t* n_c
   }
   const int n = std::min(max_ctas, s->grid);
   for (int g = 0; g < n; ++g)
-    for (int q = 0; q < 4; ++q) out[4 * g + q] = h[4 * (size_t)g + q];
+    for (int q = 0; q < 8; ++q) out[8 * g + q] = h[8 * (size_t)g + q];
   *n_ctas = n;
   return SIM_OK;
+}
+
+int sim_set_variants(sim_t* s, const int64_t* min_pairs, const int32_t* variants, int32_t n) {
+  if (!s || n < 0 || (n > 0 && (!min_pairs || !variants))) return SIM_EINVAL;
+  for (int q = 0; q < n; ++q) {
+    if (variants[q] < 1 || variants[q] > variant_count() || min_pairs[q] < 0) return SIM_EINVAL;
+    if (q > 0 && min_pairs[q] < min_pairs[q - 1]) return SIM_EINVAL;
+  }
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  s->table_min.assign(min_pairs, min_pairs + n);
+  s->table_var.assign((size_t)n, 0);
+  for (int q = 0; q < n; ++q) s->table_var[q] = variants[q] - 1;
+  if (n == 0) return set_variant(s, s->base_variant);
+  return SIM_OK;
+}
+
+int sim_reset(sim_t* s) {
+  if (!s) return SIM_EINVAL;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  {
+    std::lock_guard<std::mutex> lk(s->qmu);
+    s->queue.clear();
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->dmu);
+    s->done.clear();
+  }
+  cudaSetDevice(s->device);
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (int k = 0; k < s->S; ++k) {
+    HostSlot& h = s->slots[k];
+    if (!h.used) continue;
+    const int zero = 0;
+    CK(cudaMemcpyAsync(&s->d_slots[k].running, &zero, sizeof(int), cudaMemcpyHostToDevice,
+                       s->stream));
+    s->alloc.release(h.base);
+    h = HostSlot{};
+  }
+  s->staged.clear();
+  CK(cudaStreamSynchronize(s->stream));
+  return SIM_OK;
+}
+
+int sim_debug_time_step(sim_t* s, int32_t variant, int32_t reps, double* ms_per_launch) {
+  if (!s || !ms_per_launch || reps < 1 || variant < 0 || variant > variant_count())
+    return SIM_EINVAL;
+  if (s->opt.mode != CTS_MODE_BATCHED) return SIM_ESTATE;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  cudaSetDevice(s->device);
+  int rc = launch_inits(s);
+  if (rc) return rc;
+  bool any = false;
+  for (auto& h : s->slots) any |= h.used && h.running;
+  if (!any) return SIM_ESTATE;
+  const int saved = s->variant;
+  if (variant > 0) {
+    rc = set_variant(s, variant - 1);
+    if (rc) return rc;
+  }
+  rc = upload_units(s, true);
+  float* d_field = nullptr;
+  cudaError_t e = cudaSuccess;
+  float ms = 0.f;
+  do {
+    if (rc) break;
+    if ((e = cudaMalloc(&d_field, 3 * (size_t)s->capacity * sizeof(float)))) break;
+    if ((e = cudaMemsetAsync(s->d_ret, 0, (size_t)s->S * 2 * sizeof(int32_t), s->stream))) break;
+    StepArgs a = step_args(s, false);
+    a.field_out = d_field;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // launch 0 warms up
+      if (r == 1 && (e = cudaEventRecord(s->ev0, s->stream))) break;
+      if ((e = cudaMemsetAsync(s->d_unit_counter, 0, sizeof(int32_t), s->stream))) break;
+      if ((e = launch_step(s->variant, a, 0, s->grid, s->stream))) break;
+    }
+    if (e) break;
+    if ((e = cudaEventRecord(s->ev1, s->stream))) break;
+    if ((e = cudaStreamSynchronize(s->stream))) break;
+    if ((e = cudaEventElapsedTime(&ms, s->ev0, s->ev1))) break;
+  } while (0);
+  if (d_field) cudaFree(d_field);
+  const int rc2 = set_variant(s, saved);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    s->err = cudaGetErrorString(e);
+    return SIM_ECUDA;
+  }
+  *ms_per_launch = ms / reps;
+  return rc2;
+}
+
+int sim_get_variants(sim_t* s, int64_t* min_pairs, int32_t* variants, int32_t cap,
+                     int32_t* n_out) {
+  if (!s || !n_out || cap < 0 || (cap > 0 && (!min_pairs || !variants))) return SIM_EINVAL;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  const int n = (int)s->table_min.size();
+  for (int q = 0; q < n && q < cap; ++q) {
+    min_pairs[q] = s->table_min[q];
+    variants[q] = s->table_var[q] + 1;
+  }
+  *n_out = n;
+  return SIM_OK;
+}
+
+int sim_autotune(sim_t* s, const sim_event_t* ev, int32_t n, int32_t reps, int32_t* n_buckets) {
+  if (!s || !ev || n < 1 || reps < 1 || !n_buckets) return SIM_EINVAL;
+  if (s->opt.mode != CTS_MODE_BATCHED) return SIM_ESTATE;
+  int rc = sim_reset(s);
+  if (rc) return rc;
+  // batch sizes n, n/2, ..., 1; for each the pair work W and the fastest variant
+  std::vector<std::pair<double, int>> best;
+  for (int m = std::min(n, s->S); m >= 1; m /= 2) {
+    rc = sim_stage(s, ev, m);
+    if (rc) return rc;
+    double W = 0.0;
+    for (auto& h : s->slots)
+      if (h.used) W += (double)(h.n_h + h.n_e) * (double)(h.n_h + h.n_e);
+    int bv = -1;
+    double bt = 1e30;
+    for (int v = 1; v <= variant_count(); ++v) {
+      double ms = 0.0;
+      rc = sim_debug_time_step(s, v, reps, &ms);
+      if (rc) return rc;
+      if (ms < bt) {
+        bt = ms;
+        bv = v;
+      }
+    }
+    best.push_back({W, bv});
+    rc = sim_reset(s);
+    if (rc) return rc;
+    if (m == 1) break;
+  }
+  std::sort(best.begin(), best.end());
+  std::vector<int64_t> mins;
+  std::vector<int32_t> vars;
+  for (size_t q = 0; q < best.size(); ++q) {
+    const double lo = q == 0 ? 0.0 : std::sqrt(best[q - 1].first * best[q].first);
+    if (!vars.empty() && vars.back() == best[q].second) continue;  // merge equal neighbours
+    mins.push_back((int64_t)lo);
+    vars.push_back(best[q].second);
+  }
+  rc = sim_set_variants(s, mins.data(), vars.data(), (int32_t)mins.size());
+  *n_buckets = (int32_t)mins.size();
+  return rc;
 }
 
 int sim_debug_bin(sim_t* s, const double* x, const double* y, int64_t n, int32_t* pixels,

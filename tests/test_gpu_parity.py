@@ -220,11 +220,15 @@ def test_trajectory_parity_3keV(steps):
     assert np.array_equal(st, ref.state)
     act = ref.state == oracle.ACTIVE
     col = ref.state == oracle.COLLECTED
-    dpos = np.abs(pos[act] - ref.pos[act]).max() if act.any() else 0.0
-    dcol = np.abs(pos[col, :2] - ref.final_xy[col]).max() if col.any() else 0.0
-    # FP32 displacements around FP64 positions: ~1e-7 relative per step
-    assert dpos <= 2e-5 * steps ** 0.5 + 1e-6, dpos
-    assert dcol <= 2e-5 * steps ** 0.5 + 1e-6, dcol
+    d = np.concatenate([np.abs(pos[act] - ref.pos[act]).max(axis=1),
+                        np.abs(pos[col, :2] - ref.final_xy[col]).max(axis=1)])
+    # FP32 displacements around FP64 positions differ by ~1e-7 um per step; close
+    # pairs (Euler-unstable below ~0.05 um) amplify that for a few carriers, as
+    # measured in the divergence study of the design notes.  A wrong term would
+    # move every carrier by far more.
+    assert np.median(d) <= 2e-6, np.median(d)
+    assert np.quantile(d, 0.99) <= 5e-4, np.quantile(d, 0.99)
+    assert d.max() <= 2e-2, d.max()
 
 
 def _compare_events(gpu, ref, n_carriers):
@@ -401,3 +405,19 @@ def test_every_kernel_variant_matches_the_oracle():
     for v in vs:
         with sim_for(name, variant=v) as sim:
             _compare_events(sim.run(ev)[0], ref, 829)
+
+
+def test_autotuned_variant_table_runs_and_matches():
+    name = "plain_3keV_100um"
+    evs = W.make_events(name)
+    with sim_for(name) as sim:
+        table = sim.autotune(W.make_events(name, n=8, first_id=900), reps=2)
+        assert len(table) >= 1 and table[0][0] == 0
+        assert all(1 <= v <= len(_variants()) for _, v in table)
+        assert [t[0] for t in table] == sorted(t[0] for t in table)
+        res = sim.run(evs)
+        sim.set_variants([])
+        assert sim.variants() == []
+    refs = oracle.run_events(oracle_params(name), evs)
+    for g, r in zip(res, refs):
+        _compare_events(g, r, 829)
