@@ -31,7 +31,7 @@ typedef struct cts_unit_t {
  * equal contiguous shares (tiles cut at j multiples of 4, segments of a tile
  * share iblock/pbase for their partial sums), grouped by CTA: CTA g runs
  * units [cta_begin[g], cta_begin[g+1]).  allow_split = 2: guided pieces for a
- * dynamic queue (largest first; piece sizes halve from w/2 to w/32 of a CTA's
+ * dynamic queue (largest first; piece sizes halve from w/2 to w/64 of a CTA's
  * share w over the last half of the work) that CTAs pull from;
  * cta_begin[grid] = number of units, the rest 0.
  * allow_split = 0: whole tiles dealt out longest first.  Units are written to

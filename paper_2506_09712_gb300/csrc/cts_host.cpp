@@ -95,7 +95,8 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
   }
   if (dynamic) {
     // Guided pieces for a dynamic queue (factoring): piece sizes halve batch
-    // by batch toward the end of the step's work, all sorted largest first;
+    // by batch toward the end of the step's work (w/2 ... w/64), all sorted
+    // largest first;
     // CTAs that run faster simply take more of them.
     const double w = W / grid;
     int iblock = 0;
@@ -108,9 +109,9 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
       // factoring: the first half of the work in pieces of w/2, the next
       // quarter in w/4, ... down to w/32
       const double target = f < 0.5 ? 0.5 * w : f < 0.75 ? 0.25 * w : f < 0.875 ? 0.125 * w
-                          : f < 0.9375 ? w / 16.0 : w / 32.0;
+                          : f < 0.9375 ? w / 16.0 : f < 0.96875 ? w / 32.0 : w / 64.0;
       int ns = (int)std::max(1.0, std::ceil((double)t.ni * t.n / target));
-      ns = std::min({ns, std::max(1, t.n / kPlanMinJ), kPlanMaxPieces});
+      ns = std::min({ns, std::max(1, t.n / kPlanDynMinJ), kPlanDynMaxPieces});
       if (ns > 1 && pfl + (int64_t)3 * tile_i > partial_cap) ns = 1;
       for (int k = 0; k < ns; ++k) {
         int j0 = (int)((int64_t)t.n * k / ns) & ~3, j1 = k + 1 == ns ? t.n : (int)((int64_t)t.n * (k + 1) / ns) & ~3;

@@ -6,8 +6,9 @@
 
 namespace cts {
 
-constexpr int kPlanMinJ = 256;       // shortest j range of a tile piece
-constexpr int kPlanMaxPieces = 32;   // most pieces one tile is cut into
+constexpr int kPlanMinJ = 256;        // shortest j range of a static share's segment
+constexpr int kPlanDynMinJ = 64;      // shortest j range of a dynamic-queue piece
+constexpr int kPlanDynMaxPieces = 128;  // most dynamic-queue pieces per tile
 constexpr int64_t kArenaAlign = 32; // arena entries are handed out in multiples of this
 
 struct UnitPlan {
