@@ -253,6 +253,40 @@ def serving_leg(cts, W, torch, device):
     return out
 
 
+def large_n_leg(cts, W, torch, device, stream, steps: int = 24):
+    """The 16 straight 200 keV electron tracks (2 x 55 250 carriers each, both
+    species, 5 ps steps), all resident, for their first `steps` fused steps:
+    the pair kernel's rate at the largest event size."""
+    name = "track_200keV_320um"
+    p = W.preset(name)
+    p["sensor"]["max_steps"] = steps
+    evs = W.make_events(name)
+    out = {"workload": name, "events": len(evs), "carriers_per_event": 2 * p["n_pairs"],
+           "steps": steps}
+    with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_BATCHED, device=device,
+                       max_slots=len(evs), time_launches=1, stream=stream.cuda_stream) as sim:
+        for timed in (False, True):
+            sim.stage(evs)
+            torch.cuda.synchronize()
+            s0 = sim.stats()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.execute()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s1 = sim.stats()
+            res = sim.collect(len(evs))
+        ms = e0.elapsed_time(e1)
+        kms = s1["step_kernel_ms"] - s0["step_kernel_ms"]
+        inter = sum(r["interactions"] for r in res)
+        out.update({"interactions_per_s": inter / (ms * 1e-3),
+                    "step_kernel_tflops": FLOPS_PER_PAIR * inter / (kms * 1e-3) / 1e12,
+                    "ms_per_step": ms / steps,
+                    "statuses": sorted({int(r["status"]) for r in res})})
+    return out
+
+
 def _offered(sim, W, name, rate, n):
     """Open-loop Poisson arrivals at `rate`; latency = completion - submission."""
     arr = W.poisson_arrivals(rate, n, seed=7)
@@ -425,6 +459,12 @@ def run_ours(args, rank, world, local):
             line["serving"] = serving_leg(cts, W, torch, local)
         except Exception as e:  # reported, never fatal for the bench line
             line["serving"] = {"error": repr(e)}
+        try:
+            big = large_n_leg(cts, W, torch, local, stream)
+            big["frac"] = big["step_kernel_tflops"] / peak_tflops
+            line["large_n"] = big
+        except Exception as e:  # reported, never fatal for the bench line
+            line["large_n"] = {"error": repr(e)}
         line["cpu_baseline"] = oracle_rate(args.workload, args.cpu_seconds)
         line["cpu_baseline"]["value_ratio_gpu_over_cpu"] = value / line["cpu_baseline"]["value"]
     print(json.dumps(line), flush=True)

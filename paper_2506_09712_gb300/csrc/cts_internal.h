@@ -27,6 +27,7 @@ constexpr int kElectronBit = 4;
 constexpr int kErrNumeric = 1;    // non-finite displacement
 constexpr int kErrTimeout = 2;    // bounded wait on a copy gave up
 constexpr int kErrBounds = 4;     // index outside its slot (checked build)
+constexpr int kErrPlan = 8;       // a unit descriptor disagrees with its slot
 
 constexpr float kParked = 1.0e18f;  // shadow coordinate of retired carriers
 constexpr int kChunkJ = 1024;       // j entries per shared-memory stage
@@ -79,17 +80,27 @@ struct ExplicitRec {
   int32_t sign;
 };
 
-// A unit of pair work: TI i's of one species of one slot against the j range
-// [j0, j1) of the concatenated [holes | electrons] list.
-struct Unit {
+// A unit of pair work as the step kernel reads it: TI i's of one species of
+// one slot against a j range of the concatenated [holes | electrons] list,
+// with the arena offsets resolved on the host so that the first source copy
+// and the i loads can start as soon as the descriptor arrives.
+struct alignas(16) Unit {
+  int64_t ioff;      // arena index of the first i
+  int64_t hoff;      // arena index of the first hole source
+  int64_t eoff;      // arena index of the first electron source
   int32_t slot;
-  int32_t spec;      // species of the i's: 0 holes, 1 electrons
-  int32_t i0, ni;
-  int32_t j0, j1;
-  int32_t split, nsplit;
+  int32_t flags;     // kUnit* bits
+  int32_t ni;        // i's in the unit
+  int32_t len_h;     // hole sources
+  int32_t len_e;     // electron sources
+  int32_t nsplit;    // pieces of the tile (> 1: FP64 accumulators + combine)
   int32_t iblock;    // combine counter (nsplit > 1)
-  int32_t pbase;     // float offset of the i-block's partial sums
+  int32_t pbase;     // FP64 offset of the tile's accumulators
 };
+static_assert(sizeof(Unit) == 64, "unit descriptor is four 16-byte words");
+constexpr int kUnitElectrons = 1;  // the i's are electrons
+constexpr int kUnitDuty = 2;       // the slot's per-step bookkeeping runs in this unit
+constexpr int kUnitOddStep = 4;    // the slot's chunk starts on an odd step
 
 // Summary of one slot after a chunk (copied to the host).
 struct SlotSummary {

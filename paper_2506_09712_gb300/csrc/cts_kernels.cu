@@ -413,6 +413,34 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
     const Unit U = a.units[u];
     if (!a.dynamic) ++u;
     SlotDev* S = a.slots + U.slot;
+    const int spec = U.flags & kUnitElectrons;
+    const int p = ((U.flags & kUnitOddStep ? 1 : 0) + k) & 1;
+    const float4* __restrict__ shin = a.A.sh[p];
+    const int nch_h = a.ph.repulsion ? (U.len_h + kChunkJ - 1) / kChunkJ : 0;
+    const int nch = a.ph.repulsion ? nch_h + (U.len_e + kChunkJ - 1) / kChunkJ : 0;
+    auto chunk_src = [&](int c, int& cnt) -> const float4* {
+      if (c < nch_h) {
+        cnt = min(kChunkJ, U.len_h - c * kChunkJ);
+        return shin + U.hoff + (int64_t)c * kChunkJ;
+      }
+      const int ce = c - nch_h;
+      cnt = min(kChunkJ, U.len_e - ce * kChunkJ);
+      return shin + U.eoff + (int64_t)ce * kChunkJ;
+    };
+    // The descriptor carries every offset, so the first source copy and the
+    // i loads go out before the slot's per-step scalars are known; a unit of
+    // a finished slot only waits for its copy and is dropped.
+    if (tid == 0 && nch > 0) {
+      int cnt;
+      const float4* src = chunk_src(0, cnt);
+      tma_load_1d(stage, src, (uint32_t)cnt * 16u, &bar[0]);
+    }
+    float4 qi[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int li = r * NT + tid;
+      qi[r] = li < U.ni ? shin[U.ioff + li] : make_float4(kParked, kParked, kParked, 0.0f);
+    }
     // Prologue, spread over warps so its latencies overlap: warp 0 sums the
     // slot's retire counters of the earlier steps of this chunk (one load per
     // lane), warps 1 and 2 predict the next frame anchor of each species.
@@ -429,31 +457,37 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
         if (lane == 0) {
           const int nah = S->act_h - dh, nae = S->act_e - de;
           const int step = S->step0 + k;
+          const bool plan_ok = (step & 1) == p;
+          if (!plan_ok) atomicOr(a.err, kErrPlan);
           s_nah = nah;
           s_nae = nae;
           s_step = step;
-          s_skip = (!S->running) || nah <= 0 || (int64_t)step >= a.ph.max_steps;
+          s_skip = !plan_ok || (!S->running) || nah <= 0 || (int64_t)step >= a.ph.max_steps;
         }
       } else if (warp <= 2 && lane == 0) {
-        const int spec = warp - 1;
-        const int p = (S->step0 + k) & 1;
-        s_azn[spec] = anchor_next(a.ph, spec, S->az[p][spec]);
-        if (spec == 1) s_off = (float)(S->az[p][1] - S->az[p][0]);
+        const int sp = warp - 1;
+        s_azn[sp] = anchor_next(a.ph, sp, S->az[p][sp]);
+        if (sp == 1) s_off = (float)(S->az[p][1] - S->az[p][0]);
       }
     }
     __syncthreads();
     if (s_skip) {
+      if (nch > 0) {
+        const bool ok = mbar_wait_bounded(&bar[0], uses[0] & 1u);
+        uses[0]++;
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0) atomicOr(a.err, kErrTimeout);
+          failed = true;
+          break;
+        }
+      }
       __syncthreads();
       continue;
     }
-    if (tid == 0 && a.fused && U.spec == 0 && U.i0 == 0 && U.split == 0)
+    if (tid == 0 && a.fused && (U.flags & kUnitDuty))
       slot_duties(a, S, s_step, s_step & 1, s_nah, s_nae, s_azn[0], s_azn[1]);
     const int step = s_step;
-    const int p = step & 1;
-    const float4* __restrict__ shin = a.A.sh[p];
-    const int64_t ibase = S->base + (U.spec ? S->cap_h : 0);
-    const int nh = S->n_h, ne = S->n_e;
-    pairs_done += (unsigned long long)U.ni * (unsigned long long)(U.j1 - U.j0);
+    pairs_done += (unsigned long long)U.ni * (unsigned long long)(U.len_h + U.len_e);
     n_units_done += 1;
     if (tid == 0 && a.trace) {
       const unsigned long long t = now_ns();
@@ -464,39 +498,15 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
     float xi[R], yi[R], zi[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int li = r * NT + tid;
-      const float4 q = li < U.ni ? shin[ibase + U.i0 + li]
-                                 : make_float4(kParked, kParked, kParked, 0.0f);
-      xi[r] = q.x;
-      yi[r] = q.y;
-      zi[r] = q.z + (U.spec ? s_off : 0.0f);  // hole frame
+      xi[r] = qi[r].x;
+      yi[r] = qi[r].y;
+      zi[r] = qi[r].z + (spec ? s_off : 0.0f);  // hole frame
     }
     float sx[R], sy[R], sz[R], cx[R], cy[R], cz[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) sx[r] = sy[r] = sz[r] = cx[r] = cy[r] = cz[r] = 0.0f;
 
     if (a.ph.repulsion) {
-      const int h0 = max(U.j0, 0), h1 = min(U.j1, nh);
-      const int e0 = max(U.j0, nh), e1 = min(U.j1, nh + ne);
-      const int len_h = max(h1 - h0, 0), len_e = max(e1 - e0, 0);
-      const int nch_h = (len_h + kChunkJ - 1) / kChunkJ;
-      const int nch = nch_h + (len_e + kChunkJ - 1) / kChunkJ;
-      const float4* src_h = shin + S->base + h0;
-      const float4* src_e = shin + S->base + S->cap_h + (e0 - nh);
-      auto chunk_src = [&](int c, int& cnt) -> const float4* {
-        if (c < nch_h) {
-          cnt = min(kChunkJ, len_h - c * kChunkJ);
-          return src_h + (int64_t)c * kChunkJ;
-        }
-        const int ce = c - nch_h;
-        cnt = min(kChunkJ, len_e - ce * kChunkJ);
-        return src_e + (int64_t)ce * kChunkJ;
-      };
-      if (tid == 0 && nch > 0) {
-        int cnt;
-        const float4* src = chunk_src(0, cnt);
-        tma_load_1d(stage, src, (uint32_t)cnt * 16u, &bar[0]);
-      }
       for (int c = 0; c < nch; ++c) {
         const int st = c & 1;
         int cnt;
@@ -523,8 +533,8 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int li = r * NT + tid;
-            const float zq = li < U.ni ? shin[ibase + U.i0 + li].z : kParked;
-            zi[r] = U.spec ? zq : zq - s_off;
+            const float zq = li < U.ni ? shin[U.ioff + li].z : kParked;
+            zi[r] = spec ? zq : zq - s_off;
           }
         }
         const float4* sj = stage + st * kChunkJ;
@@ -666,8 +676,8 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
       for (int r = 0; r < R; ++r) {
         const int li = r * NT + tid;
         if (li < U.ni)
-          update_carrier(a, S, U.slot, U.spec, ibase + U.i0 + li, step, p, k, kc * vx[r],
-                         kc * vy[r], kc * vz[r], s_azn[U.spec]);
+          update_carrier(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
+                         kc * vy[r], kc * vz[r], s_azn[spec]);
       }
     } else {
       const int64_t cap = a.A.capacity;
@@ -675,7 +685,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
       for (int r = 0; r < R; ++r) {
         const int li = r * NT + tid;
         if (li < U.ni) {
-          const int64_t idx = ibase + U.i0 + li;
+          const int64_t idx = U.ioff + li;
           a.field_out[idx] = kc * vx[r];
           a.field_out[cap + idx] = kc * vy[r];
           a.field_out[2 * cap + idx] = kc * vz[r];

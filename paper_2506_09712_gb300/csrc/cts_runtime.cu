@@ -420,6 +420,39 @@ StepArgs step_args(sim_t* s, bool fused) {
   return a;
 }
 
+// Where a slot's carriers sit in the arena, as the unit descriptors need it.
+struct SlotGeom {
+  int64_t base = 0;
+  int32_t cap_h = 0, n_h = 0;
+  int64_t step0 = 0;  // event-local step at the chunk start
+};
+
+// Device descriptors of planned units: arena offsets of each unit's i's and
+// of its hole and electron sources, and the parity of the slot's first step.
+void device_units(const std::vector<UnitPlan>& plan, const std::vector<SlotGeom>& g, Unit* out) {
+  for (size_t q = 0; q < plan.size(); ++q) {
+    const UnitPlan& u = plan[q];
+    const SlotGeom& sg = g[u.slot];
+    const int h1 = std::min(u.j1, sg.n_h);
+    const int e0 = std::max(u.j0, sg.n_h);
+    Unit d{};
+    d.ioff = sg.base + (u.spec ? sg.cap_h : 0) + u.i0;
+    d.hoff = sg.base + u.j0;
+    d.eoff = sg.base + sg.cap_h + (e0 - sg.n_h);
+    d.slot = u.slot;
+    d.flags = (u.spec ? kUnitElectrons : 0) |
+              (u.spec == 0 && u.i0 == 0 && u.split == 0 ? kUnitDuty : 0) |
+              ((sg.step0 & 1) ? kUnitOddStep : 0);
+    d.ni = u.ni;
+    d.len_h = std::max(h1 - u.j0, 0);
+    d.len_e = std::max(u.j1 - e0, 0);
+    d.nsplit = u.nsplit;
+    d.iblock = u.iblock;
+    d.pbase = u.pbase;
+    out[q] = d;
+  }
+}
+
 // Build and upload the unit list of the running slots.
 int upload_units(sim_t* s, bool allow_split) {
   std::vector<int32_t> nh(s->S, 0), ne(s->S, 0);
@@ -438,8 +471,15 @@ int upload_units(sim_t* s, bool allow_split) {
     return SIM_EINVAL;
   }
   const int n = (int)s->plan.size();
-  static_assert(sizeof(UnitPlan) == sizeof(Unit), "unit layout");
-  std::memcpy(s->h_units, s->plan.data(), n * sizeof(Unit));
+  std::vector<SlotGeom> geom(s->S);
+  for (int k = 0; k < s->S; ++k) {
+    const HostSlot& h = s->slots[k];
+    geom[k].base = h.base;
+    geom[k].cap_h = h.rec.cap_h;
+    geom[k].n_h = h.n_h;
+    geom[k].step0 = h.n_steps;
+  }
+  device_units(s->plan, geom, s->h_units);
   std::memcpy(s->h_cta_begin, s->plan_begin.data(), (s->grid + 1) * sizeof(int32_t));
   CK(h2d(s, s->d_units, s->h_units, std::max(n, 1) * sizeof(Unit)));
   CK(h2d(s, s->d_cta_begin, s->h_cta_begin, (s->grid + 1) * sizeof(int32_t)));
@@ -549,6 +589,11 @@ int run_chunk(sim_t* s) {
     s->broken = true;
     s->err = "a bounded device wait gave up";
     return SIM_ETIMEOUT;
+  }
+  if (*s->h_err & kErrPlan) {
+    s->broken = true;
+    s->err = "a unit descriptor disagrees with its slot on the device";
+    return SIM_ECUDA;
   }
   return SIM_OK;
 }
@@ -1260,7 +1305,10 @@ int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, in
     if ((e = cudaMemcpyAsync(d_slot, &sd, sizeof(SlotDev), cudaMemcpyHostToDevice, s->stream)) !=
         cudaSuccess)
       break;
-    std::memcpy(s->h_units, plan.data(), plan.size() * sizeof(Unit));
+    SlotGeom sg;
+    sg.cap_h = n_h;
+    sg.n_h = n_h;
+    device_units(plan, std::vector<SlotGeom>{sg}, s->h_units);
     std::memcpy(s->h_cta_begin, begin.data(), begin.size() * sizeof(int32_t));
     if ((e = cudaMemcpyAsync(s->d_units, s->h_units, std::max<size_t>(plan.size(), 1) * sizeof(Unit),
                              cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
