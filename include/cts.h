@@ -110,6 +110,10 @@ typedef struct sim_options_t {
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
   int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */
   int32_t time_launches;   /* 1 = time every step-kernel launch with CUDA events */
+  int32_t step_launches;   /* 1 = one step-kernel launch per step; 0 = one launch
+                              per chunk with dynamic-queue variants: a slot's
+                              next step starts as soon as all of its tiles are
+                              updated, without a device-wide barrier */
   void* stream;            /* cudaStream_t to launch on; NULL = own stream */
 } sim_options_t;
 
@@ -300,6 +304,15 @@ int cts_field_noalloc(const float* dev_x, const float* dev_y, const float* dev_z
  * (1-based; 0 = the current one); *ms_per_launch receives the mean launch
  * time from CUDA events.  The autotuner's measurement. */
 int sim_debug_time_step(sim_t* sim, int32_t variant, int32_t reps, double* ms_per_launch);
+
+/* Per-launch log of the step kernel, kept while the handle was created with
+ * options.time_launches != 0 (at most 1 << 20 entries, oldest dropped).
+ * Copies up to `cap` entries, oldest first, as triples (kernel ms from CUDA
+ * events around the launch, pair interactions the launch's units cover
+ * including carriers retired since the last compaction, events running in
+ * the chunk) into out[3 * cap], writes the count to *n_out and clears the
+ * log.  Returns SIM_OK or SIM_EINVAL. */
+int sim_debug_launch_log(sim_t* sim, double* out, int32_t cap, int32_t* n_out);
 
 /* Host-side fault injection for the failure-path tests: the next chunk (or
  * poll) reports the given code as if the device or queue had raised it

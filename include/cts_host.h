@@ -33,7 +33,9 @@ typedef struct cts_unit_t {
  * units [cta_begin[g], cta_begin[g+1]).  allow_split = 2: guided pieces for a
  * dynamic queue (largest first; piece sizes halve from w/2 to w/64 of a CTA's
  * share w over the last half of the work) that CTAs pull from;
- * cta_begin[grid] = number of units, the rest 0.
+ * cta_begin[grid] = number of units, the rest 0.  allow_split = 3: the same
+ * pieces ordered slot by slot, the halving applied within each slot's work
+ * (the queue a multi-step launch replays once per step).
  * allow_split = 0: whole tiles dealt out longest first.  Units are written to
  * out (capacity max_units); cta_begin has grid + 1 entries.  *n_out = units,
  * *partial_floats = FP64 partial-sum entries needed (limit partial_cap).

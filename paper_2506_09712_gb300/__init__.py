@@ -50,6 +50,7 @@ class sim_options_t(C.Structure):
                 ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32),
                 ("variant", C.c_int32), ("disable_graphs", C.c_int32),
                 ("keep_final_xy", C.c_int32), ("time_launches", C.c_int32),
+                ("step_launches", C.c_int32),
                 ("stream", C.c_void_p)]
 
 
@@ -90,7 +91,8 @@ class cts_unit_t(C.Structure):
 EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_execute",
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
-            "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_set_variants",
+            "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_debug_launch_log",
+            "sim_set_variants",
             "sim_get_variants", "sim_autotune", "sim_reset", "cts_field_noalloc", "cts_plan_units", "cts_arena_replay",
             "cts_estimate_steps"]
 
@@ -138,6 +140,7 @@ def load(build_if_missing: bool = True):
         "sim_debug_inject": [C.c_void_p, C.c_int],
         "sim_debug_trace_step": [C.c_void_p, P(u64), i32, P(i32)],
         "sim_debug_time_step": [C.c_void_p, i32, i32, P(d)],
+        "sim_debug_launch_log": [C.c_void_p, P(d), i32, P(i32)],
         "sim_set_variants": [C.c_void_p, P(i64), P(i32), i32],
         "sim_reset": [C.c_void_p],
         "sim_get_variants": [C.c_void_p, P(i64), P(i32), i32, P(i32)],
@@ -280,6 +283,16 @@ def sim_debug_trajectory(h, event: sim_event_t, n_steps, n_carriers):
 
 def sim_debug_inject(h, fault):
     return load().sim_debug_inject(h, int(fault))
+
+
+def sim_debug_launch_log(h, cap=1 << 20):
+    """Per-launch (kernel ms, pair interactions covered, events running) rows
+    of the step kernel since the last call (handle made with time_launches)."""
+    out = np.zeros((cap, 3), dtype=np.float64)
+    n = C.c_int32(0)
+    _check(load().sim_debug_launch_log(h, out.ctypes.data_as(C.POINTER(C.c_double)), int(cap),
+                                       C.byref(n)), "sim_debug_launch_log")
+    return out[:n.value].copy()
 
 
 def sim_debug_time_step(h, variant=0, reps=3):

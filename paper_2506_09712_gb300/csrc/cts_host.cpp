@@ -31,15 +31,19 @@ struct Tile {
 
 int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, int grid,
                bool allow_split, int max_units, int64_t partial_cap, std::vector<UnitPlan>* out,
-               std::vector<int32_t>* cta_begin, int64_t* partial_floats, bool dynamic) {
+               std::vector<int32_t>* cta_begin, int64_t* partial_floats, bool dynamic,
+               bool slot_major) {
   out->clear();
   cta_begin->assign((size_t)std::max(grid, 0) + 1, 0);
   *partial_floats = 0;
   if (tile_i <= 0 || grid <= 0 || n_slots < 0 || max_units <= 0) return -1;
   std::vector<Tile> tiles;
+  std::vector<double> slot_c0((size_t)std::max(n_slots, 0), 0.0), slot_w(slot_c0);
   double W = 0.0;
   for (int s = 0; s < n_slots; ++s) {
     const int nh = std::max(n_h[s], 0), ne = std::max(n_e[s], 0);
+    slot_c0[s] = W;
+    slot_w[s] = (double)(nh + ne) * (double)(nh + ne);
     if (nh <= 0) continue;  // an event with no hole is finished
     const int n = nh + ne;
     for (int spec = 0; spec < 2; ++spec) {
@@ -105,9 +109,11 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
     std::vector<Piece> pieces;
     for (size_t ti = 0; ti < tiles.size(); ++ti) {
       const Tile& t = tiles[ti];
-      const double f = t.c0 / W;
+      // position of the tile in the work the schedule drains: the whole step,
+      // or (slot_major) its own slot's step
+      const double f = slot_major ? (t.c0 - slot_c0[t.slot]) / slot_w[t.slot] : t.c0 / W;
       // factoring: the first half of the work in pieces of w/2, the next
-      // quarter in w/4, ... down to w/32
+      // quarter in w/4, ... down to w/64
       const double target = f < 0.5 ? 0.5 * w : f < 0.75 ? 0.25 * w : f < 0.875 ? 0.125 * w
                           : f < 0.9375 ? w / 16.0 : f < 0.96875 ? w / 32.0 : w / 64.0;
       int ns = (int)std::max(1.0, std::ceil((double)t.ni * t.n / target));
@@ -131,6 +137,8 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
         pfl += (int64_t)3 * tile_i;
       }
     std::stable_sort(pieces.begin(), pieces.end(), [&](const Piece& a, const Piece& b) {
+      if (slot_major && tiles[a.t].slot != tiles[b.t].slot)
+        return tiles[a.t].slot < tiles[b.t].slot;
       return (double)tiles[a.t].ni * (a.j1 - a.j0) > (double)tiles[b.t].ni * (b.j1 - b.j0);
     });
     if ((int64_t)pieces.size() > max_units) return -2;
@@ -271,7 +279,8 @@ int cts_plan_units(const int32_t* n_h, const int32_t* n_e, int32_t n_slots, int3
   std::vector<cts::UnitPlan> units;
   std::vector<int32_t> begin;
   const int rc = cts::plan_units(n_h, n_e, n_slots, tile_i, grid, allow_split != 0, max_units,
-                                 partial_cap, &units, &begin, partial_floats, allow_split == 2);
+                                 partial_cap, &units, &begin, partial_floats, allow_split >= 2,
+                                 allow_split == 3);
   if (rc != 0) return rc;
   for (size_t k = 0; k < units.size(); ++k) {
     const cts::UnitPlan& u = units[k];

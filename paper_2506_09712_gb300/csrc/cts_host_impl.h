@@ -18,10 +18,14 @@ struct UnitPlan {
 // Static mode: cta_begin receives grid + 1 offsets, CTA g runs units
 // [begin[g], begin[g+1]).  Dynamic mode: units form one queue (largest first)
 // that CTAs pull from with an atomic counter; cta_begin is all zeros except
-// begin[grid] = number of units.
+// begin[grid] = number of units.  slot_major (dynamic only): the queue holds
+// each slot's pieces together, slot after slot, the piece sizes shrinking
+// within each slot, so that a queue replayed for several steps finishes every
+// slot's step long before the slot's next step is reached.
 int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, int grid,
                bool allow_split, int max_units, int64_t partial_cap, std::vector<UnitPlan>* out,
-               std::vector<int32_t>* cta_begin, int64_t* partial_floats, bool dynamic);
+               std::vector<int32_t>* cta_begin, int64_t* partial_floats, bool dynamic,
+               bool slot_major = false);
 
 class ArenaAllocator {
  public:

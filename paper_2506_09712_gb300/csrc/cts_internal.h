@@ -96,6 +96,8 @@ struct alignas(16) Unit {
   int32_t nsplit;    // pieces of the tile (> 1: FP64 accumulators + combine)
   int32_t iblock;    // combine counter (nsplit > 1)
   int32_t pbase;     // FP64 offset of the tile's accumulators
+  int32_t ntiles;    // tiles of the slot (its step is done when all are updated)
+  int32_t pad;
 };
 static_assert(sizeof(Unit) == 64, "unit descriptor is four 16-byte words");
 constexpr int kUnitElectrons = 1;  // the i's are electrons
@@ -143,6 +145,7 @@ struct StepArgs {
   int32_t* ret;              // [K][S][2]
   double* partial;           // FP64 accumulators of split tiles (3 x tile_i each, kept zero)
   int32_t* combine_count;    // per i-block
+  int32_t* tiles_done;       // [K][S]: tiles of each slot updated at each chunk step
   float* field_out;          // FIELD_ONLY output, SoA [3][capacity]
   int32_t* err;              // global error bits
   unsigned long long* trace; // optional: per CTA {smid, t_start, t_end, pairs, units,
@@ -165,7 +168,9 @@ Variant variant_info(int v);
 cudaError_t variant_occupancy(int v, int* blocks_per_sm);
 size_t variant_smem(int v);
 
-cudaError_t launch_step(int v, const StepArgs& a, int k, int grid, cudaStream_t s);
+// Steps k0 .. k0 + nk - 1 of the chunk in one launch (nk > 1 needs a dynamic
+// variant and a slot-major plan).
+cudaError_t launch_step(int v, const StepArgs& a, int k0, int nk, int grid, cudaStream_t s);
 cudaError_t launch_update(const StepArgs& a, int k, int n_slots_list, const int32_t* slot_list,
                           int grid, cudaStream_t s);
 cudaError_t launch_init(const Phys& ph, Arena A, SlotDev* slots, const int32_t* slot_list,

@@ -142,6 +142,26 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   return false;
 }
 
+// Bounded wait for a counter written by other CTAs of the launch to reach
+// target (acquire); about two seconds at most, then false.
+constexpr unsigned long long kCountWaitNs = 2000000000ull;
+__device__ __forceinline__ bool wait_count_bounded(const int32_t* ctr, int target) {
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (uint32_t it = 0;; ++it) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+    if (v >= target) {
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+      return true;
+    }
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > kCountWaitNs) return false;
+    __nanosleep(it < 32 ? 64 : 512);
+  }
+}
+
 __device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -232,8 +252,9 @@ __device__ __forceinline__ void pair_chunk_packed(const float4* __restrict__ sj,
 // yields the (x_j, x_j+1) and (x_j+2, x_j+3) register pairs directly; the i
 // position is held duplicated, (x_i, x_i).  m is a multiple of 4 (the copy is
 // padded with parked sources, which contribute exactly zero).  Accumulators
-// hold (sum over even j, sum over odd j).
-template <int R, bool NEG>
+// hold (sum over even j, sum over odd j).  Only the first RA of the R i slots
+// are computed (the rest of a ragged tile holds no carriers).
+template <int R, int RA, bool NEG>
 __device__ __forceinline__ void pair_chunk_jpacked(const float* __restrict__ xs,
                                                    const float* __restrict__ ys,
                                                    const float* __restrict__ zs, int m,
@@ -254,7 +275,7 @@ __device__ __forceinline__ void pair_chunk_jpacked(const float* __restrict__ xs,
       const float2 qy = h ? make_float2(Y.z, Y.w) : make_float2(Y.x, Y.y);
       const float2 qz = h ? make_float2(Z.z, Z.w) : make_float2(Z.x, Z.y);
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
+      for (int r = 0; r < RA; ++r) {
         const float2 dx = NEG ? __ffma2_rn(xi[r], m1, qx) : __ffma2_rn(qx, m1, xi[r]);
         const float2 dy = NEG ? __ffma2_rn(yi[r], m1, qy) : __ffma2_rn(qy, m1, yi[r]);
         const float2 dz = NEG ? __ffma2_rn(zi[r], m1, qz) : __ffma2_rn(qz, m1, zi[r]);
@@ -289,12 +310,12 @@ __device__ __forceinline__ void update_carrier(const StepArgs& a, SlotDev* S, in
   float4* __restrict__ shout = a.A.sh[p ^ 1];
   const int id = a.A.cid[idx];
   const int64_t rid = S->base + id;
-  const int8_t st = a.A.cstate[rid];
+  const int8_t st = __ldcg(a.A.cstate + rid);
   if ((st & kStateMask) != kStateActive) {
     shout[idx] = make_float4(kParked, kParked, kParked, 0.0f);
     return;
   }
-  double x = a.A.px[idx], y = a.A.py[idx], z = a.A.pz[idx];
+  double x = __ldcg(a.A.px + idx), y = __ldcg(a.A.py + idx), z = __ldcg(a.A.pz + idx);
   if (ph.drift) Ez -= ph.f_ea - ph.f_eb * (float)z;
   const float Em = sqrtf(Ex * Ex + Ey * Ey + Ez * Ez);
   const float mu = mobility_f(ph, spec, Em);
@@ -364,7 +385,7 @@ __device__ __forceinline__ void active_counts(const StepArgs& a, const SlotDev* 
 // MODE 0: scalar FP32 pair loop; 1: packed over pairs of i's; 2: packed over
 // pairs of sources (struct-of-arrays copy of each chunk in shared memory).
 template <int NT, int R, int MODE, int JU, int MINB>
-__global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
+__global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int nk) {
   constexpr int TI = NT * R;
   static_assert(MODE != 1 || R % 2 == 0, "packed-i variants pair i's two by two");
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -396,23 +417,40 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
     return t;
   };
   if (a.trace && tid == 0) t_start = now_ns();
-  // this CTA's share of the step's pair work: a static equal-cost range, or
-  // pieces pulled from the step's queue
+  // This CTA's share of the launch's pair work: a static equal-cost range of
+  // one step, or pieces pulled from the queue, which lists the step's units
+  // once for each of the nk steps k0 .. k0 + nk - 1 of the launch.
   __shared__ int s_u;
-  const int u_begin = a.dynamic ? 0 : a.cta_begin[blockIdx.x];
-  const int u_end = a.dynamic ? a.cta_begin[gridDim.x] : a.cta_begin[blockIdx.x + 1];
-  int u = u_begin;
+  const int n_u = a.cta_begin[gridDim.x];
+  const int q_begin = a.dynamic ? 0 : a.cta_begin[blockIdx.x];
+  const int q_end = a.dynamic ? n_u * nk : a.cta_begin[blockIdx.x + 1];
+  int q = q_begin;
   for (;;) {
     if (a.dynamic) {
-      if (tid == 0) s_u = atomicAdd(&a.unit_counter[k], 1);
+      if (tid == 0) s_u = atomicAdd(&a.unit_counter[k0], 1);
       __syncthreads();
-      u = s_u;
+      q = s_u;
     }
-    if (u >= u_end) break;
+    if (q >= q_end) break;
     if (tid == 0) t_mark = now_ns();
-    const Unit U = a.units[u];
-    if (!a.dynamic) ++u;
+    const int kq = a.dynamic ? q / n_u : 0;
+    const int k = k0 + kq;
+    const Unit U = a.units[a.dynamic ? q - kq * n_u : q];
+    if (!a.dynamic) ++q;
     SlotDev* S = a.slots + U.slot;
+    if (kq > 0) {
+      // A later step of the launch starts once every tile of the slot has
+      // been updated at the step before.  The pieces of that step sit earlier
+      // in the queue and were taken by running CTAs, so the wait ends.
+      bool ok = true;
+      if (tid == 0)
+        ok = wait_count_bounded(a.tiles_done + (int64_t)(k - 1) * a.S + U.slot, U.ntiles);
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(a.err, kErrTimeout);
+        failed = true;
+        break;
+      }
+    }
     const int spec = U.flags & kUnitElectrons;
     const int p = ((U.flags & kUnitOddStep ? 1 : 0) + k) & 1;
     const float4* __restrict__ shin = a.A.sh[p];
@@ -439,7 +477,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int li = r * NT + tid;
-      qi[r] = li < U.ni ? shin[U.ioff + li] : make_float4(kParked, kParked, kParked, 0.0f);
+      qi[r] = li < U.ni ? __ldcg(shin + U.ioff + li) : make_float4(kParked, kParked, kParked, 0.0f);
     }
     // Prologue, spread over warps so its latencies overlap: warp 0 sums the
     // slot's retire counters of the earlier steps of this chunk (one load per
@@ -449,8 +487,8 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
       if (warp == 0) {
         int dh = 0, de = 0;
         for (int kk = lane; kk < k; kk += 32) {
-          dh += a.ret[((int64_t)kk * a.S + U.slot) * 2 + 0];
-          de += a.ret[((int64_t)kk * a.S + U.slot) * 2 + 1];
+          dh += __ldcg(a.ret + ((int64_t)kk * a.S + U.slot) * 2 + 0);
+          de += __ldcg(a.ret + ((int64_t)kk * a.S + U.slot) * 2 + 1);
         }
         dh = __reduce_add_sync(0xffffffffu, dh);
         de = __reduce_add_sync(0xffffffffu, de);
@@ -466,29 +504,31 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
         }
       } else if (warp <= 2 && lane == 0) {
         const int sp = warp - 1;
-        s_azn[sp] = anchor_next(a.ph, sp, S->az[p][sp]);
-        if (sp == 1) s_off = (float)(S->az[p][1] - S->az[p][0]);
+        s_azn[sp] = anchor_next(a.ph, sp, __ldcg(&S->az[p][sp]));
+        if (sp == 1) s_off = (float)(__ldcg(&S->az[p][1]) - __ldcg(&S->az[p][0]));
       }
     }
     __syncthreads();
-    if (s_skip) {
-      if (nch > 0) {
-        const bool ok = mbar_wait_bounded(&bar[0], uses[0] & 1u);
-        uses[0]++;
-        if (__syncthreads_or(!ok)) {
-          if (tid == 0) atomicOr(a.err, kErrTimeout);
-          failed = true;
-          break;
-        }
+    // A finished slot runs no pairs: its pieces only let the copy issued above
+    // land and take part in the tile's completion below.
+    const bool skip = s_skip;
+    if (skip && nch > 0) {
+      const bool ok = mbar_wait_bounded(&bar[0], uses[0] & 1u);
+      uses[0]++;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(a.err, kErrTimeout);
+        failed = true;
+        break;
       }
-      __syncthreads();
-      continue;
     }
-    if (tid == 0 && a.fused && (U.flags & kUnitDuty))
+    const int nch_run = skip ? 0 : nch;
+    if (!skip && tid == 0 && a.fused && (U.flags & kUnitDuty))
       slot_duties(a, S, s_step, s_step & 1, s_nah, s_nae, s_azn[0], s_azn[1]);
     const int step = s_step;
-    pairs_done += (unsigned long long)U.ni * (unsigned long long)(U.len_h + U.len_e);
-    n_units_done += 1;
+    if (!skip) {
+      pairs_done += (unsigned long long)U.ni * (unsigned long long)(U.len_h + U.len_e);
+      n_units_done += 1;
+    }
     if (tid == 0 && a.trace) {
       const unsigned long long t = now_ns();
       ns_pro += t - t_mark;
@@ -507,11 +547,11 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
     for (int r = 0; r < R; ++r) sx[r] = sy[r] = sz[r] = cx[r] = cy[r] = cz[r] = 0.0f;
 
     if (a.ph.repulsion) {
-      for (int c = 0; c < nch; ++c) {
+      for (int c = 0; c < nch_run; ++c) {
         const int st = c & 1;
         int cnt;
         chunk_src(c, cnt);
-        if (tid == 0 && c + 1 < nch) {
+        if (tid == 0 && c + 1 < nch_run) {
           int cn;
           const float4* src = chunk_src(c + 1, cn);
           tma_load_1d(stage + (st ^ 1) * kChunkJ, src, (uint32_t)cn * 16u, &bar[st ^ 1]);
@@ -523,7 +563,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
           // a bounded wait, and stop this CTA.
           if (tid == 0) {
             atomicOr(a.err, kErrTimeout);
-            if (c + 1 < nch) mbar_wait_bounded(&bar[st ^ 1], uses[st ^ 1] & 1u);
+            if (c + 1 < nch_run) mbar_wait_bounded(&bar[st ^ 1], uses[st ^ 1] & 1u);
           }
           failed = true;
           break;
@@ -533,7 +573,7 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int li = r * NT + tid;
-            const float zq = li < U.ni ? shin[U.ioff + li].z : kParked;
+            const float zq = li < U.ni ? __ldcg(shin + U.ioff + li).z : kParked;
             zi[r] = spec ? zq : zq - s_off;
           }
         }
@@ -562,12 +602,25 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
               qz2[r] = make_float2(zi[r], zi[r]);
               ax2[r] = ay2[r] = az2[r] = make_float2(0.0f, 0.0f);
             }
-            if (c < nch_h)
-              pair_chunk_jpacked<R, false>(soa_x + sub, soa_y + sub, soa_z + sub, m, qx2, qy2,
-                                           qz2, ax2, ay2, az2, eps2);
-            else
-              pair_chunk_jpacked<R, true>(soa_x + sub, soa_y + sub, soa_z + sub, m, qx2, qy2,
-                                          qz2, ax2, ay2, az2, eps2);
+            // a tile whose carriers fill at most half of the i slots computes
+            // only that half
+            constexpr int RH = R > 1 ? R / 2 : 1;
+            const bool half = R > 1 && U.ni <= RH * NT;
+            if (c < nch_h) {
+              if (half)
+                pair_chunk_jpacked<R, RH, false>(soa_x + sub, soa_y + sub, soa_z + sub, m, qx2,
+                                                 qy2, qz2, ax2, ay2, az2, eps2);
+              else
+                pair_chunk_jpacked<R, R, false>(soa_x + sub, soa_y + sub, soa_z + sub, m, qx2,
+                                                qy2, qz2, ax2, ay2, az2, eps2);
+            } else {
+              if (half)
+                pair_chunk_jpacked<R, RH, true>(soa_x + sub, soa_y + sub, soa_z + sub, m, qx2,
+                                                qy2, qz2, ax2, ay2, az2, eps2);
+              else
+                pair_chunk_jpacked<R, R, true>(soa_x + sub, soa_y + sub, soa_z + sub, m, qx2,
+                                               qy2, qz2, ax2, ay2, az2, eps2);
+            }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
               tx[r] = ax2[r].x + ax2[r].y;
@@ -628,19 +681,22 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
       vz[r] = sz[r] - cz[r];
     }
 
+    // Completion of the tile: each piece adds its compensated sum (S - c of
+    // two FP32 values is exact in FP64) into the tile's FP64 accumulators; the
+    // CTA finishing the tile's last piece reads them once, clears them for the
+    // next step, updates the tile's carriers and counts the tile as done.
+    bool last = true;
     if (U.nsplit > 1) {
-      // Add the piece's compensated sum (S - c of two FP32 values is exact in
-      // FP64) into the tile's FP64 accumulators; the CTA finishing the tile's
-      // last piece reads them once, clears them for the next step and goes on
-      // to the update.
       double* acc = a.partial + U.pbase;
+      if (!skip) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int li = r * NT + tid;
-        if (li < U.ni) {
-          atomicAdd(acc + li, (double)sx[r] - (double)cx[r]);
-          atomicAdd(acc + TI + li, (double)sy[r] - (double)cy[r]);
-          atomicAdd(acc + 2 * TI + li, (double)sz[r] - (double)cz[r]);
+        for (int r = 0; r < R; ++r) {
+          const int li = r * NT + tid;
+          if (li < U.ni) {
+            atomicAdd(acc + li, (double)sx[r] - (double)cx[r]);
+            atomicAdd(acc + TI + li, (double)sy[r] - (double)cy[r]);
+            atomicAdd(acc + 2 * TI + li, (double)sz[r] - (double)cz[r]);
+          }
         }
       }
       __threadfence();
@@ -651,45 +707,54 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k) {
         if (s_last) a.combine_count[U.iblock] = 0;
       }
       __syncthreads();
-      if (!s_last) {
-        __syncthreads();
-        continue;
-      }
-      __threadfence();
+      last = s_last;
+      if (last && !skip) {
+        __threadfence();
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int li = r * NT + tid;
-        if (li < U.ni) {
-          vx[r] = (float)__ldcg(acc + li);
-          vy[r] = (float)__ldcg(acc + TI + li);
-          vz[r] = (float)__ldcg(acc + 2 * TI + li);
-          acc[li] = 0.0;
-          acc[TI + li] = 0.0;
-          acc[2 * TI + li] = 0.0;
+        for (int r = 0; r < R; ++r) {
+          const int li = r * NT + tid;
+          if (li < U.ni) {
+            vx[r] = (float)__ldcg(acc + li);
+            vy[r] = (float)__ldcg(acc + TI + li);
+            vz[r] = (float)__ldcg(acc + 2 * TI + li);
+            acc[li] = 0.0;
+            acc[TI + li] = 0.0;
+            acc[2 * TI + li] = 0.0;
+          }
         }
       }
     }
 
-    const float kc = a.ph.f_kc;
-    if (a.fused) {
+    if (last) {
+      const float kc = a.ph.f_kc;
+      if (skip) {
+      } else if (a.fused) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int li = r * NT + tid;
-        if (li < U.ni)
-          update_carrier(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
-                         kc * vy[r], kc * vz[r], s_azn[spec]);
-      }
-    } else {
-      const int64_t cap = a.A.capacity;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int li = r * NT + tid;
-        if (li < U.ni) {
-          const int64_t idx = U.ioff + li;
-          a.field_out[idx] = kc * vx[r];
-          a.field_out[cap + idx] = kc * vy[r];
-          a.field_out[2 * cap + idx] = kc * vz[r];
+        for (int r = 0; r < R; ++r) {
+          const int li = r * NT + tid;
+          if (li < U.ni)
+            update_carrier(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
+                           kc * vy[r], kc * vz[r], s_azn[spec]);
         }
+      } else {
+        const int64_t cap = a.A.capacity;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const int li = r * NT + tid;
+          if (li < U.ni) {
+            const int64_t idx = U.ioff + li;
+            a.field_out[idx] = kc * vx[r];
+            a.field_out[cap + idx] = kc * vy[r];
+            a.field_out[2 * cap + idx] = kc * vz[r];
+          }
+        }
+      }
+      // publish the tile's positions, states and counters before counting it
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        atomicAdd(a.tiles_done + (int64_t)k * a.S + U.slot, 1);
       }
     }
     if (tid == 0 && a.trace) ns_epi += now_ns() - t_mark;
@@ -1069,7 +1134,7 @@ __global__ void normals_kernel(const unsigned long long* in, int64_t n, double* 
 struct VariantEntry {
   int nt, r;
   const char* name;
-  void (*fn)(StepArgs, int);
+  void (*fn)(StepArgs, int, int);
   int ctas_per_sm, dynamic, mode;
 };
 
@@ -1081,6 +1146,7 @@ struct VariantEntry {
   {NT, R, NAME, step_kernel<NT, R, MODE, JU, MB>, CPS, DYN, MODE}
 const VariantEntry kVariants[] = {
     CTS_V(256, 2, 2, 4, 3, 0, 1, "nt256_r2_jpair_dyn"),
+    CTS_V(256, 4, 2, 4, 2, 0, 1, "nt256_r4_jpair_dyn"),
     CTS_V(128, 2, 2, 4, 6, 0, 1, "nt128_r2_jpair_dyn"),
     CTS_V(128, 4, 2, 4, 4, 0, 1, "nt128_r4_jpair_dyn"),
     CTS_V(512, 1, 2, 4, 2, 0, 1, "nt512_r1_jpair_dyn"),
@@ -1116,9 +1182,9 @@ cudaError_t variant_occupancy(int v, int* blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.nt, smem_of(e));
 }
 
-cudaError_t launch_step(int v, const StepArgs& a, int k, int grid, cudaStream_t s) {
+cudaError_t launch_step(int v, const StepArgs& a, int k0, int nk, int grid, cudaStream_t s) {
   const VariantEntry& e = kVariants[v];
-  e.fn<<<grid, e.nt, smem_of(e), s>>>(a, k);
+  e.fn<<<grid, e.nt, smem_of(e), s>>>(a, k0, nk);
   return cudaGetLastError();
 }
 

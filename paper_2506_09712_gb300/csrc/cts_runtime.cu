@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -33,6 +34,7 @@ double now_ns() {
 
 constexpr int kDefaultSlots = 256;
 constexpr int kDefaultK = 32;
+constexpr size_t kLaunchLogCap = size_t(1) << 20;
 constexpr int64_t kDefaultBudget = 1ll << 30;
 constexpr int kMaxUnits = 1 << 16;
 constexpr int kDefaultQueue = 1 << 16;
@@ -102,6 +104,7 @@ struct sim_t {
   int32_t* d_ret = nullptr;
   double* d_partial = nullptr;
   int32_t* d_combine = nullptr;
+  int32_t* d_tiles_done = nullptr;
   int32_t* d_err = nullptr;
   float* d_field = nullptr;
   ExplicitRec* d_explicit = nullptr;
@@ -121,6 +124,7 @@ struct sim_t {
   // host state
   std::vector<HostSlot> slots;
   ArenaAllocator alloc;
+  std::deque<std::array<double, 3>> launch_log;  // (ms, pairs, running) per step launch
   std::vector<UnitPlan> plan;
   std::vector<int32_t> plan_begin;
   std::mutex qmu;
@@ -136,7 +140,8 @@ struct sim_t {
   int inject = 0;
   std::vector<int> staged;  // slots admitted by sim_stage, in staging order
 
-  // one captured K-step chunk per kernel variant
+  // one captured K-step chunk per kernel variant and launch shape
+  // (index 2 * variant + 1 for one launch per chunk)
   std::vector<cudaGraphExec_t> graphs;
   std::vector<int> graph_K;
   // per-variant occupancy (CTAs per SM), queried once
@@ -412,6 +417,7 @@ StepArgs step_args(sim_t* s, bool fused) {
   a.ret = s->d_ret;
   a.partial = s->d_partial;
   a.combine_count = s->d_combine;
+  a.tiles_done = s->d_tiles_done;
   a.field_out = s->d_field;
   a.err = s->d_err;
   a.ph = s->ph;
@@ -430,6 +436,10 @@ struct SlotGeom {
 // Device descriptors of planned units: arena offsets of each unit's i's and
 // of its hole and electron sources, and the parity of the slot's first step.
 void device_units(const std::vector<UnitPlan>& plan, const std::vector<SlotGeom>& g, Unit* out) {
+  // every tile has exactly one piece with split 0
+  std::vector<int32_t> ntiles(g.size(), 0);
+  for (const UnitPlan& u : plan)
+    if (u.split == 0) ++ntiles[u.slot];
   for (size_t q = 0; q < plan.size(); ++q) {
     const UnitPlan& u = plan[q];
     const SlotGeom& sg = g[u.slot];
@@ -449,12 +459,13 @@ void device_units(const std::vector<UnitPlan>& plan, const std::vector<SlotGeom>
     d.nsplit = u.nsplit;
     d.iblock = u.iblock;
     d.pbase = u.pbase;
+    d.ntiles = ntiles[u.slot];
     out[q] = d;
   }
 }
 
 // Build and upload the unit list of the running slots.
-int upload_units(sim_t* s, bool allow_split) {
+int upload_units(sim_t* s, bool allow_split, bool slot_major = false) {
   std::vector<int32_t> nh(s->S, 0), ne(s->S, 0);
   for (int k = 0; k < s->S; ++k)
     if (s->slots[k].used && s->slots[k].running) {
@@ -465,7 +476,7 @@ int upload_units(sim_t* s, bool allow_split) {
   const bool split = allow_split && s->ph.repulsion;
   const int rc = plan_units(nh.data(), ne.data(), s->S, s->tile_i, s->grid, split, kMaxUnits,
                             s->partial_cap, &s->plan, &s->plan_begin, &pfl,
-                            split && s->dynamic);
+                            split && s->dynamic, split && s->dynamic && slot_major);
   if (rc != 0) {
     s->err = "unit plan does not fit the unit buffer";
     return SIM_EINVAL;
@@ -486,15 +497,17 @@ int upload_units(sim_t* s, bool allow_split) {
   return SIM_OK;
 }
 
-// Issue one chunk: K fused steps (or, in PLAIN mode, field + update launches
-// for one step), the close kernel and the summary copy.
-int issue_chunk(sim_t* s, int K) {
+// Issue one chunk: K fused steps (one launch per chunk, or one per step), or
+// in PLAIN mode field + update launches for one step; then the close kernel
+// and the summary copy.
+int issue_chunk(sim_t* s, int K, bool multi) {
   const bool plain = s->opt.mode == CTS_MODE_PLAIN;
   CK(cudaMemsetAsync(s->d_unit_counter, 0, K * sizeof(int32_t), s->stream));
   CK(cudaMemsetAsync(s->d_ret, 0, (size_t)K * s->S * 2 * sizeof(int32_t), s->stream));
+  CK(cudaMemsetAsync(s->d_tiles_done, 0, (size_t)K * s->S * sizeof(int32_t), s->stream));
   if (plain) {
     const StepArgs a = step_args(s, false);
-    CK(launch_step(s->variant, a, 0, s->grid, s->stream));
+    CK(launch_step(s->variant, a, 0, 1, s->grid, s->stream));
     CK(launch_update(a, 0, 1, s->d_list, std::max(1, s->sm_count * 4), s->stream));
     s->st_launch += 2;
   } else {
@@ -503,11 +516,17 @@ int issue_chunk(sim_t* s, int K) {
     // inside a stream capture the events become external event-record nodes
     const unsigned evflag = capturing(s) ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (timed) CK(cudaEventRecordWithFlags(s->lev[0], s->stream, evflag));
-    for (int k = 0; k < K; ++k) {
-      CK(launch_step(s->variant, a, k, s->grid, s->stream));
-      if (timed) CK(cudaEventRecordWithFlags(s->lev[k + 1], s->stream, evflag));
+    if (multi) {
+      CK(launch_step(s->variant, a, 0, K, s->grid, s->stream));
+      if (timed) CK(cudaEventRecordWithFlags(s->lev[1], s->stream, evflag));
+      s->st_launch += 1;
+    } else {
+      for (int k = 0; k < K; ++k) {
+        CK(launch_step(s->variant, a, k, 1, s->grid, s->stream));
+        if (timed) CK(cudaEventRecordWithFlags(s->lev[k + 1], s->stream, evflag));
+      }
+      s->st_launch += K;
     }
-    s->st_launch += K;
   }
   CK(launch_close(s->ph, s->A, s->d_slots, nullptr, s->S, s->d_ret, s->S, K, s->d_summary,
                   s->stream));
@@ -539,12 +558,17 @@ int run_chunk(sim_t* s) {
     int rcv = set_variant(s, v);
     if (rcv) return rcv;
   }
-  int rc = upload_units(s, !plain);
+  // one launch for the whole chunk: the queue replays the step's pieces K
+  // times, slot by slot
+  const bool multi = !plain && s->dynamic && s->ph.repulsion && !s->opt.step_launches;
+  int rc = upload_units(s, !plain, multi);
   if (rc) return rc;
+  const int gi = 2 * s->variant + (multi ? 1 : 0);
+  const int nl = multi ? 1 : K;  // step-kernel launches in the chunk
   CK(cudaEventRecord(s->ev0, s->stream));
   if (!plain && !s->opt.disable_graphs) {
-    cudaGraphExec_t& graph = s->graphs[s->variant];
-    if (!graph || s->graph_K[s->variant] != K) {
+    cudaGraphExec_t& graph = s->graphs[gi];
+    if (!graph || s->graph_K[gi] != K) {
       if (graph) {
         cudaGraphExecDestroy(graph);
         graph = nullptr;
@@ -552,7 +576,7 @@ int run_chunk(sim_t* s) {
       cudaGraph_t g = nullptr;
       CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
       const int64_t launches = s->st_launch, hb = s->st_h2d, db = s->st_d2h;
-      rc = issue_chunk(s, K);
+      rc = issue_chunk(s, K, multi);
       s->st_launch = launches;
       s->st_h2d = hb;
       s->st_d2h = db;
@@ -561,13 +585,13 @@ int run_chunk(sim_t* s) {
       CK(ce);
       CK(cudaGraphInstantiate(&graph, g, 0));
       cudaGraphDestroy(g);
-      s->graph_K[s->variant] = K;
+      s->graph_K[gi] = K;
     }
     CK(cudaGraphLaunch(graph, s->stream));
-    s->st_launch += K + 1;
+    s->st_launch += nl + 1;
     s->st_d2h += (int64_t)s->S * sizeof(SlotSummary) + sizeof(int32_t);
   } else {
-    rc = issue_chunk(s, K);
+    rc = issue_chunk(s, K, multi);
     if (rc) return rc;
   }
   CK(cudaEventRecord(s->ev1, s->stream));
@@ -576,12 +600,18 @@ int run_chunk(sim_t* s) {
   CK(cudaEventElapsedTime(&ms, s->ev0, s->ev1));
   s->st_ms += ms;
   if (s->opt.time_launches && !plain) {
-    for (int k = 0; k < K; ++k) {
+    double pairs = 0.0;
+    for (const UnitPlan& u : s->plan) pairs += (double)u.ni * (double)(u.j1 - u.j0);
+    double running = 0.0;
+    for (const HostSlot& h : s->slots) running += h.used && h.running;
+    for (int k = 0; k < nl; ++k) {
       float lm = 0.f;
       CK(cudaEventElapsedTime(&lm, s->lev[k], s->lev[k + 1]));
       s->st_kernel_ms += lm;
+      if (s->launch_log.size() >= kLaunchLogCap) s->launch_log.pop_front();
+      s->launch_log.push_back({(double)lm, pairs * (K / nl), running});
     }
-    s->st_kernel_launches += K;
+    s->st_kernel_launches += nl;
   }
   s->st_steps += K;
   s->st_chunks += 1;
@@ -823,6 +853,7 @@ int alloc_all(sim_t* s) {
   AL(s->d_ret, (int64_t)kMaxK * s->S * 2);
   AL(s->d_partial, s->partial_cap);
   AL(s->d_combine, kMaxUnits);
+  AL(s->d_tiles_done, (int64_t)kMaxK * s->S);
   AL(s->d_err, 1);
   AL(s->d_explicit, C);
   AL(s->d_list, s->S);
@@ -854,7 +885,8 @@ void free_all(sim_t* s) {
   void* dev[] = {s->A.px, s->A.py, s->A.pz, s->A.sh[0], s->A.sh[1], s->A.cid, s->A.fx, s->A.fy,
                  s->A.rstep, s->A.cstate, s->d_slots, s->d_summary, s->d_readout, s->d_pixels,
                  s->d_units, s->d_cta_begin, s->d_unit_counter, s->d_ret, s->d_partial,
-                 s->d_combine, s->d_err, s->d_field, s->d_explicit, s->d_list};
+                 s->d_combine, s->d_tiles_done, s->d_err, s->d_field, s->d_explicit,
+                 s->d_list};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {s->h_summary, s->h_units, s->h_cta_begin, s->h_list, s->h_slotdev, s->h_readout,
@@ -961,8 +993,8 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
     }
     s->own_stream = true;
   }
-  s->graphs.assign(variant_count(), nullptr);
-  s->graph_K.assign(variant_count(), -1);
+  s->graphs.assign(2 * variant_count(), nullptr);
+  s->graph_K.assign(2 * variant_count(), -1);
   s->occ_cache.assign(variant_count(), 0);
   s->variant = -1;
   rc = alloc_all(s);
@@ -1324,7 +1356,7 @@ int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, in
     a.slots = d_slot;
     a.field_out = d_field;
     a.S = 1;
-    if ((e = launch_step(s->variant, a, 0, s->grid, s->stream)) != cudaSuccess) break;
+    if ((e = launch_step(s->variant, a, 0, 1, s->grid, s->stream)) != cudaSuccess) break;
     std::vector<float> f(3 * (size_t)n);
     if ((e = cudaMemcpyAsync(f.data(), d_field, 3 * (size_t)n * sizeof(float),
                              cudaMemcpyDeviceToHost, s->stream)) != cudaSuccess)
@@ -1371,7 +1403,7 @@ int sim_debug_trace_step(sim_t* s, uint64_t* out, int32_t max_ctas, int32_t* n_c
     StepArgs a = step_args(s, false);
     a.field_out = d_field;
     a.trace = d_trace;
-    if ((e = launch_step(s->variant, a, 0, s->grid, s->stream))) break;
+    if ((e = launch_step(s->variant, a, 0, 1, s->grid, s->stream))) break;
     if ((e = cudaMemcpyAsync(h.data(), d_trace, h.size() * sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, s->stream)))
       break;
@@ -1387,6 +1419,17 @@ int sim_debug_trace_step(sim_t* s, uint64_t* out, int32_t max_ctas, int32_t* n_c
   for (int g = 0; g < n; ++g)
     for (int q = 0; q < 8; ++q) out[8 * g + q] = h[8 * (size_t)g + q];
   *n_ctas = n;
+  return SIM_OK;
+}
+
+int sim_debug_launch_log(sim_t* s, double* out, int32_t cap, int32_t* n_out) {
+  if (!s || cap < 0 || !n_out || (cap > 0 && !out)) return SIM_EINVAL;
+  std::lock_guard<std::mutex> dl(s->drive_mu);
+  const int n = (int)std::min<size_t>((size_t)cap, s->launch_log.size());
+  for (int q = 0; q < n; ++q)
+    for (int c = 0; c < 3; ++c) out[3 * q + c] = s->launch_log[q][c];
+  s->launch_log.clear();
+  *n_out = n;
   return SIM_OK;
 }
 
@@ -1460,7 +1503,7 @@ int sim_debug_time_step(sim_t* s, int32_t variant, int32_t reps, double* ms_per_
     for (int r = 0; r <= reps && e == cudaSuccess; ++r) {  // launch 0 warms up
       if (r == 1 && (e = cudaEventRecord(s->ev0, s->stream))) break;
       if ((e = cudaMemsetAsync(s->d_unit_counter, 0, sizeof(int32_t), s->stream))) break;
-      if ((e = launch_step(s->variant, a, 0, s->grid, s->stream))) break;
+      if ((e = launch_step(s->variant, a, 0, 1, s->grid, s->stream))) break;
     }
     if (e) break;
     if ((e = cudaEventRecord(s->ev1, s->stream))) break;

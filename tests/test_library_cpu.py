@@ -221,3 +221,25 @@ def test_guided_dynamic_plan(lib, n_h, n_e):
     # the smallest pieces are much smaller than the largest when there is enough work
     if cost.sum() > 608 * 512 * 4096:
         assert cost[-1] * 8 <= cost[0]
+
+
+@pytest.mark.parametrize("n_h,n_e", [([5525] * 64, [0] * 64), ([5525] * 3, [0] * 3),
+                                     ([3000, 0, 900], [2000, 0, 10]), ([829], [0])])
+def test_slot_major_plan_for_multi_step_launches(lib, n_h, n_e):
+    # allow_split = 3: the same pieces, slot by slot, shrinking within each slot,
+    # so that a queue replayed over several steps finishes a slot's step well
+    # before the slot's next step comes up
+    rc, units, begin, pfl = cts.cts_plan_units(n_h, n_e, 512, 608, allow_split=3)
+    assert rc == 0
+    assert _check_cover(units, n_h, n_e)
+    assert begin[-1] == len(units) and np.all(begin[:-1] == 0)
+    slots = units[:, 0]
+    assert np.all(np.diff(slots) >= 0)                # slot-major
+    cost = units[:, 3] * (units[:, 5] - units[:, 4])
+    for s in np.unique(slots):
+        c = cost[slots == s]
+        assert np.all(np.diff(c) <= 0)                # largest first within the slot
+    # one slot: the same pieces as the single-step guided queue
+    if len(n_h) == 1:
+        rc2, units2, _, _ = cts.cts_plan_units(n_h, n_e, 512, 608, allow_split=2)
+        assert np.array_equal(units, units2)
