@@ -420,6 +420,13 @@ def run_ours(args, rank, world, local):
             "flops_per_pair": FLOPS_PER_PAIR,
             "step_kernel_ms": kms, "step_kernel_launches": kl,
             "kernel_share_of_timed": kms / (sum(ms)) if ms else None}
+    # the attainable FP32 FMA rate of FMA chains on this GPU (packed f32x2)
+    try:
+        fma = cts.sim_debug_fma_peak(local, True) / 1e12
+        roof["fma_chain_tflops"] = fma
+        roof["frac_of_fma_chain"] = achieved / fma if achieved else None
+    except cts.SimError:
+        pass
     if achieved and clocks.get("sm_mhz"):
         roof["frac_at_measured_clock"] = achieved / (
             sm_count * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)

@@ -305,6 +305,15 @@ int cts_field_noalloc(const float* dev_x, const float* dev_y, const float* dev_z
  * time from CUDA events.  The autotuner's measurement. */
 int sim_debug_time_step(sim_t* sim, int32_t variant, int32_t reps, double* ms_per_launch);
 
+/* FP32 FMA throughput of device `device` (CUDA ordinal) measured by chains of
+ * independent fused multiply-adds, packed f32x2 (packed = 1) or scalar: the
+ * attainable counterpart of the nominal FP32 peak that the pair kernel's
+ * 16 flops per interaction are compared with (Sec. 2.1, Eq. 4 is FP32 FMA
+ * work).  *flops_per_s receives the best of three timed launches (2 flops per
+ * FMA lane).  Allocates a small output buffer.  Returns SIM_OK, SIM_EINVAL,
+ * SIM_ENODEV or SIM_ECUDA. */
+int sim_debug_fma_peak(int32_t device, int32_t packed, double* flops_per_s);
+
 /* Per-launch log of the step kernel, kept while the handle was created with
  * options.time_launches != 0 (at most 1 << 20 entries, oldest dropped).
  * Copies up to `cap` entries, oldest first, as triples (kernel ms from CUDA

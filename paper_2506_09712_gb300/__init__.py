@@ -92,6 +92,7 @@ EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_e
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
             "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_debug_launch_log",
+            "sim_debug_fma_peak",
             "sim_set_variants",
             "sim_get_variants", "sim_autotune", "sim_reset", "cts_field_noalloc", "cts_plan_units", "cts_arena_replay",
             "cts_estimate_steps"]
@@ -141,6 +142,7 @@ def load(build_if_missing: bool = True):
         "sim_debug_trace_step": [C.c_void_p, P(u64), i32, P(i32)],
         "sim_debug_time_step": [C.c_void_p, i32, i32, P(d)],
         "sim_debug_launch_log": [C.c_void_p, P(d), i32, P(i32)],
+        "sim_debug_fma_peak": [i32, i32, P(d)],
         "sim_set_variants": [C.c_void_p, P(i64), P(i32), i32],
         "sim_reset": [C.c_void_p],
         "sim_get_variants": [C.c_void_p, P(i64), P(i32), i32, P(i32)],
@@ -283,6 +285,14 @@ def sim_debug_trajectory(h, event: sim_event_t, n_steps, n_carriers):
 
 def sim_debug_inject(h, fault):
     return load().sim_debug_inject(h, int(fault))
+
+
+def sim_debug_fma_peak(device=0, packed=True):
+    """Measured FP32 FMA throughput (flops/s) of FMA chains on `device`."""
+    v = C.c_double(0.0)
+    _check(load().sim_debug_fma_peak(int(device), 1 if packed else 0, C.byref(v)),
+           "sim_debug_fma_peak")
+    return v.value
 
 
 def sim_debug_launch_log(h, cap=1 << 20):

@@ -182,6 +182,8 @@ cudaError_t launch_bin(const Phys& ph, Arena A, const SlotDev* slots, const int3
                        int n, int32_t* pixels, SlotReadout* readout, cudaStream_t s);
 cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, int64_t n,
                               int32_t* pixels, long long* outside, cudaStream_t s);
+// 16 FMA lane-ops per thread and iteration; 256 threads per CTA.
+cudaError_t launch_fma_chain(bool packed, float* out, int grid, int iters, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                           uint32_t* curand_out, cudaStream_t s);
 cudaError_t launch_normals(const unsigned long long* in, int64_t n, double* out, cudaStream_t s);

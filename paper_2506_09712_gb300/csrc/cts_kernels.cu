@@ -1092,6 +1092,32 @@ __global__ void bin_points_kernel(Phys ph, const double* x, const double* y, int
 // ---------------------------------------------------------------------------
 // Test hooks.
 // ---------------------------------------------------------------------------
+// FP32 FMA throughput probe: independent FMA chains per thread (packed f32x2
+// or scalar), the denominator the pair kernel's FP32 work is compared with.
+template <bool PACKED>
+__global__ void __launch_bounds__(256) fma_chain_kernel(float* out, int iters) {
+  constexpr int C = 8;
+  float2 a[C];
+#pragma unroll
+  for (int q = 0; q < C; ++q) a[q] = make_float2(threadIdx.x * 1e-3f + q, 0.5f * q);
+  const float2 m = make_float2(0.999f, 0.999f), c = make_float2(1e-3f, 1e-3f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      if (PACKED) {
+        a[q] = __ffma2_rn(a[q], m, c);
+      } else {
+        a[q].x = fmaf(a[q].x, m.x, c.x);
+        a[q].y = fmaf(a[q].y, m.y, c.y);
+      }
+    }
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int q = 0; q < C; ++q) s += a[q].x + a[q].y;
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void philox_kernel(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                               uint32_t* curand_out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1222,6 +1248,14 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
   int grid = (int)((n + threads - 1) / threads);
   grid = grid < 1 ? 1 : (grid > 4096 ? 4096 : grid);
   bin_points_kernel<<<grid, threads, 0, s>>>(ph, x, y, n, pixels, outside);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fma_chain(bool packed, float* out, int grid, int iters, cudaStream_t s) {
+  if (packed)
+    fma_chain_kernel<true><<<grid, 256, 0, s>>>(out, iters);
+  else
+    fma_chain_kernel<false><<<grid, 256, 0, s>>>(out, iters);
   return cudaGetLastError();
 }
 

@@ -508,7 +508,13 @@ int issue_chunk(sim_t* s, int K, bool multi) {
   if (plain) {
     const StepArgs a = step_args(s, false);
     CK(launch_step(s->variant, a, 0, 1, s->grid, s->stream));
-    CK(launch_update(a, 0, 1, s->d_list, std::max(1, s->sm_count * 4), s->stream));
+    // one thread per carrier of the running event (the grid is captured
+    // nowhere: PLAIN chunks are launched directly)
+    int n = 0;
+    for (const HostSlot& h : s->slots)
+      if (h.used && h.running) n = std::max(n, h.n_h + h.n_e);
+    const int grid = std::min(std::max(1, (n + 255) / 256), s->sm_count * 4);
+    CK(launch_update(a, 0, 1, s->d_list, grid, s->stream));
     s->st_launch += 2;
   } else {
     const StepArgs a = step_args(s, true);
@@ -1644,6 +1650,40 @@ int sim_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32
   cudaFree(dout);
   if (dcur) cudaFree(dcur);
   return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
+int sim_debug_fma_peak(int32_t device, int32_t packed, double* flops_per_s) {
+  if (!flops_per_s || device < 0) return SIM_EINVAL;
+  int sms = 0;
+  if (check_device(device, &sms)) return SIM_ENODEV;
+  cudaSetDevice(device);
+  const int grid = sms * 8;  // 2048 threads per SM
+  const int iters = 1 << 11;
+  float* d = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaSuccess;
+  float best = 0.0f;
+  do {
+    if ((e = cudaMalloc(&d, (size_t)grid * 256 * sizeof(float)))) break;
+    if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) break;
+    if ((e = launch_fma_chain(packed != 0, d, grid, iters / 8, 0))) break;  // warm-up
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      if ((e = cudaEventRecord(e0, 0))) break;
+      if ((e = launch_fma_chain(packed != 0, d, grid, iters, 0))) break;
+      if ((e = cudaEventRecord(e1, 0))) break;
+      if ((e = cudaEventSynchronize(e1))) break;
+      float ms = 0.0f;
+      if ((e = cudaEventElapsedTime(&ms, e0, e1))) break;
+      if (best == 0.0f || ms < best) best = ms;
+    }
+  } while (0);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess || !(best > 0.0f)) return SIM_ECUDA;
+  // 16 FMA lane-ops = 32 flops per thread and iteration
+  *flops_per_s = (double)grid * 256.0 * iters * 32.0 / (best * 1e-3);
+  return SIM_OK;
 }
 
 int sim_debug_normals(const uint64_t* in, int64_t n, double* out) {

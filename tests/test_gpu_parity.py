@@ -421,3 +421,15 @@ def test_autotuned_variant_table_runs_and_matches():
     refs = oracle.run_events(oracle_params(name), evs)
     for g, r in zip(res, refs):
         _compare_events(g, r, 829)
+
+
+@pytest.mark.gpu
+def test_fma_chain_probe_is_within_the_nominal_peak():
+    # the attainable FP32 FMA rate: positive and not above the nominal
+    # SMs x 128 lanes x 2 flops x the highest SM clock
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2 * 2.2e9
+    for packed in (True, False):
+        f = cts.sim_debug_fma_peak(0, packed)
+        assert 0.3 * nominal < f < 1.02 * nominal, (packed, f, nominal)

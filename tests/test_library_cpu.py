@@ -89,6 +89,9 @@ def test_kernel_hooks_without_device(lib):
     with pytest.raises(cts.SimError) as e:
         cts.sim_debug_philox([[0, 0, 0, 0]], [[0, 0]])
     assert e.value.code == cts.SIM_ENODEV
+    with pytest.raises(cts.SimError) as e:
+        cts.sim_debug_fma_peak(0)
+    assert e.value.code == cts.SIM_ENODEV
 
 
 def _check_cover(units, n_h, n_e):
