@@ -107,6 +107,11 @@ def lib():
         _lib.or_run_event.restype = C.c_int
         _lib.or_run_events.argtypes = [P(_Params), P(_Event), i64, P(_Result)]
         _lib.or_max_threads.restype = C.c_int
+        _lib.or_fano_pairs.argtypes = [u64, u64, d, d]; _lib.or_fano_pairs.restype = i32
+        _lib.or_readout_event.argtypes = [P(i32), i32, u64, u64, d, d, d, d, d, P(d), P(d),
+                                          P(i32), P(i32), P(d), P(i32)]
+        _lib.or_readout_event.restype = C.c_int
+        _lib.or_spectrum_add.argtypes = [P(d), i32, d, d, i32, P(i64)]
     return _lib
 
 
@@ -199,6 +204,47 @@ def thermal_voltage(T):
 
 def n_pairs(energy_keV):
     return lib().or_n_pairs(energy_keV)
+
+
+def fano_pairs(seed, event_id, energy_keV, fano=0.13):
+    """Carrier pairs of one photon with Fano fluctuations (Sec. 4.2)."""
+    return lib().or_fano_pairs(int(seed), int(event_id), float(energy_keV), float(fano))
+
+
+# Readout parameters of the detector (Sec. 4.1 selection, Sec. 4.2 noise).
+READOUT_DEFAULTS = dict(ev_per_pair=3.62, noise_keV=0.13, window_keV=1.0, veto_factor=3.0,
+                        spec_lo_keV=0.0, spec_bin_keV=0.1)
+
+
+def readout(counts, seeds, event_ids, beam_keV, n_bins, **kw):
+    """Readout of events' pixel counts (n_ev x grid_n x grid_n): noisy pixel
+    energies, 3 x 3 cluster around the largest pixel, pile-up veto, energy
+    window and the single-pixel spectrum of the accepted clusters.  Returns a
+    dict of arrays: e (keV maps), cluster (n_ev x 9), cx, cy, e_cluster,
+    accepted, vetoed, spectrum (n_bins)."""
+    prm = dict(READOUT_DEFAULTS, **kw)
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    n_ev, g = counts.shape[0], counts.shape[1]
+    out = dict(e=np.zeros((n_ev, g, g)), cluster=np.zeros((n_ev, 9)),
+               cx=np.zeros(n_ev, np.int32), cy=np.zeros(n_ev, np.int32),
+               e_cluster=np.zeros(n_ev), accepted=np.zeros(n_ev, np.int32),
+               vetoed=np.zeros(n_ev, np.int32), spectrum=np.zeros(n_bins, np.int64))
+    L = lib()
+    for k in range(n_ev):
+        e = np.zeros(g * g); cl = np.zeros(9)
+        cx, cy, v = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        ec = C.c_double(0.0)
+        acc = L.or_readout_event(_ptr(counts[k], C.c_int32), g, int(seeds[k]), int(event_ids[k]),
+                                 prm["ev_per_pair"], prm["noise_keV"], float(beam_keV),
+                                 prm["window_keV"], prm["veto_factor"], _ptr(e, C.c_double),
+                                 _ptr(cl, C.c_double), C.byref(cx), C.byref(cy), C.byref(ec),
+                                 C.byref(v))
+        L.or_spectrum_add(_ptr(cl, C.c_double), acc, prm["spec_lo_keV"], prm["spec_bin_keV"],
+                          n_bins, _ptr(out["spectrum"], C.c_int64))
+        out["e"][k] = e.reshape(g, g); out["cluster"][k] = cl
+        out["cx"][k], out["cy"][k], out["e_cluster"][k] = cx.value, cy.value, ec.value
+        out["accepted"][k], out["vetoed"][k] = acc, v.value
+    return out
 
 
 def sigma_um(energy_keV):

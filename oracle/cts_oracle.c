@@ -21,7 +21,8 @@
  *   -E(z) e_z with E(z) = (Vb - Vd)/H + 2 Vd (H - z)/H^2.
  *
  * Parity status: pinned (closed forms, invariants, a library Philox, exact
- * small configurations) -- see tests/test_oracle_*.py.  The paper's own
+ * small configurations, hand-built readout maps and the statistics of the
+ * Fano and noise draws) -- see tests/test_oracle_*.py.  The paper's own
  * printed physics numbers (Table 1, GGD betas) depend on unprinted mobility
  * parameters and are checked only qualitatively.
  */
@@ -48,7 +49,8 @@ enum { OR_HOLES = 1, OR_BOTH = 3 };
 enum { OR_MOB_CT = 0, OR_MOB_CONST = 1 };
 enum { OR_PHOTON = 0, OR_TRACK = 1, OR_EXPLICIT = 2 };
 enum { OR_ACTIVE = 0, OR_COLLECTED = 1, OR_RETIRED = 2 };
-enum { OR_PURPOSE_DIFFUSION = 0, OR_PURPOSE_INIT = 1 };
+enum { OR_PURPOSE_DIFFUSION = 0, OR_PURPOSE_INIT = 1, OR_PURPOSE_FANO = 2,
+       OR_PURPOSE_NOISE = 3 };
 
 typedef struct {
   double thickness_um;   /* H */
@@ -481,4 +483,88 @@ int or_max_threads(void) {
 #else
   return 1;
 #endif
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Detector readout (Sec. 4.1 selection; Sec. 4.2 event generation).         */
+/* ------------------------------------------------------------------------ */
+
+/* Carrier-pair count with Fano statistics (Sec. 4.2 applies a Fano factor of
+ * 0.13): the mean is E / 3.62 eV and the variance F times the mean; a normal
+ * approximation, N = round(mean + sqrt(F * mean) * g), g the first normal of
+ * the event's FANO stream (carrier 0, step 0), at least 1 pair.  F = 0 gives
+ * or_n_pairs exactly. */
+int32_t or_fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano) {
+  const double mean = energy_keV * 1000.0 / OR_EV_PER_PAIR;
+  if (!(fano > 0.0)) return or_n_pairs(energy_keV);
+  double g[3];
+  or_normals3(seed, event_id, OR_PURPOSE_FANO, 0u, 0u, g);
+  const double n = floor(mean + sqrt(fano * mean) * g[0] + 0.5);
+  return n < 1.0 ? 1 : (int32_t)n;
+}
+
+/* Readout of one event's pixel counts (grid_n x grid_n, row-major, index
+ * iy * grid_n + ix), following the selection described in Sec. 4.1 and the
+ * generation in Sec. 4.2:
+ *   energy of pixel p: e_p = counts_p * ev_per_pair / 1000 + noise * g_p keV,
+ *     g_p the first normal of the event's NOISE stream at carrier p;
+ *   centre: the pixel of largest e (the first in row-major order on ties);
+ *   cluster: the 3 x 3 pixels around the centre that lie on the grid, its
+ *     energy the sum of their e;
+ *   pile-up veto: a pixel of the 7 x 7 window around the centre, outside the
+ *     3 x 3, on the grid, with e > veto_factor * noise rejects the event;
+ *   window: the event is accepted only if |cluster energy - beam| <= window.
+ * Pixels off the grid are not read out: they neither add nor veto.  Writes
+ * e[grid_n^2], cluster[9] (row-major 3 x 3 around the centre, NaN off the
+ * grid), *cx, *cy, *e_cluster and returns 1 if the event is accepted. */
+int or_readout_event(const int32_t* counts, int32_t grid_n, uint64_t seed, uint64_t event_id,
+                     double ev_per_pair, double noise_keV, double beam_keV, double window_keV,
+                     double veto_factor, double* e, double* cluster, int32_t* cx, int32_t* cy,
+                     double* e_cluster, int32_t* vetoed) {
+  const int32_t n = grid_n;
+  int32_t best = 0;
+  for (int32_t p = 0; p < n * n; ++p) {
+    double g[3] = {0.0, 0.0, 0.0};
+    if (noise_keV > 0.0) or_normals3(seed, event_id, OR_PURPOSE_NOISE, (uint32_t)p, 0u, g);
+    e[p] = (double)counts[p] * ev_per_pair * 1e-3 + noise_keV * g[0];
+    if (e[p] > e[best]) best = p;
+  }
+  const int32_t bx = best % n, by = best / n;
+  double sum = 0.0;
+  for (int32_t dy = -1; dy <= 1; ++dy)
+    for (int32_t dx = -1; dx <= 1; ++dx) {
+      const int32_t x = bx + dx, y = by + dy;
+      const int on = x >= 0 && y >= 0 && x < n && y < n;
+      const double v = on ? e[y * n + x] : NAN;
+      cluster[(dy + 1) * 3 + (dx + 1)] = v;
+      if (on) sum += v;
+    }
+  int32_t veto = 0;
+  for (int32_t dy = -3; dy <= 3; ++dy)
+    for (int32_t dx = -3; dx <= 3; ++dx) {
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+      const int32_t x = bx + dx, y = by + dy;
+      if (x < 0 || y < 0 || x >= n || y >= n) continue;
+      if (e[y * n + x] > veto_factor * noise_keV) veto = 1;
+    }
+  *cx = bx;
+  *cy = by;
+  *e_cluster = sum;
+  *vetoed = veto;
+  return !veto && fabs(sum - beam_keV) <= window_keV;
+}
+
+/* Single-pixel spectrum (Sec. 4.1: single-pixel energies of the accepted
+ * 3 x 3 clusters): each on-grid cluster pixel of an accepted event adds one
+ * count to bin floor((e - lo) / width) of n_bins, values outside ignored. */
+void or_spectrum_add(const double* cluster, int32_t accepted, double lo_keV, double width_keV,
+                     int32_t n_bins, int64_t* hist) {
+  if (!accepted) return;
+  for (int k = 0; k < 9; ++k) {
+    const double v = cluster[k];
+    if (isnan(v)) continue;
+    const double b = floor((v - lo_keV) / width_keV);
+    if (b >= 0.0 && b < (double)n_bins) hist[(int64_t)b] += 1;
+  }
 }
