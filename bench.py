@@ -210,10 +210,21 @@ def aggregate(dist, device, elapsed_ms: float, *counts: float):
 # Our arm
 # ---------------------------------------------------------------------------
 def kernel_source_hash() -> str:
+    """Hash of the source the step kernel is compiled from: the data layout
+    (cts_internal.h up to its launcher declarations), the device helpers and
+    the kernel (cts_kernels.cu up to the next kernel) and the variant table.
+    Other kernels in the same files do not change it."""
+    csrc = os.path.join(ROOT, "paper_2506_09712_gb300", "csrc")
+    with open(os.path.join(csrc, "cts_internal.h")) as fh:
+        hdr = fh.read()
+    with open(os.path.join(csrc, "cts_kernels.cu")) as fh:
+        ker = fh.read()
+    parts = [hdr.split("// ---- kernel launchers")[0],
+             ker.split("// Update alone:")[0],
+             ker[ker.index("const VariantEntry kVariants[]"):ker.index("#undef CTS_V")]]
     h = hashlib.sha256()
-    for f in ("cts_kernels.cu", "cts_internal.h"):
-        with open(os.path.join(ROOT, "paper_2506_09712_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    for part in parts:
+        h.update(part.encode())
     return h.hexdigest()[:16]
 
 
@@ -466,6 +477,25 @@ def run_ours(args, rank, world, local):
             line["serving"] = serving_leg(cts, W, torch, local)
         except Exception as e:  # reported, never fatal for the bench line
             line["serving"] = {"error": repr(e)}
+        # detector readout of the batch's pixel maps, repeated to 1e4 events
+        # with distinct noise streams (one call: copies, kernel, copies back)
+        try:
+            g = int(p["sensor"]["grid_n"])
+            maps = np.stack([r["pixels"].reshape(g, g) for r in res])
+            reps = -(-10_000 // len(maps))
+            maps = np.tile(maps, (reps, 1, 1))[:10_000]
+            ids = np.arange(len(maps), dtype=np.uint64)
+            seeds = np.full(len(maps), W.MASTER_SEED, np.uint64)
+            beam = float(p["energies"][0][0])
+            cts.sim_readout(maps[:64], seeds[:64], ids[:64], beam, 300, device=local)
+            t0 = time.perf_counter()
+            ro = cts.sim_readout(maps, seeds, ids, beam, 300, device=local)
+            dt = time.perf_counter() - t0
+            line["readout"] = {"events": len(maps), "events_per_s": len(maps) / dt,
+                               "accepted_frac": float(ro["accepted"].mean()),
+                               "api": "sim_readout (host maps in, clusters and spectrum out)"}
+        except Exception as e:  # reported, never fatal for the bench line
+            line["readout"] = {"error": repr(e)}
         try:
             big = large_n_leg(cts, W, torch, local, stream)
             big["frac"] = big["step_kernel_tflops"] / peak_tflops

@@ -305,6 +305,48 @@ int cts_field_noalloc(const float* dev_x, const float* dev_y, const float* dev_z
  * time from CUDA events.  The autotuner's measurement. */
 int sim_debug_time_step(sim_t* sim, int32_t variant, int32_t reps, double* ms_per_launch);
 
+/* Detector readout of simulated events (Sec. 4.1 describes the selection of
+ * the measured clusters; Sec. 4.2 applies it, with Fano statistics and about
+ * 0.13 keV of noise, to simulated events).  Parameters: */
+typedef struct sim_readout_params_t {
+  int32_t grid_n;        /* pixels per side of each count map (1 .. 32) */
+  int32_t n_bins;        /* bins of the single-pixel spectrum (0 = none) */
+  double ev_per_pair;    /* eV per carrier pair (3.62) */
+  double noise_keV;      /* Gaussian noise per pixel, standard deviation (0.13); 0 = none */
+  double beam_keV;       /* photon energy: centre of the cluster-energy window */
+  double window_keV;     /* half width of the window (1.0) */
+  double veto_factor;    /* pile-up threshold in units of noise_keV (3.0) */
+  double spec_lo_keV;    /* lower edge of the spectrum's first bin */
+  double spec_bin_keV;   /* spectrum bin width (0.1) */
+} sim_readout_params_t;
+
+/* One event's cluster.  Pixel energy = count * ev_per_pair + noise * g, g the
+ * first Box-Muller normal of the event's stream at (carrier = pixel index
+ * iy * grid_n + ix, step 0, purpose 3).  The centre (cx, cy) is the pixel of
+ * largest energy (first in row-major order on ties); e[9] holds the 3 x 3
+ * pixels around it, row-major, NaN off the grid; e_cluster is their sum.
+ * vetoed = some pixel of the 7 x 7 window outside the 3 x 3, on the grid,
+ * exceeds veto_factor * noise_keV (pile-up cut); accepted = not vetoed and
+ * |e_cluster - beam_keV| <= window_keV.  Off-grid pixels are not read out. */
+typedef struct sim_cluster_t {
+  int32_t accepted, vetoed, cx, cy;
+  double e_cluster;
+  double e[9];
+} sim_cluster_t;
+
+/* Readout of n_events pixel-count maps (host memory, n_events x grid_n x
+ * grid_n int32, row-major per event, e.g. sim_result_t.pixels) with per-event
+ * seeds and ids on GPU `device`: writes clusters[n_events], optionally the
+ * noisy pixel energies pixel_keV[n_events x grid_n^2] (NULL to skip), and
+ * adds to spectrum[n_bins] (NULL if n_bins = 0) one count per on-grid pixel
+ * of every accepted cluster, in bin floor((e - spec_lo_keV) / spec_bin_keV).
+ * All buffers are the caller's host memory; the call allocates device memory
+ * for the copies and synchronises.  Returns SIM_OK, SIM_EINVAL, SIM_ENODEV
+ * or SIM_ECUDA. */
+int sim_readout(const sim_readout_params_t* prm, const int32_t* counts, const uint64_t* seeds,
+                const uint64_t* event_ids, int32_t n_events, int32_t device, double* pixel_keV,
+                sim_cluster_t* clusters, int64_t* spectrum);
+
 /* FP32 FMA throughput of device `device` (CUDA ordinal) measured by chains of
  * independent fused multiply-adds, packed f32x2 (packed = 1) or scalar: the
  * attainable counterpart of the nominal FP32 peak that the pair kernel's

@@ -58,6 +58,17 @@ double cts_estimate_steps(double thickness_um, double bias_V, double depletion_V
                           double mu0_cm2, double vsat_cms, double beta, double dt_ps,
                           double depth_um);
 
+/* Carrier-pair count of one photon with Fano statistics (Sec. 4.2 applies a
+ * Fano factor of 0.13 to the number of carriers): mean E / 3.62 eV, variance
+ * fano times the mean, drawn as round(mean + sqrt(fano * mean) * g) with g the
+ * first Box-Muller normal of the event's counter-based stream (Philox4x32-10,
+ * key = seed, counter = (0, 0, event low word, event high word ^ 2 << 28)),
+ * at least 1.  fano = 0 gives round(E / 3.62 eV).  The result goes into
+ * sim_event_t.n_pairs.  Returns 0, or -1 for a null pointer, energy <= 0 or
+ * fano < 0. */
+int cts_fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano,
+                   int32_t* n_pairs);
+
 #ifdef __cplusplus
 }
 #endif

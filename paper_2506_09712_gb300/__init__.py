@@ -54,6 +54,18 @@ class sim_options_t(C.Structure):
                 ("stream", C.c_void_p)]
 
 
+class sim_readout_params_t(C.Structure):
+    _fields_ = [("grid_n", C.c_int32), ("n_bins", C.c_int32), ("ev_per_pair", C.c_double),
+                ("noise_keV", C.c_double), ("beam_keV", C.c_double), ("window_keV", C.c_double),
+                ("veto_factor", C.c_double), ("spec_lo_keV", C.c_double),
+                ("spec_bin_keV", C.c_double)]
+
+
+class sim_cluster_t(C.Structure):
+    _fields_ = [("accepted", C.c_int32), ("vetoed", C.c_int32), ("cx", C.c_int32),
+                ("cy", C.c_int32), ("e_cluster", C.c_double), ("e", C.c_double * 9)]
+
+
 class sim_event_t(C.Structure):
     _fields_ = [("event_id", C.c_uint64), ("seed", C.c_uint64), ("kind", C.c_int32),
                 ("n_pairs", C.c_int32), ("energy_keV", C.c_double), ("depth_um", C.c_double),
@@ -92,7 +104,7 @@ EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_e
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
             "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_debug_launch_log",
-            "sim_debug_fma_peak",
+            "sim_debug_fma_peak", "sim_readout", "cts_fano_pairs",
             "sim_set_variants",
             "sim_get_variants", "sim_autotune", "sim_reset", "cts_field_noalloc", "cts_plan_units", "cts_arena_replay",
             "cts_estimate_steps"]
@@ -143,6 +155,9 @@ def load(build_if_missing: bool = True):
         "sim_debug_time_step": [C.c_void_p, i32, i32, P(d)],
         "sim_debug_launch_log": [C.c_void_p, P(d), i32, P(i32)],
         "sim_debug_fma_peak": [i32, i32, P(d)],
+        "sim_readout": [P(sim_readout_params_t), P(i32), P(u64), P(u64), i32, i32, P(d),
+                        P(sim_cluster_t), P(i64)],
+        "cts_fano_pairs": [u64, u64, d, d, P(i32)],
         "sim_set_variants": [C.c_void_p, P(i64), P(i32), i32],
         "sim_reset": [C.c_void_p],
         "sim_get_variants": [C.c_void_p, P(i64), P(i32), i32, P(i32)],
@@ -285,6 +300,51 @@ def sim_debug_trajectory(h, event: sim_event_t, n_steps, n_carriers):
 
 def sim_debug_inject(h, fault):
     return load().sim_debug_inject(h, int(fault))
+
+
+def cts_fano_pairs(seed, event_id, energy_keV, fano=0.13):
+    """Carrier pairs of one photon with Fano statistics (goes into n_pairs)."""
+    n = C.c_int32(0)
+    rc = load().cts_fano_pairs(int(seed), int(event_id), float(energy_keV), float(fano),
+                               C.byref(n))
+    if rc != 0:
+        raise ValueError("cts_fano_pairs: bad arguments")
+    return n.value
+
+
+READOUT_DEFAULTS = dict(ev_per_pair=3.62, noise_keV=0.13, window_keV=1.0, veto_factor=3.0,
+                        spec_lo_keV=0.0, spec_bin_keV=0.1)
+
+
+def sim_readout(counts, seeds, event_ids, beam_keV, n_bins=0, device=0, want_pixels=False,
+                **kw):
+    """Detector readout of pixel-count maps (n_ev x g x g) on the GPU: noisy
+    pixel energies, the 3 x 3 cluster around the largest pixel, the pile-up
+    veto, the energy window and the single-pixel spectrum.  Returns a dict
+    like the oracle's readout: e (if want_pixels), cluster, cx, cy,
+    e_cluster, accepted, vetoed, spectrum."""
+    prm_d = dict(READOUT_DEFAULTS, **kw)
+    counts = np.ascontiguousarray(counts, dtype=np.int32)
+    n_ev, g = counts.shape[0], counts.shape[1]
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    ids = np.ascontiguousarray(event_ids, dtype=np.uint64)
+    prm = sim_readout_params_t(grid_n=g, n_bins=int(n_bins), beam_keV=float(beam_keV),
+                               **{k: float(v) for k, v in prm_d.items()})
+    cl = (sim_cluster_t * max(n_ev, 1))()
+    spec = np.zeros(max(int(n_bins), 1), np.int64)
+    pix = np.zeros((n_ev, g, g)) if want_pixels else None
+    _check(load().sim_readout(C.byref(prm), _ptr(counts, C.c_int32), _ptr(seeds, C.c_uint64),
+                              _ptr(ids, C.c_uint64), n_ev, int(device),
+                              _ptr(pix, C.c_double) if want_pixels else None, cl,
+                              _ptr(spec, C.c_int64) if n_bins > 0 else None), "sim_readout")
+    raw = np.frombuffer(cl, dtype=np.uint8, count=96 * n_ev).reshape(n_ev, 96)
+    ints = raw[:, :16].copy().view(np.int32).reshape(n_ev, 4)
+    dbl = raw[:, 16:].copy().view(np.float64).reshape(n_ev, 10)
+    out = dict(cluster=dbl[:, 1:], e_cluster=dbl[:, 0], accepted=ints[:, 0], vetoed=ints[:, 1],
+               cx=ints[:, 2], cy=ints[:, 3], spectrum=spec[:int(n_bins)])
+    if want_pixels:
+        out["e"] = pix
+    return out
 
 
 def sim_debug_fma_peak(device=0, packed=True):

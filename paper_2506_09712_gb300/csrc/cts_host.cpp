@@ -267,6 +267,48 @@ double estimate_steps(double H, double Vb, double Vd, double mu0_cm2, double vsa
   return t / (dt_ps * 1e-3);
 }
 
+// ---------------------------------------------------------------------------
+// Fano-distributed carrier count (Sec. 4.2): mean E / 3.62 eV, variance F
+// times the mean, drawn as round(mean + sqrt(F mean) g) from the event's
+// counter-based stream.  Philox4x32-10 (Salmon et al., SC'11) and the
+// Box-Muller cosine branch, written for the host.
+// ---------------------------------------------------------------------------
+namespace {
+struct Philox {
+  uint32_t c[4];
+  uint32_t k[2];
+  void rounds() {
+    for (int r = 0; r < 10; ++r) {
+      const uint64_t a = (uint64_t)0xD2511F53u * c[0];
+      const uint64_t b = (uint64_t)0xCD9E8D57u * c[2];
+      const uint32_t x0 = (uint32_t)(b >> 32) ^ c[1] ^ k[0];
+      const uint32_t x2 = (uint32_t)(a >> 32) ^ c[3] ^ k[1];
+      c[1] = (uint32_t)b;
+      c[3] = (uint32_t)a;
+      c[0] = x0;
+      c[2] = x2;
+      k[0] += 0x9E3779B9u;
+      k[1] += 0xBB67AE85u;
+    }
+  }
+};
+constexpr uint32_t kPurposeFano = 2;
+constexpr double kEvPerPair = 3.62;
+}  // namespace
+
+int fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano) {
+  const double mean = energy_keV * 1000.0 / kEvPerPair;
+  if (!(fano > 0.0)) return (int)std::llround(mean);
+  Philox g{{0u, 0u, (uint32_t)event_id, (uint32_t)(event_id >> 32) ^ (kPurposeFano << 28)},
+           {(uint32_t)seed, (uint32_t)(seed >> 32)}};
+  g.rounds();
+  const double u0 = ((double)(g.c[0] >> 9) + 0.5) / 8388608.0;
+  const double u1 = ((double)(g.c[1] >> 9) + 0.5) / 8388608.0;
+  const double z = std::sqrt(-2.0 * std::log(u0)) * std::cos(2.0 * 3.14159265358979323846 * u1);
+  const double n = std::floor(mean + std::sqrt(fano * mean) * z + 0.5);
+  return n < 1.0 ? 1 : (int)n;
+}
+
 }  // namespace cts
 
 extern "C" {
@@ -305,6 +347,13 @@ int cts_arena_replay(int64_t capacity, const int64_t* ops, int32_t n_ops, int64_
       result[k] = 0;
     }
   }
+  return 0;
+}
+
+int cts_fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano,
+                   int32_t* n_pairs) {
+  if (!n_pairs || !(energy_keV > 0.0) || !(fano >= 0.0)) return -1;
+  *n_pairs = cts::fano_pairs(seed, event_id, energy_keV, fano);
   return 0;
 }
 

@@ -27,6 +27,9 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
                std::vector<int32_t>* cta_begin, int64_t* partial_floats, bool dynamic,
                bool slot_major = false);
 
+// Fano-distributed carrier-pair count of one photon (see cts_fano_pairs).
+int fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano);
+
 class ArenaAllocator {
  public:
   explicit ArenaAllocator(int64_t capacity = 0);

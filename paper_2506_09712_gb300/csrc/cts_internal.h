@@ -182,6 +182,27 @@ cudaError_t launch_bin(const Phys& ph, Arena A, const SlotDev* slots, const int3
                        int n, int32_t* pixels, SlotReadout* readout, cudaStream_t s);
 cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, int64_t n,
                               int32_t* pixels, long long* outside, cudaStream_t s);
+// Readout of pixel-count maps: one CTA per event (grid_n <= 32).  ClusterRec
+// has the layout of the public sim_cluster_t.
+struct ClusterRec {
+  int32_t accepted, vetoed, cx, cy;
+  double e_cluster;
+  double e[9];
+};
+static_assert(sizeof(ClusterRec) == 96, "cluster record layout");
+constexpr int kReadoutMaxGrid = 32;
+struct ReadoutArgs {
+  const int32_t* counts;
+  const unsigned long long* seeds;
+  const unsigned long long* ids;
+  double* pixel_keV;    // optional
+  ClusterRec* clusters;
+  unsigned long long* spectrum;
+  int32_t grid_n, n_bins;
+  double ev_per_pair, noise_keV, beam_keV, window_keV, veto_factor, spec_lo_keV, spec_bin_keV;
+};
+cudaError_t launch_readout(const ReadoutArgs& r, int n_events, cudaStream_t s);
+
 // 16 FMA lane-ops per thread and iteration; 256 threads per CTA.
 cudaError_t launch_fma_chain(bool packed, float* out, int grid, int iters, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,

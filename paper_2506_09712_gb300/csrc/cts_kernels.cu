@@ -1092,6 +1092,88 @@ __global__ void bin_points_kernel(Phys ph, const double* x, const double* y, int
 // ---------------------------------------------------------------------------
 // Test hooks.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Detector readout of pixel-count maps (Sec. 4.1 selection, Sec. 4.2 noise):
+// one CTA per event.  Pixel energies with Gaussian noise from the event's
+// stream (purpose 3, carrier = pixel), the centre at the largest pixel (first
+// in row-major order on ties), the 3 x 3 cluster, the 7 x 7 pile-up veto and
+// the cluster-energy window; accepted clusters add their on-grid pixels to
+// the single-pixel spectrum.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) readout_kernel(ReadoutArgs r) {
+  __shared__ double e[kReadoutMaxGrid * kReadoutMaxGrid];
+  __shared__ double wv[8];
+  __shared__ int wi[8];
+  const int ev = blockIdx.x, n = r.grid_n, np = n * n;
+  const int32_t* cnt = r.counts + (int64_t)ev * np;
+  const uint64_t seed = r.seeds[ev], id = r.ids[ev];
+  double best = -INFINITY;
+  int bi = np;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    double g = 0.0;
+    if (r.noise_keV > 0.0) g = normals_d(stream_words(seed, id, 3u, (uint32_t)p, 0u)).x;
+    const double v = (double)cnt[p] * r.ev_per_pair * 1e-3 + r.noise_keV * g;
+    e[p] = v;
+    if (r.pixel_keV) r.pixel_keV[(int64_t)ev * np + p] = v;
+    if (v > best || (v == best && p < bi)) {
+      best = v;
+      bi = p;
+    }
+  }
+  // (largest energy, smallest index) over the block
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_down_sync(0xffffffffu, best, o);
+    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    wv[warp] = best;
+    wi[warp] = bi;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+    if (wv[w] > best || (wv[w] == best && wi[w] < bi)) {
+      best = wv[w];
+      bi = wi[w];
+    }
+  const int bx = bi % n, by = bi / n;
+  ClusterRec c;
+  c.e_cluster = 0.0;
+  for (int dy = -1; dy <= 1; ++dy)
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int x = bx + dx, y = by + dy;
+      const bool on = x >= 0 && y >= 0 && x < n && y < n;
+      const double v = on ? e[y * n + x] : __longlong_as_double(0x7ff8000000000000ll);
+      c.e[(dy + 1) * 3 + (dx + 1)] = v;
+      if (on) c.e_cluster += v;
+    }
+  int veto = 0;
+  for (int dy = -3; dy <= 3; ++dy)
+    for (int dx = -3; dx <= 3; ++dx) {
+      if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+      const int x = bx + dx, y = by + dy;
+      if (x < 0 || y < 0 || x >= n || y >= n) continue;
+      if (e[y * n + x] > r.veto_factor * r.noise_keV) veto = 1;
+    }
+  c.cx = bx;
+  c.cy = by;
+  c.vetoed = veto;
+  c.accepted = !veto && fabs(c.e_cluster - r.beam_keV) <= r.window_keV;
+  r.clusters[ev] = c;
+  if (c.accepted && r.spectrum)
+    for (int k = 0; k < 9; ++k) {
+      const double v = c.e[k];
+      if (isnan(v)) continue;
+      const double b = floor((v - r.spec_lo_keV) / r.spec_bin_keV);
+      if (b >= 0.0 && b < (double)r.n_bins) atomicAdd(r.spectrum + (int64_t)b, 1ull);
+    }
+}
+
 // FP32 FMA throughput probe: independent FMA chains per thread (packed f32x2
 // or scalar), the denominator the pair kernel's FP32 work is compared with.
 template <bool PACKED>
@@ -1248,6 +1330,11 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
   int grid = (int)((n + threads - 1) / threads);
   grid = grid < 1 ? 1 : (grid > 4096 ? 4096 : grid);
   bin_points_kernel<<<grid, threads, 0, s>>>(ph, x, y, n, pixels, outside);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_readout(const ReadoutArgs& r, int n_events, cudaStream_t s) {
+  if (n_events > 0) readout_kernel<<<n_events, 256, 0, s>>>(r);
   return cudaGetLastError();
 }
 

@@ -1652,6 +1652,84 @@ int sim_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32
   return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
 }
 
+int sim_readout(const sim_readout_params_t* prm, const int32_t* counts, const uint64_t* seeds,
+                const uint64_t* event_ids, int32_t n_events, int32_t device, double* pixel_keV,
+                sim_cluster_t* clusters, int64_t* spectrum) {
+  static_assert(sizeof(sim_cluster_t) == sizeof(ClusterRec), "cluster record layout");
+  if (!prm || n_events < 0 || device < 0) return SIM_EINVAL;
+  const int g = prm->grid_n;
+  if (g < 1 || g > kReadoutMaxGrid || prm->n_bins < 0) return SIM_EINVAL;
+  if (prm->n_bins > 0 && (!spectrum || !(prm->spec_bin_keV > 0.0))) return SIM_EINVAL;
+  if (!(prm->noise_keV >= 0.0) || !(prm->window_keV >= 0.0) || !(prm->ev_per_pair > 0.0))
+    return SIM_EINVAL;
+  if (n_events > 0 && (!counts || !seeds || !event_ids || !clusters)) return SIM_EINVAL;
+  int sms = 0;
+  if (check_device(device, &sms)) return SIM_ENODEV;
+  cudaSetDevice(device);
+  if (n_events == 0) return SIM_OK;
+  const size_t np = (size_t)g * g, ne = (size_t)n_events;
+  ReadoutArgs r{};
+  r.grid_n = g;
+  r.n_bins = prm->n_bins;
+  r.ev_per_pair = prm->ev_per_pair;
+  r.noise_keV = prm->noise_keV;
+  r.beam_keV = prm->beam_keV;
+  r.window_keV = prm->window_keV;
+  r.veto_factor = prm->veto_factor;
+  r.spec_lo_keV = prm->spec_lo_keV;
+  r.spec_bin_keV = prm->spec_bin_keV;
+  int32_t* dc = nullptr;
+  unsigned long long *ds = nullptr, *di = nullptr, *dh = nullptr;
+  double* de = nullptr;
+  ClusterRec* dcl = nullptr;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaSuccess;
+  std::vector<unsigned long long> hist((size_t)std::max(prm->n_bins, 1), 0ull);
+  do {
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking))) break;
+    if ((e = cudaMalloc(&dc, ne * np * sizeof(int32_t)))) break;
+    if ((e = cudaMalloc(&ds, ne * sizeof(unsigned long long)))) break;
+    if ((e = cudaMalloc(&di, ne * sizeof(unsigned long long)))) break;
+    if ((e = cudaMalloc(&dcl, ne * sizeof(ClusterRec)))) break;
+    if (pixel_keV && (e = cudaMalloc(&de, ne * np * sizeof(double)))) break;
+    if (prm->n_bins > 0) {
+      if ((e = cudaMalloc(&dh, (size_t)prm->n_bins * sizeof(unsigned long long)))) break;
+      if ((e = cudaMemsetAsync(dh, 0, (size_t)prm->n_bins * sizeof(unsigned long long), st)))
+        break;
+    }
+    if ((e = cudaMemcpyAsync(dc, counts, ne * np * sizeof(int32_t), cudaMemcpyHostToDevice, st)))
+      break;
+    if ((e = cudaMemcpyAsync(ds, seeds, ne * sizeof(uint64_t), cudaMemcpyHostToDevice, st))) break;
+    if ((e = cudaMemcpyAsync(di, event_ids, ne * sizeof(uint64_t), cudaMemcpyHostToDevice, st)))
+      break;
+    r.counts = dc;
+    r.seeds = ds;
+    r.ids = di;
+    r.pixel_keV = de;
+    r.clusters = dcl;
+    r.spectrum = dh;
+    if ((e = launch_readout(r, n_events, st))) break;
+    if ((e = cudaMemcpyAsync(clusters, dcl, ne * sizeof(ClusterRec), cudaMemcpyDeviceToHost, st)))
+      break;
+    if (de && (e = cudaMemcpyAsync(pixel_keV, de, ne * np * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st)))
+      break;
+    if (dh && (e = cudaMemcpyAsync(hist.data(), dh, (size_t)prm->n_bins * sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, st)))
+      break;
+    if ((e = cudaStreamSynchronize(st))) break;
+    for (int b = 0; b < prm->n_bins; ++b) spectrum[b] += (int64_t)hist[b];
+  } while (0);
+  cudaFree(dc);
+  cudaFree(ds);
+  cudaFree(di);
+  cudaFree(dcl);
+  if (de) cudaFree(de);
+  if (dh) cudaFree(dh);
+  if (st) cudaStreamDestroy(st);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
 int sim_debug_fma_peak(int32_t device, int32_t packed, double* flops_per_s) {
   if (!flops_per_s || device < 0) return SIM_EINVAL;
   int sms = 0;

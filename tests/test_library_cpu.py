@@ -246,3 +246,25 @@ def test_slot_major_plan_for_multi_step_launches(lib, n_h, n_e):
     if len(n_h) == 1:
         rc2, units2, _, _ = cts.cts_plan_units(n_h, n_e, 512, 608, allow_split=2)
         assert np.array_equal(units, units2)
+
+
+def test_fano_pairs_match_the_oracle():
+    # the library's host draw and the oracle's are separate implementations of
+    # the same counter-based stream and normal approximation
+    import oracle
+    for e in (3.0, 8.0, 17.5, 25.0):
+        for k in range(0, 3000, 7):
+            assert cts.cts_fano_pairs(20250611, k, e, 0.13) == oracle.fano_pairs(20250611, k, e, 0.13)
+        assert cts.cts_fano_pairs(1, 2, e, 0.0) == oracle.n_pairs(e)
+    with pytest.raises(ValueError):
+        cts.cts_fano_pairs(1, 2, -1.0, 0.13)
+
+
+def test_readout_rejects_bad_arguments_before_the_device(lib):
+    import numpy as np
+    with pytest.raises(cts.SimError) as e:
+        cts.sim_readout(np.zeros((1, 33, 33), np.int32), [1], [0], 20.0)
+    assert e.value.code == cts.SIM_EINVAL
+    with pytest.raises(cts.SimError) as e:
+        cts.sim_readout(np.zeros((1, 9, 9), np.int32), [1], [0], 20.0, n_bins=10, spec_bin_keV=0.0)
+    assert e.value.code == cts.SIM_EINVAL
