@@ -52,6 +52,7 @@ class _Params(C.Structure):
         ("mob_model", C.c_int32),
         ("mu0_h", C.c_double), ("vsat_h", C.c_double), ("beta_h", C.c_double),
         ("mu0_e", C.c_double), ("vsat_e", C.c_double), ("beta_e", C.c_double),
+        ("spherical", C.c_int32),
     ]
 
 
@@ -108,6 +109,7 @@ def lib():
         _lib.or_run_events.argtypes = [P(_Params), P(_Event), i64, P(_Result)]
         _lib.or_max_threads.restype = C.c_int
         _lib.or_fano_pairs.argtypes = [u64, u64, d, d]; _lib.or_fano_pairs.restype = i32
+        _lib.or_field_spherical.argtypes = [i64, P(i64), P(d), P(d), P(d), d, P(d), P(d), P(d)]
         _lib.or_readout_event.argtypes = [P(i32), i32, u64, u64, d, d, d, d, d, P(d), P(d),
                                           P(i32), P(i32), P(d), P(i32)]
         _lib.or_readout_event.restype = C.c_int
@@ -148,6 +150,7 @@ def make_params(sensor: dict, field: dict | None = None, mobility: dict | None =
     p.mu0_e = mobility.get("mu0_e", 0.0)
     p.vsat_e = mobility.get("vsat_e", 1.0)
     p.beta_e = mobility.get("beta_e", 1.0)
+    p.spherical = field.get("spherical", 0)
     return p
 
 
@@ -204,6 +207,20 @@ def thermal_voltage(T):
 
 def n_pairs(energy_keV):
     return lib().or_n_pairs(energy_keV)
+
+
+def field_spherical(xyz, kc=None):
+    """FP64 repulsion field of the simplified spherical model (Eq. 7) on the
+    holes at xyz (n x 3): k_C Q(<r) (r_i - c) / r^3, c the mean position."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    x, y, z = (np.ascontiguousarray(xyz[:, k]) for k in range(3))
+    rows = np.arange(n, dtype=np.int64)
+    ex, ey, ez = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().or_field_spherical(n, _ptr(rows, C.c_int64), _ptr(x, C.c_double), _ptr(y, C.c_double),
+                             _ptr(z, C.c_double), coulomb_k() if kc is None else kc,
+                             _ptr(ex, C.c_double), _ptr(ey, C.c_double), _ptr(ez, C.c_double))
+    return np.stack([ex, ey, ez], axis=1)
 
 
 def fano_pairs(seed, event_id, energy_keV, fano=0.13):

@@ -68,6 +68,7 @@ typedef struct {
   int32_t mob_model;     /* OR_MOB_CT or OR_MOB_CONST */
   double mu0_h, vsat_h, beta_h; /* holes: cm^2/Vs, cm/s, - */
   double mu0_e, vsat_e, beta_e; /* electrons */
+  int32_t spherical;     /* 1: repulsion by the simplified spherical model (Eq. 7) */
 } or_params_t;
 
 typedef struct {
@@ -265,6 +266,48 @@ void or_bin(const or_params_t* P, int64_t n, const double* x, const double* y,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Simplified spherical model (Sec. 2.2, Eq. 7): the repulsion field of a    */
+/* hole at distance r from the cloud centre is k_C Q(<r) / r^3 times its     */
+/* offset from the centre, Q(<r) the number of holes strictly closer.  The    */
+/* centre is the mean position of the active holes.  Written as the plain     */
+/* double loop over pairs (no sorting), holes only.                          */
+/* ------------------------------------------------------------------------ */
+void or_field_spherical(int64_t n_act, const int64_t* rows, const double* x, const double* y,
+                        const double* z, double kc, double* ex, double* ey, double* ez) {
+  double cx = 0.0, cy = 0.0, cz = 0.0;
+  for (int64_t r = 0; r < n_act; ++r) {
+    cx += x[rows[r]];
+    cy += y[rows[r]];
+    cz += z[rows[r]];
+  }
+  if (n_act > 0) {
+    cx /= (double)n_act;
+    cy /= (double)n_act;
+    cz /= (double)n_act;
+  }
+  double* d2 = (double*)calloc((size_t)(n_act > 0 ? n_act : 1), sizeof(double));
+  for (int64_t r = 0; r < n_act; ++r) {
+    const int64_t c = rows[r];
+    const double dx = x[c] - cx, dy = y[c] - cy, dz = z[c] - cz;
+    d2[r] = dx * dx + dy * dy + dz * dz;
+  }
+  for (int64_t r = 0; r < n_act; ++r) {
+    int64_t q = 0;
+    for (int64_t s = 0; s < n_act; ++s)
+      if (d2[s] < d2[r]) ++q;
+    const int64_t c = rows[r];
+    ex[r] = ey[r] = ez[r] = 0.0;
+    if (q == 0) continue;
+    const double rr = sqrt(d2[r]);
+    const double f = kc * (double)q / (d2[r] * rr);
+    ex[r] = f * (x[c] - cx);
+    ey[r] = f * (y[c] - cy);
+    ez[r] = f * (z[c] - cz);
+  }
+  free(d2);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Event initialisation (Algorithm 1, first step; Sec. 2.1 and Eq. 2).       */
 /* ------------------------------------------------------------------------ */
 int64_t or_event_carriers(const or_params_t* P, const or_event_t* ev) {
@@ -402,10 +445,13 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
     }
     if (holes_active == 0) break;
     if (step >= P->max_steps) { R->status = OR_EMAXSTEPS; break; }
-    R->interactions += n_act * (n_act - 1);
+    /* pair terms of Eq. 4, or (spherical model) field evaluations */
+    R->interactions += P->spherical ? n_act : n_act * (n_act - 1);
 
     /* Field of every active carrier from the positions at the step start. */
-    if (P->repulsion) {
+    if (P->repulsion && P->spherical) {
+      or_field_spherical(n_act, rows, x, y, z, kc, ex, ey, ez);
+    } else if (P->repulsion) {
       or_field_rows(n, x, y, z, sign, state, rows, n_act, kc, P->softening_um,
                     parallel, ex, ey, ez);
     } else {

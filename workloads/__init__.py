@@ -81,8 +81,11 @@ def preset(name: str) -> dict:
     return copy.deepcopy(PRESETS[name])
 
 
-def field_switches(repulsion=1, drift=1, diffusion=1) -> dict:
-    return dict(repulsion=int(repulsion), drift=int(drift), diffusion=int(diffusion))
+def field_switches(repulsion=1, drift=1, diffusion=1, spherical=0) -> dict:
+    """Transport-term switches; spherical = 1 selects the simplified spherical
+    repulsion model instead of the pairwise field."""
+    return dict(repulsion=int(repulsion), drift=int(drift), diffusion=int(diffusion),
+                spherical=int(spherical))
 
 
 def sample_depths(rng: np.random.Generator, energy_keV, thickness_um: float) -> np.ndarray:
