@@ -298,6 +298,30 @@ def large_n_leg(cts, W, torch, device, stream, steps: int = 24):
     return out
 
 
+def spherical_leg(cts, W, torch, device, stream, events, p):
+    """The same batch under the simplified spherical model (Sec. 2.2, Eq. 7):
+    whole-simulation events/s, the paper's fast comparison method."""
+    with cts.Simulator(p["sensor"], p["mobility"], W.field_switches(spherical=1),
+                       mode=cts.CTS_MODE_BATCHED, device=device, max_slots=len(events),
+                       stream=stream.cuda_stream) as sim:
+        ms = []
+        for _ in range(3):
+            sim.stage(events)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.execute()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res = sim.collect(len(events))
+            ms.append(e0.elapsed_time(e1))
+    t = min(ms[1:])
+    return {"field": "spherical (Eq. 7)", "events": len(events), "ms_per_batch": t,
+            "events_per_s": len(events) / (t * 1e-3),
+            "statuses_ok": all(r["status"] == 0 for r in res)}
+
+
 def _offered(sim, W, name, rate, n):
     """Open-loop Poisson arrivals at `rate`; latency = completion - submission."""
     arr = W.poisson_arrivals(rate, n, seed=7)
@@ -496,6 +520,11 @@ def run_ours(args, rank, world, local):
                                "api": "sim_readout (host maps in, clusters and spectrum out)"}
         except Exception as e:  # reported, never fatal for the bench line
             line["readout"] = {"error": repr(e)}
+        try:
+            line["spherical"] = spherical_leg(cts, W, torch, local, stream, events, p)
+            line["spherical"]["comprehensive_events_per_s"] = events_per_s
+        except Exception as e:  # reported, never fatal for the bench line
+            line["spherical"] = {"error": repr(e)}
         try:
             big = large_n_leg(cts, W, torch, local, stream)
             big["frac"] = big["step_kernel_tflops"] / peak_tflops

@@ -81,12 +81,19 @@ typedef struct sim_sensor_t {
   int32_t species;
 } sim_sensor_t;
 
-/* Switches of the three transport terms (1 = on); all on reproduces Eqs. 3, 5. */
+/* Switches of the three transport terms (1 = on); all on reproduces Eqs. 3, 5.
+ * spherical = 1 replaces the pairwise repulsion field (Eq. 4) by the
+ * simplified spherical model of Sec. 2.2 (Eq. 7): field k_C Q(<r) (r - c) / r^3
+ * about the mean position c of the event's active holes, Q(<r) the number of
+ * holes strictly closer to c.  It needs species CTS_HOLES and events of at
+ * most 16384 carriers (SIM_EINVAL otherwise); the result's interactions then
+ * count one field evaluation per active hole and step.  The debug field and
+ * timing hooks always use the pairwise field. */
 typedef struct sim_field_t {
   int32_t repulsion;
   int32_t drift;
   int32_t diffusion;
-  int32_t reserved;
+  int32_t spherical;
 } sim_field_t;
 
 /* Field-dependent mobility (Sec. 2.1, Jacoboni-Canali form), per species. */

@@ -35,7 +35,7 @@ class sim_sensor_t(C.Structure):
 
 class sim_field_t(C.Structure):
     _fields_ = [("repulsion", C.c_int32), ("drift", C.c_int32), ("diffusion", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("spherical", C.c_int32)]
 
 
 class sim_mobility_t(C.Structure):
@@ -459,7 +459,8 @@ def make_sensor(d: dict) -> sim_sensor_t:
 
 def make_field(d: dict | None = None) -> sim_field_t:
     d = d or {}
-    return sim_field_t(d.get("repulsion", 1), d.get("drift", 1), d.get("diffusion", 1), 0)
+    return sim_field_t(d.get("repulsion", 1), d.get("drift", 1), d.get("diffusion", 1),
+                       d.get("spherical", 0))
 
 
 def make_mobility(d: dict) -> sim_mobility_t:

@@ -182,6 +182,11 @@ cudaError_t launch_bin(const Phys& ph, Arena A, const SlotDev* slots, const int3
                        int n, int32_t* pixels, SlotReadout* readout, cudaStream_t s);
 cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, int64_t n,
                               int32_t* pixels, long long* outside, cudaStream_t s);
+// Simplified spherical model: one CTA per slot for steps k0 .. k0 + nk - 1;
+// events of at most kSphMax holes (sorted in shared memory).
+constexpr int kSphMax = 16384;
+cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s);
+
 // Readout of pixel-count maps: one CTA per event (grid_n <= 32).  ClusterRec
 // has the layout of the public sim_cluster_t.
 struct ClusterRec {

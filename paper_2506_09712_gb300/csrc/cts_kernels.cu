@@ -1093,6 +1093,141 @@ __global__ void bin_points_kernel(Phys ph, const double* x, const double* y, int
 // Test hooks.
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
+// Simplified spherical model (Sec. 2.2, Eq. 7), holes only: one CTA per
+// event runs the chunk's steps by itself (an event's step needs only its own
+// carriers).  Per step: the FP64 centre of the active holes (a fixed-order
+// block reduction), the squared distances as order-preserving 64-bit keys,
+// a bitonic sort in shared memory, the enclosed count Q(<r) = the first
+// position of a key's run in the sorted order, the field k_C Q (r - c) / r^3
+// and the fused update.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
+  // warp trees, then thread 0 adds the warp totals in warp order
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    red[32] = t;
+  }
+  __syncthreads();
+  t = red[32];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, int nk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSphMax]
+  int32_t* idx = reinterpret_cast<int32_t*>(key + kSphMax);                    // [kSphMax]
+  __shared__ double red[33];
+  __shared__ double s_azn;
+  const int slot = blockIdx.x;
+  if (slot >= a.S) return;
+  SlotDev* S = a.slots + slot;
+  if (!S->running) return;
+  const int nh = S->n_h;
+  if (nh <= 0 || nh > kSphMax) {
+    if (nh > kSphMax && threadIdx.x == 0) atomicOr(a.err, kErrPlan);
+    return;
+  }
+  int p2 = 2;
+  while (p2 < nh) p2 <<= 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const Phys& ph = a.ph;
+  for (int kq = 0; kq < nk; ++kq) {
+    const int k = k0 + kq;
+    const int step = S->step0 + k;
+    const int p = step & 1;
+    // centre of the active holes
+    double sx = 0.0, sy = 0.0, sz = 0.0, cnt = 0.0;
+    for (int t = tid; t < nh; t += nt) {
+      const int64_t ai = S->base + t;
+      const int8_t st = __ldcg(a.A.cstate + S->base + a.A.cid[ai]);
+      if ((st & kStateMask) != kStateActive) continue;
+      sx += __ldcg(a.A.px + ai);
+      sy += __ldcg(a.A.py + ai);
+      sz += __ldcg(a.A.pz + ai);
+      cnt += 1.0;
+    }
+    cnt = block_sum_fixed(cnt, red);
+    const int nah = (int)cnt;
+    if (nah <= 0 || (int64_t)step >= ph.max_steps) break;
+    sx = block_sum_fixed(sx, red) / cnt;
+    sy = block_sum_fixed(sy, red) / cnt;
+    sz = block_sum_fixed(sz, red) / cnt;
+    if (tid == 0) {
+      const double azn = anchor_next(ph, 0, __ldcg(&S->az[p][0]));
+      s_azn = azn;
+      atomicAdd(&S->interactions, (unsigned long long)nah);
+      S->n_steps = step + 1;
+      S->az[p ^ 1][0] = azn;
+      S->az[p ^ 1][1] = azn;
+    }
+    // keys: squared distance from the centre (non-negative doubles order like
+    // their bit patterns); retired holes and padding sort last
+    for (int t = tid; t < p2; t += nt) {
+      unsigned long long kv = ~0ull;
+      if (t < nh) {
+        const int64_t ai = S->base + t;
+        const int8_t st = __ldcg(a.A.cstate + S->base + a.A.cid[ai]);
+        if ((st & kStateMask) == kStateActive) {
+          const double dx = __ldcg(a.A.px + ai) - sx, dy = __ldcg(a.A.py + ai) - sy,
+                       dz = __ldcg(a.A.pz + ai) - sz;
+          kv = (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz);
+        }
+      }
+      key[t] = kv;
+      idx[t] = t;
+    }
+    __syncthreads();
+    for (int size = 2; size <= p2; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = tid; t < (p2 >> 1); t += nt) {
+          const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const unsigned long long kl = key[lo], kh = key[hi];
+          if ((kl > kh) == up) {
+            key[lo] = kh;
+            key[hi] = kl;
+            const int32_t il = idx[lo];
+            idx[lo] = idx[hi];
+            idx[hi] = il;
+          }
+        }
+        __syncthreads();
+      }
+    // field and update, by sorted position; positions >= nah hold retired
+    // holes (parked shadow only) and padding entries (skipped)
+    const double kc = ph.kc;
+    const double azn = s_azn;
+    for (int j = tid; j < p2; j += nt) {
+      const int t = idx[j];
+      if (t >= nh) continue;
+      const int64_t ai = S->base + t;
+      float ex = 0.0f, ey = 0.0f, ez = 0.0f;
+      if (j < nah && ph.repulsion) {
+        int q = j;
+        while (q > 0 && key[q - 1] == key[j]) --q;
+        if (q > 0) {
+          const double dx = __ldcg(a.A.px + ai) - sx, dy = __ldcg(a.A.py + ai) - sy,
+                       dz = __ldcg(a.A.pz + ai) - sz;
+          const double d2 = __longlong_as_double((long long)key[j]);
+          const double f = kc * (double)q / (d2 * sqrt(d2));
+          ex = (float)(f * dx);
+          ey = (float)(f * dy);
+          ez = (float)(f * dz);
+        }
+      }
+      update_carrier(a, S, slot, 0, ai, step, p, k, ex, ey, ez, azn);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Detector readout of pixel-count maps (Sec. 4.1 selection, Sec. 4.2 noise):
 // one CTA per event.  Pixel energies with Gaussian noise from the event's
 // stream (purpose 3, carrier = pixel), the centre at the largest pixel (first
@@ -1330,6 +1465,20 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
   int grid = (int)((n + threads - 1) / threads);
   grid = grid < 1 ? 1 : (grid > 4096 ? 4096 : grid);
   bin_points_kernel<<<grid, threads, 0, s>>>(ph, x, y, n, pixels, outside);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s) {
+  static bool attr_set = false;
+  const size_t smem = (size_t)kSphMax * (sizeof(unsigned long long) + sizeof(int32_t));
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(spherical_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (a.S > 0) spherical_kernel<<<a.S, 1024, smem, s>>>(a, k0, nk);
   return cudaGetLastError();
 }
 

@@ -198,6 +198,9 @@ int validate_params(const sim_sensor_t* se, const sim_field_t* f, const sim_mobi
   if (!(se->depletion_V >= 0) || !(se->bias_V >= se->depletion_V)) return SIM_EINVAL;
   if (se->grid_n < 1 || se->grid_n > 4096 || se->max_steps < 1) return SIM_EINVAL;
   if (se->species != CTS_HOLES && se->species != CTS_BOTH) return SIM_EINVAL;
+  // the simplified spherical model moves holes only (Sec. 2.2)
+  if (f->spherical != 0 && f->spherical != 1) return SIM_EINVAL;
+  if (f->spherical && se->species != CTS_HOLES) return SIM_EINVAL;
   if (m->model != CTS_MOB_CT && m->model != CTS_MOB_CONST) return SIM_EINVAL;
   if (!(m->mu0_h > 0) || !(m->vsat_h > 0) || !(m->beta_h > 0)) return SIM_EINVAL;
   if (se->species == CTS_BOTH && (!(m->mu0_e > 0) || !(m->vsat_e > 0) || !(m->beta_e > 0)))
@@ -290,6 +293,7 @@ int prepare_event(sim_t* s, const sim_event_t* ev, EventRec* r) {
     r->cap_e = s->sensor.species == CTS_BOTH ? r->n_pairs : 0;
   }
   if ((int64_t)r->cap_h + r->cap_e > s->capacity) return SIM_ENOMEM_BUDGET;
+  if (s->field.spherical && r->cap_h > kSphMax) return SIM_EINVAL;
   return SIM_OK;
 }
 
@@ -505,7 +509,16 @@ int issue_chunk(sim_t* s, int K, bool multi) {
   CK(cudaMemsetAsync(s->d_unit_counter, 0, K * sizeof(int32_t), s->stream));
   CK(cudaMemsetAsync(s->d_ret, 0, (size_t)K * s->S * 2 * sizeof(int32_t), s->stream));
   CK(cudaMemsetAsync(s->d_tiles_done, 0, (size_t)K * s->S * sizeof(int32_t), s->stream));
-  if (plain) {
+  if (s->field.spherical) {
+    // the spherical model: one CTA per slot runs all K steps of its event
+    const StepArgs a = step_args(s, true);
+    const bool timed = s->opt.time_launches != 0 && !plain;
+    const unsigned evflag = capturing(s) ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (timed) CK(cudaEventRecordWithFlags(s->lev[0], s->stream, evflag));
+    CK(launch_spherical(a, 0, K, s->stream));
+    if (timed) CK(cudaEventRecordWithFlags(s->lev[1], s->stream, evflag));
+    s->st_launch += 1;
+  } else if (plain) {
     const StepArgs a = step_args(s, false);
     CK(launch_step(s->variant, a, 0, 1, s->grid, s->stream));
     // one thread per carrier of the running event (the grid is captured
@@ -566,11 +579,12 @@ int run_chunk(sim_t* s) {
   }
   // one launch for the whole chunk: the queue replays the step's pieces K
   // times, slot by slot
-  const bool multi = !plain && s->dynamic && s->ph.repulsion && !s->opt.step_launches;
-  int rc = upload_units(s, !plain, multi);
+  const bool sph = s->field.spherical != 0;
+  const bool multi = !plain && !sph && s->dynamic && s->ph.repulsion && !s->opt.step_launches;
+  int rc = sph ? SIM_OK : upload_units(s, !plain, multi);
   if (rc) return rc;
-  const int gi = 2 * s->variant + (multi ? 1 : 0);
-  const int nl = multi ? 1 : K;  // step-kernel launches in the chunk
+  const int gi = sph ? 2 * variant_count() : 2 * s->variant + (multi ? 1 : 0);
+  const int nl = (multi || sph) ? 1 : K;  // step-kernel launches in the chunk
   CK(cudaEventRecord(s->ev0, s->stream));
   if (!plain && !s->opt.disable_graphs) {
     cudaGraphExec_t& graph = s->graphs[gi];
@@ -999,8 +1013,8 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
     }
     s->own_stream = true;
   }
-  s->graphs.assign(2 * variant_count(), nullptr);
-  s->graph_K.assign(2 * variant_count(), -1);
+  s->graphs.assign(2 * variant_count() + 1, nullptr);
+  s->graph_K.assign(2 * variant_count() + 1, -1);
   s->occ_cache.assign(variant_count(), 0);
   s->variant = -1;
   rc = alloc_all(s);

@@ -268,3 +268,15 @@ def test_readout_rejects_bad_arguments_before_the_device(lib):
     with pytest.raises(cts.SimError) as e:
         cts.sim_readout(np.zeros((1, 9, 9), np.int32), [1], [0], 20.0, n_bins=10, spec_bin_keV=0.0)
     assert e.value.code == cts.SIM_EINVAL
+
+
+def test_spherical_model_needs_holes_only(lib):
+    import workloads as W
+    p = W.preset("track_200keV_320um")
+    with pytest.raises(cts.SimError) as e:
+        cts.Simulator(p["sensor"], p["mobility"], field=W.field_switches(spherical=1))
+    assert e.value.code == cts.SIM_EINVAL
+    p = W.preset("batch_20keV_320um")
+    with pytest.raises(cts.SimError) as e:
+        cts.Simulator(p["sensor"], p["mobility"], field=dict(W.field_switches(), spherical=2))
+    assert e.value.code == cts.SIM_EINVAL
