@@ -1201,7 +1201,7 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
       }
     // field and update, by sorted position; positions >= nah hold retired
     // holes (parked shadow only) and padding entries (skipped)
-    const double kc = ph.kc;
+    const float kcf = ph.f_kc;
     const double azn = s_azn;
     for (int j = tid; j < p2; j += nt) {
       const int t = idx[j];
@@ -1212,13 +1212,16 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
         int q = j;
         while (q > 0 && key[q - 1] == key[j]) --q;
         if (q > 0) {
-          const double dx = __ldcg(a.A.px + ai) - sx, dy = __ldcg(a.A.py + ai) - sy,
-                       dz = __ldcg(a.A.pz + ai) - sz;
-          const double d2 = __longlong_as_double((long long)key[j]);
-          const double f = kc * (double)q / (d2 * sqrt(d2));
-          ex = (float)(f * dx);
-          ey = (float)(f * dy);
-          ez = (float)(f * dz);
+          // offsets and the enclosed count in FP64, the field itself in FP32
+          // like the pairwise path (FP64 sqrt and division are slow here)
+          const float dx = (float)(__ldcg(a.A.px + ai) - sx),
+                      dy = (float)(__ldcg(a.A.py + ai) - sy),
+                      dz = (float)(__ldcg(a.A.pz + ai) - sz);
+          const float rs = rsqrtf((float)__longlong_as_double((long long)key[j]));
+          const float f = kcf * (float)q * rs * rs * rs;
+          ex = f * dx;
+          ey = f * dy;
+          ez = f * dz;
         }
       }
       update_carrier(a, S, slot, 0, ai, step, p, k, ex, ey, ez, azn);
