@@ -322,6 +322,28 @@ def spherical_leg(cts, W, torch, device, stream, events, p):
             "statuses_ok": all(r["status"] == 0 for r in res)}
 
 
+def mip_leg(cts, W, device):
+    """The MIP study of Sec. 4.3: per-axis RMS of the collected electrons of
+    perpendicular 50 um tracks with and without repulsion (paper: 1.24 ->
+    1.27 um with its unprinted electron mobility), and with electrons alone."""
+    import numpy as np
+    name = "mip_50um"
+    p = W.preset(name)
+    evs = W.make_events(name)
+    out = {"workload": name, "events": len(evs), "paper_rms_um": {"without": 1.24, "with": 1.27}}
+    for label, field, sensor in [("with_repulsion", W.field_switches(), p["sensor"]),
+                                 ("without_repulsion", W.field_switches(repulsion=0), p["sensor"]),
+                                 ("electrons_only_with_repulsion", W.field_switches(),
+                                  dict(p["sensor"], species=1))]:
+        with cts.Simulator(sensor, p["mobility"], field, device=device, keep_final_xy=1) as sim:
+            res = sim.run(evs, keep_xy_capacity=2 * p["n_pairs"])
+        d = np.concatenate([r["final_xy"][~np.isnan(r["final_xy"][:, 0])] - [e["x_um"], e["y_um"]]
+                            for r, e in zip(res, evs)])
+        out[label + "_rms_um"] = float(np.sqrt((d ** 2).mean(axis=0)).mean())
+    out["ratio"] = out["with_repulsion_rms_um"] / out["without_repulsion_rms_um"]
+    return out
+
+
 def _offered(sim, W, name, rate, n):
     """Open-loop Poisson arrivals at `rate`; latency = completion - submission."""
     arr = W.poisson_arrivals(rate, n, seed=7)
@@ -525,6 +547,10 @@ def run_ours(args, rank, world, local):
             line["spherical"]["comprehensive_events_per_s"] = events_per_s
         except Exception as e:  # reported, never fatal for the bench line
             line["spherical"] = {"error": repr(e)}
+        try:
+            line["mip"] = mip_leg(cts, W, local)
+        except Exception as e:  # reported, never fatal for the bench line
+            line["mip"] = {"error": repr(e)}
         try:
             big = large_n_leg(cts, W, torch, local, stream)
             big["frac"] = big["step_kernel_tflops"] / peak_tflops

@@ -22,6 +22,10 @@ Presets (sizes from the paper's sensors and energies, Sec. 2 and Sec. 4):
   track_200keV_320um    16 straight 150 um electron tracks, 55 250 pairs, both
                         carrier species, 320 um / 200 V / Vd 60 V, dt 5 ps,
                         17x17 pixels
+  mip_50um              10 minimum-ionising tracks perpendicular through a
+                        50 um sensor (Vd 20 V, 50 V), 80 pairs/um (4000),
+                        lateral sigma 1 nm, both species, dt 5 ps; electrons
+                        are the collected species (see MIP_MOBILITY)
 """
 from __future__ import annotations
 
@@ -54,6 +58,15 @@ def _sensor(thickness, bias, vdep, dt_ps, grid_n, species=HOLES):
                 softening_um=1e-6)
 
 
+# The MIP study collects electrons.  Flipping every charge and the drift field
+# leaves the equations of motion unchanged, so the collected species (the
+# library's "holes", collected at z = 0) takes the electron parameters and
+# the other species (drifting to the back) the hole parameters.
+MIP_MOBILITY = dict(model=MOB_CT, mu0_h=ELECTRON_MOBILITY["mu0_e"],
+                    vsat_h=ELECTRON_MOBILITY["vsat_e"], beta_h=ELECTRON_MOBILITY["beta_e"],
+                    mu0_e=HOLE_MOBILITY["mu0_h"], vsat_e=HOLE_MOBILITY["vsat_h"],
+                    beta_e=HOLE_MOBILITY["beta_h"])
+
 PRESETS = {
     "plain_3keV_100um": dict(
         sensor=_sensor(100, 50, 20, 50, 5), mobility=dict(HOLE_MOBILITY),
@@ -69,6 +82,10 @@ PRESETS = {
         sensor=_sensor(320, 150, 60, 10, 9), mobility=dict(HOLE_MOBILITY),
         n_events=2000, energies=[(8.0, 0.6), (17.5, 0.3), (25.0, 0.1)], sigma_um=-1.0,
         rate_hz=2000.0),
+    "mip_50um": dict(
+        sensor=_sensor(50, 50, 20, 5, 9, species=BOTH), mobility=dict(MIP_MOBILITY),
+        n_events=10, track=True, n_pairs=4000, track_len_um=50.0, theta_max_deg=0.0,
+        sigma_um=0.001),
     "track_200keV_320um": dict(
         sensor=_sensor(320, 200, 60, 5, 17, species=BOTH),
         mobility=dict(HOLE_MOBILITY, **ELECTRON_MOBILITY), n_events=16, track=True,
