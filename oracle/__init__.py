@@ -109,6 +109,10 @@ def lib():
         _lib.or_run_events.argtypes = [P(_Params), P(_Event), i64, P(_Result)]
         _lib.or_max_threads.restype = C.c_int
         _lib.or_fano_pairs.argtypes = [u64, u64, d, d]; _lib.or_fano_pairs.restype = i32
+        _lib.or_ggd_pdf.argtypes = [d, d, d]; _lib.or_ggd_pdf.restype = d
+        _lib.or_fit_ggd.argtypes = [P(d), i64, P(d), P(d)]; _lib.or_fit_ggd.restype = C.c_int
+        _lib.or_ggd_sample.argtypes = [u64, u64, u32, u32, d, d]; _lib.or_ggd_sample.restype = d
+        _lib.or_generate_event.argtypes = [u64, u64, i32, d, d, d, d, d, i32, P(i32), P(i64)]
         _lib.or_field_spherical.argtypes = [i64, P(i64), P(d), P(d), P(d), d, P(d), P(d), P(d)]
         _lib.or_readout_event.argtypes = [P(i32), i32, u64, u64, d, d, d, d, d, P(d), P(d),
                                           P(i32), P(i32), P(d), P(i32)]
@@ -221,6 +225,72 @@ def field_spherical(xyz, kc=None):
                              _ptr(z, C.c_double), coulomb_k() if kc is None else kc,
                              _ptr(ex, C.c_double), _ptr(ey, C.c_double), _ptr(ez, C.c_double))
     return np.stack([ex, ey, ez], axis=1)
+
+
+def ggd_pdf(x, alpha, beta):
+    """Eq. 8, the generalised Gaussian density on the whole line."""
+    return lib().or_ggd_pdf(float(x), float(alpha), float(beta))
+
+
+def fit_ggd(x):
+    """Maximum-likelihood (alpha, beta) of Eq. 8 for samples centred at 0."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    if lib().or_fit_ggd(_ptr(x, C.c_double), x.size, C.byref(a), C.byref(b)) != 0:
+        raise ValueError("fit_ggd needs at least two non-zero samples")
+    return a.value, b.value
+
+
+def ggd_samples(seed, event_id, n, alpha, beta, axis=0):
+    """The generator's GGD variates of carriers 0 .. n-1 on one axis."""
+    L = lib()
+    return np.array([L.or_ggd_sample(int(seed), int(event_id), c, axis, float(alpha),
+                                     float(beta)) for c in range(n)])
+
+
+def generate(events, pitch_um, grid_n):
+    """Fast event generation (Sec. 4.2) from per-event dicts with seed,
+    event_id, n_pairs, x_um, y_um, alpha, beta: pixel counts (n_ev x g x g)
+    and carriers outside the grid."""
+    L = lib()
+    pix = np.zeros((len(events), grid_n, grid_n), np.int32)
+    out = np.zeros(len(events), np.int64)
+    for k, e in enumerate(events):
+        o = C.c_int64(0)
+        L.or_generate_event(int(e["seed"]), int(e["event_id"]), int(e["n_pairs"]),
+                            float(e["x_um"]), float(e["y_um"]), float(e["alpha"]),
+                            float(e["beta"]), float(pitch_um), int(grid_n),
+                            _ptr(pix[k], C.c_int32), C.byref(o))
+        out[k] = o.value
+    return pix, out
+
+
+def alpha_of_t(p, t):
+    """Eq. 10: alpha(t) = p0 + p1 sqrt(t) + p2 t + p3 t^2."""
+    t = np.asarray(t, dtype=np.float64)
+    return p[0] + p[1] * np.sqrt(t) + p[2] * t + p[3] * t * t
+
+
+def beta_of_t(p, t):
+    """Eq. 11 as read here: beta(t) = 2 + p0 max(t - p1, 0)^p2 + p3 exp(p4 t)."""
+    t = np.asarray(t, dtype=np.float64)
+    return 2.0 + p[0] * np.maximum(t - p[1], 0.0) ** p[2] + p[3] * np.exp(p[4] * t)
+
+
+def fit_alpha_of_t(t, alpha, w=None):
+    """Weighted linear least squares of Eq. 10 (numpy's solver)."""
+    t = np.asarray(t, dtype=np.float64)
+    A = np.stack([np.ones_like(t), np.sqrt(t), t, t * t], axis=1)
+    w = np.ones_like(t) if w is None else np.asarray(w, dtype=np.float64)
+    return np.linalg.lstsq(A * w[:, None], np.asarray(alpha) * w, rcond=None)[0]
+
+
+def fit_beta_of_t(t, beta, p0, sigma=None):
+    """Least squares of Eq. 11 from the starting point p0 (scipy's solver)."""
+    from scipy import optimize
+    return optimize.curve_fit(lambda tt, *q: beta_of_t(q, tt), np.asarray(t, float),
+                              np.asarray(beta, float), p0=list(p0), sigma=sigma,
+                              maxfev=20000)[0]
 
 
 def fano_pairs(seed, event_id, energy_keV, fano=0.13):

@@ -50,7 +50,7 @@ enum { OR_MOB_CT = 0, OR_MOB_CONST = 1 };
 enum { OR_PHOTON = 0, OR_TRACK = 1, OR_EXPLICIT = 2 };
 enum { OR_ACTIVE = 0, OR_COLLECTED = 1, OR_RETIRED = 2 };
 enum { OR_PURPOSE_DIFFUSION = 0, OR_PURPOSE_INIT = 1, OR_PURPOSE_FANO = 2,
-       OR_PURPOSE_NOISE = 3 };
+       OR_PURPOSE_NOISE = 3, OR_PURPOSE_GGD = 4 };
 
 typedef struct {
   double thickness_um;   /* H */
@@ -612,5 +612,114 @@ void or_spectrum_add(const double* cluster, int32_t accepted, double lo_keV, dou
     if (isnan(v)) continue;
     const double b = floor((v - lo_keV) / width_keV);
     if (b >= 0.0 && b < (double)n_bins) hist[(int64_t)b] += 1;
+  }
+}
+
+
+/* ------------------------------------------------------------------------ */
+/* Generalised Gaussian model of the collected cloud (Sec. 3.1, Eq. 8) and   */
+/* fast event generation from it (Sec. 4.2).                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 8: f(x) = beta / (2 alpha Gamma(1/beta)) exp(-(|x|/alpha)^beta), the
+ * density on the whole line (the printed form omits the factor 1/2 of the
+ * two-sided density and the absolute value). */
+double or_ggd_pdf(double x, double alpha, double beta) {
+  return beta / (2.0 * alpha * tgamma(1.0 / beta)) * exp(-pow(fabs(x) / alpha, beta));
+}
+
+/* Maximum-likelihood fit of Eq. 8 to samples centred at 0: for a given beta
+ * the likelihood is largest at alpha^beta = (beta / n) sum |x|^beta; the
+ * profile log-likelihood is maximised over beta in [0.3, 20] by golden
+ * section on log beta (it is unimodal there for real data).  Returns 0, -1 if
+ * n < 2 or all samples are 0. */
+static double or_ggd_profile(const double* x, int64_t n, double beta, double* alpha) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += pow(fabs(x[i]), beta);
+  const double a = pow(beta * s / (double)n, 1.0 / beta);
+  *alpha = a;
+  return (double)n * (log(beta / (2.0 * a)) - lgamma(1.0 / beta) - 1.0 / beta);
+}
+
+int or_fit_ggd(const double* x, int64_t n, double* alpha, double* beta) {
+  if (n < 2) return -1;
+  int any = 0;
+  for (int64_t i = 0; i < n; ++i) any |= x[i] != 0.0;
+  if (!any) return -1;
+  const double g = 0.5 * (sqrt(5.0) - 1.0);
+  double lo = log(0.3), hi = log(20.0), a;
+  double c = hi - g * (hi - lo), d = lo + g * (hi - lo);
+  double fc = or_ggd_profile(x, n, exp(c), &a), fd = or_ggd_profile(x, n, exp(d), &a);
+  for (int it = 0; it < 200 && hi - lo > 1e-12; ++it) {
+    if (fc > fd) {
+      hi = d; d = c; fd = fc;
+      c = hi - g * (hi - lo);
+      fc = or_ggd_profile(x, n, exp(c), &a);
+    } else {
+      lo = c; c = d; fc = fd;
+      d = lo + g * (hi - lo);
+      fd = or_ggd_profile(x, n, exp(d), &a);
+    }
+  }
+  *beta = exp(0.5 * (lo + hi));
+  or_ggd_profile(x, n, *beta, alpha);
+  return 0;
+}
+
+/* One standard Gamma(shape) variate, shape > 0, from the event's GGD stream:
+ * Gamma(shape + 1) by Marsaglia and Tsang's squeeze-free rejection (ACM TOMS
+ * 26, 2000) with attempt k drawing (z, u) from counter (carrier, 4 k + axis'),
+ * then the boost Gamma(shape) = Gamma(shape + 1) U^(1 / shape) with U from a
+ * counter of its own.  axis' = 2 * axis for the rejection loop. */
+static double or_gamma(uint64_t seed, uint64_t ev, uint32_t carrier, uint32_t axis, double shape,
+                       uint32_t* sign_word) {
+  const double d = shape + 1.0 - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+  double g = d;
+  for (uint32_t k = 0; k < 64; ++k) {
+    uint32_t w[4];
+    or_stream_words(seed, ev, OR_PURPOSE_GGD, carrier, 4u * k + 2u * axis, w);
+    const double z = sqrt(-2.0 * log(or_uniform(w[0]))) * cos(2.0 * OR_PI * or_uniform(w[1]));
+    const double v1 = 1.0 + c * z;
+    if (v1 <= 0.0) continue;
+    const double v = v1 * v1 * v1;
+    if (log(or_uniform(w[2])) < 0.5 * z * z + d - d * v + d * log(v)) {
+      g = d * v;
+      break;
+    }
+  }
+  uint32_t b[4];
+  or_stream_words(seed, ev, OR_PURPOSE_GGD, carrier, 4u * 64u + axis, b);
+  *sign_word = b[1];
+  return g * pow(or_uniform(b[0]), 1.0 / shape);
+}
+
+/* One GGD(alpha, beta) variate: alpha G^(1/beta), G ~ Gamma(1/beta), with a
+ * random sign (the generalised Gaussian is |X|/alpha = G^(1/beta)). */
+double or_ggd_sample(uint64_t seed, uint64_t ev, uint32_t carrier, uint32_t axis, double alpha,
+                     double beta) {
+  uint32_t sw;
+  const double g = or_gamma(seed, ev, carrier, axis, 1.0 / beta, &sw);
+  const double m = alpha * pow(g, 1.0 / beta);
+  return (sw >> 31) ? -m : m;
+}
+
+/* Fast generation of one event (Sec. 4.2): n carriers with x and y drawn
+ * independently from GGD(alpha, beta) about the entry point (x0, y0), binned
+ * into the grid_n x grid_n pixels of pitch p centred on the origin (the same
+ * pixel rule as the readout of simulated events).  Adds to pixels and
+ * *outside. */
+void or_generate_event(uint64_t seed, uint64_t ev, int32_t n, double x0, double y0, double alpha,
+                       double beta, double pitch_um, int32_t grid_n, int32_t* pixels,
+                       int64_t* outside) {
+  for (int32_t c = 0; c < n; ++c) {
+    const double x = x0 + or_ggd_sample(seed, ev, (uint32_t)c, 0u, alpha, beta);
+    const double y = y0 + or_ggd_sample(seed, ev, (uint32_t)c, 1u, alpha, beta);
+    const double fx = floor(x / pitch_um + 0.5 * (double)grid_n);
+    const double fy = floor(y / pitch_um + 0.5 * (double)grid_n);
+    if (fx < 0.0 || fy < 0.0 || fx >= (double)grid_n || fy >= (double)grid_n) {
+      *outside += 1;
+      continue;
+    }
+    pixels[(int64_t)fy * grid_n + (int64_t)fx] += 1;
   }
 }
