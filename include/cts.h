@@ -354,6 +354,32 @@ int sim_readout(const sim_readout_params_t* prm, const int32_t* counts, const ui
                 const uint64_t* event_ids, int32_t n_events, int32_t device, double* pixel_keV,
                 sim_cluster_t* clusters, int64_t* spectrum);
 
+/* Fast event generation (Sec. 4.2) from the generalised Gaussian model of
+ * Sec. 3 (Eq. 8): one event's n_pairs carriers land at (x_um, y_um) plus
+ * independent x and y offsets drawn from GGD(alpha, beta) (alpha, beta from
+ * cts_ggd_params_at at the event's drift time; n_pairs e.g. from
+ * cts_fano_pairs), binned like simulated events into grid_n x grid_n pixels
+ * of pitch pitch_um centred on the origin.  Offsets are alpha G^(1/beta)
+ * with a random sign, G ~ Gamma(1/beta) by Marsaglia-Tsang rejection for
+ * Gamma(1/beta + 1) and a U^beta boost, drawn in FP32 from the event's
+ * counter-based stream (purpose 4). */
+typedef struct sim_gen_event_t {
+  uint64_t seed, event_id;
+  int32_t n_pairs;
+  int32_t reserved;
+  double x_um, y_um;
+  double alpha, beta;
+} sim_gen_event_t;
+
+/* Generate n_events events (host array) on GPU `device`: pixel counts into
+ * pixels[n_events x grid_n^2] (row-major per event) and carriers that land
+ * off the grid into outside[n_events] (NULL to skip), both host memory.
+ * grid_n 1 .. 32, alpha > 0, beta in [0.3, 20], n_pairs >= 0.  Allocates
+ * device memory for the copies and synchronises.  Returns SIM_OK,
+ * SIM_EINVAL, SIM_ENODEV or SIM_ECUDA. */
+int sim_generate(const sim_gen_event_t* events, int32_t n_events, double pitch_um, int32_t grid_n,
+                 int32_t device, int32_t* pixels, int64_t* outside);
+
 /* FP32 FMA throughput of device `device` (CUDA ordinal) measured by chains of
  * independent fused multiply-adds, packed f32x2 (packed = 1) or scalar: the
  * attainable counterpart of the nominal FP32 peak that the pair kernel's

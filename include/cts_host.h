@@ -69,6 +69,36 @@ double cts_estimate_steps(double thickness_um, double bias_V, double depletion_V
 int cts_fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano,
                    int32_t* n_pairs);
 
+/* Generalised Gaussian model of the collected cloud (Sec. 3).  Eq. 8, read
+ * as the two-sided density beta / (2 alpha Gamma(1/beta)) exp(-(|x|/alpha)^beta)
+ * of positions x relative to the photon's entry point.
+ *
+ * cts_fit_ggd: maximum-likelihood (alpha, beta) of n samples (for a given
+ * beta the optimum has alpha^beta = beta / n sum |x|^beta; beta is found by
+ * golden section on the profile likelihood over [0.3, 20]).  Returns 0, or -1
+ * for n < 2, all-zero or non-finite samples. */
+int cts_fit_ggd(const double* x, int64_t n, double* alpha, double* beta);
+
+/* Eq. 10, alpha(t) = p0 + p1 sqrt(t) + p2 t + p3 t^2 of the drift time t
+ * (ns): weighted linear least squares of n >= 4 points (w = NULL: equal
+ * weights; else residuals are multiplied by w).  Writes p_alpha[4]; returns
+ * 0, or -1 for bad input or a singular system. */
+int cts_fit_alpha_t(const double* t, const double* alpha, const double* w, int32_t n,
+                    double* p_alpha);
+
+/* Eq. 11, read as beta(t) = 2 + p0 max(t - p1, 0)^p2 + p3 exp(p4 t) (the
+ * printed power of t - p1 is undefined below p1): Levenberg-Marquardt least
+ * squares of n >= 5 points from the starting point in p_beta[5], which
+ * receives the fit; sigma (NULL = 1) divides the residuals.  Returns 0, or
+ * -1 for bad input or a non-finite cost at the start. */
+int cts_fit_beta_t(const double* t, const double* beta, const double* sigma, int32_t n,
+                   double* p_beta);
+
+/* alpha(t) and beta(t) of Eqs. 10 and 11 at drift time t >= 0.  Returns 0,
+ * -1 for bad input, -2 if either comes out non-positive. */
+int cts_ggd_params_at(const double* p_alpha, const double* p_beta, double t, double* alpha,
+                      double* beta);
+
 #ifdef __cplusplus
 }
 #endif

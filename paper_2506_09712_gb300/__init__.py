@@ -66,6 +66,12 @@ class sim_cluster_t(C.Structure):
                 ("cy", C.c_int32), ("e_cluster", C.c_double), ("e", C.c_double * 9)]
 
 
+class sim_gen_event_t(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("event_id", C.c_uint64), ("n_pairs", C.c_int32),
+                ("reserved", C.c_int32), ("x_um", C.c_double), ("y_um", C.c_double),
+                ("alpha", C.c_double), ("beta", C.c_double)]
+
+
 class sim_event_t(C.Structure):
     _fields_ = [("event_id", C.c_uint64), ("seed", C.c_uint64), ("kind", C.c_int32),
                 ("n_pairs", C.c_int32), ("energy_keV", C.c_double), ("depth_um", C.c_double),
@@ -104,7 +110,8 @@ EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_e
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
             "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_debug_launch_log",
-            "sim_debug_fma_peak", "sim_readout", "cts_fano_pairs",
+            "sim_debug_fma_peak", "sim_readout", "cts_fano_pairs", "sim_generate",
+            "cts_fit_ggd", "cts_fit_alpha_t", "cts_fit_beta_t", "cts_ggd_params_at",
             "sim_set_variants",
             "sim_get_variants", "sim_autotune", "sim_reset", "cts_field_noalloc", "cts_plan_units", "cts_arena_replay",
             "cts_estimate_steps"]
@@ -158,6 +165,11 @@ def load(build_if_missing: bool = True):
         "sim_readout": [P(sim_readout_params_t), P(i32), P(u64), P(u64), i32, i32, P(d),
                         P(sim_cluster_t), P(i64)],
         "cts_fano_pairs": [u64, u64, d, d, P(i32)],
+        "sim_generate": [P(sim_gen_event_t), i32, d, i32, i32, P(i32), P(i64)],
+        "cts_fit_ggd": [P(d), i64, P(d), P(d)],
+        "cts_fit_alpha_t": [P(d), P(d), P(d), i32, P(d)],
+        "cts_fit_beta_t": [P(d), P(d), P(d), i32, P(d)],
+        "cts_ggd_params_at": [P(d), P(d), d, P(d), P(d)],
         "sim_set_variants": [C.c_void_p, P(i64), P(i32), i32],
         "sim_reset": [C.c_void_p],
         "sim_get_variants": [C.c_void_p, P(i64), P(i32), i32, P(i32)],
@@ -310,6 +322,66 @@ def cts_fano_pairs(seed, event_id, energy_keV, fano=0.13):
     if rc != 0:
         raise ValueError("cts_fano_pairs: bad arguments")
     return n.value
+
+
+def sim_generate(events, pitch_um, grid_n, device=0):
+    """Fast generation on the GPU from dicts with seed, event_id, n_pairs,
+    x_um, y_um, alpha, beta: pixel counts (n_ev x g x g) and off-grid counts."""
+    n = len(events)
+    arr = (sim_gen_event_t * max(n, 1))()
+    for k, e in enumerate(events):
+        arr[k] = sim_gen_event_t(int(e["seed"]), int(e["event_id"]), int(e["n_pairs"]), 0,
+                                 float(e["x_um"]), float(e["y_um"]), float(e["alpha"]),
+                                 float(e["beta"]))
+    pix = np.zeros((n, grid_n, grid_n), np.int32)
+    out = np.zeros(max(n, 1), np.int64)
+    _check(load().sim_generate(arr, n, float(pitch_um), int(grid_n), int(device),
+                               _ptr(pix, C.c_int32), _ptr(out, C.c_int64)), "sim_generate")
+    return pix, out[:n]
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def cts_fit_ggd(x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    if load().cts_fit_ggd(_dptr(x), x.size, C.byref(a), C.byref(b)) != 0:
+        raise ValueError("cts_fit_ggd: need two or more finite, not all zero samples")
+    return a.value, b.value
+
+
+def cts_fit_alpha_t(t, alpha, w=None):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    al = np.ascontiguousarray(alpha, dtype=np.float64)
+    wv = None if w is None else np.ascontiguousarray(w, dtype=np.float64)
+    p = np.zeros(4)
+    if load().cts_fit_alpha_t(_dptr(t), _dptr(al), _dptr(wv) if wv is not None else None,
+                              t.size, _dptr(p)) != 0:
+        raise ValueError("cts_fit_alpha_t failed")
+    return p
+
+
+def cts_fit_beta_t(t, beta, p0, sigma=None):
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    be = np.ascontiguousarray(beta, dtype=np.float64)
+    sg = None if sigma is None else np.ascontiguousarray(sigma, dtype=np.float64)
+    p = np.array(p0, dtype=np.float64)
+    if load().cts_fit_beta_t(_dptr(t), _dptr(be), _dptr(sg) if sg is not None else None,
+                             t.size, _dptr(p)) != 0:
+        raise ValueError("cts_fit_beta_t failed")
+    return p
+
+
+def cts_ggd_params_at(p_alpha, p_beta, t):
+    pa = np.ascontiguousarray(p_alpha, dtype=np.float64)
+    pb = np.ascontiguousarray(p_beta, dtype=np.float64)
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    rc = load().cts_ggd_params_at(_dptr(pa), _dptr(pb), float(t), C.byref(a), C.byref(b))
+    if rc != 0:
+        raise ValueError("cts_ggd_params_at: bad input or non-positive parameters")
+    return a.value, b.value
 
 
 READOUT_DEFAULTS = dict(ev_per_pair=3.62, noise_keV=0.13, window_keV=1.0, veto_factor=3.0,

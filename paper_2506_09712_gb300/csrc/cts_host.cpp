@@ -309,6 +309,166 @@ int fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano)
   return n < 1.0 ? 1 : (int)n;
 }
 
+// ---------------------------------------------------------------------------
+// Generalised Gaussian model of the collected cloud (Sec. 3, Eqs. 8, 10, 11).
+// ---------------------------------------------------------------------------
+namespace {
+// profile log-likelihood of Eq. 8 at shape b, given the logs of |x| (zeros
+// contribute nothing to the sum of |x|^b and are passed as -inf)
+double ggd_profile(const std::vector<double>& lx, double b, double* alpha) {
+  double sum = 0.0;
+  for (double l : lx) sum += std::exp(b * l);
+  const double n = (double)lx.size();
+  const double a = std::pow(b * sum / n, 1.0 / b);
+  *alpha = a;
+  return n * (std::log(b / (2.0 * a)) - std::lgamma(1.0 / b) - 1.0 / b);
+}
+
+// solve the k x k system m x = r by Gaussian elimination with partial pivoting
+bool solve_small(std::vector<double> m, std::vector<double> r, int k, double* x) {
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < k; ++i)
+      if (std::fabs(m[i * k + c]) > std::fabs(m[piv * k + c])) piv = i;
+    if (!(std::fabs(m[piv * k + c]) > 0.0)) return false;
+    if (piv != c) {
+      for (int j = 0; j < k; ++j) std::swap(m[c * k + j], m[piv * k + j]);
+      std::swap(r[c], r[piv]);
+    }
+    for (int i = c + 1; i < k; ++i) {
+      const double f = m[i * k + c] / m[c * k + c];
+      for (int j = c; j < k; ++j) m[i * k + j] -= f * m[c * k + j];
+      r[i] -= f * r[c];
+    }
+  }
+  for (int c = k - 1; c >= 0; --c) {
+    double v = r[c];
+    for (int j = c + 1; j < k; ++j) v -= m[c * k + j] * x[j];
+    x[c] = v / m[c * k + c];
+  }
+  return true;
+}
+}  // namespace
+
+double beta_of_t(const double* p, double t) {
+  const double u = t - p[1];
+  return 2.0 + (u > 0.0 ? p[0] * std::pow(u, p[2]) : 0.0) + p[3] * std::exp(p[4] * t);
+}
+
+double alpha_of_t(const double* p, double t) {
+  return p[0] + p[1] * std::sqrt(t) + p[2] * t + p[3] * t * t;
+}
+
+int fit_ggd(const double* x, int64_t n, double* alpha, double* beta) {
+  if (!x || n < 2) return -1;
+  std::vector<double> lx((size_t)n);
+  bool any = false;
+  for (int64_t i = 0; i < n; ++i) {
+    const double v = std::fabs(x[i]);
+    if (!std::isfinite(v)) return -1;
+    any |= v > 0.0;
+    lx[(size_t)i] = v > 0.0 ? std::log(v) : -INFINITY;
+  }
+  if (!any) return -1;
+  // golden-section search of the profile likelihood over log(beta)
+  const double r = 0.6180339887498949;
+  double lo = std::log(0.3), hi = std::log(20.0), a = 0.0;
+  double x1 = hi - r * (hi - lo), x2 = lo + r * (hi - lo);
+  double f1 = ggd_profile(lx, std::exp(x1), &a), f2 = ggd_profile(lx, std::exp(x2), &a);
+  while (hi - lo > 1e-12) {
+    if (f1 > f2) {
+      hi = x2;
+      x2 = x1;
+      f2 = f1;
+      x1 = hi - r * (hi - lo);
+      f1 = ggd_profile(lx, std::exp(x1), &a);
+    } else {
+      lo = x1;
+      x1 = x2;
+      f1 = f2;
+      x2 = lo + r * (hi - lo);
+      f2 = ggd_profile(lx, std::exp(x2), &a);
+    }
+  }
+  *beta = std::exp(0.5 * (lo + hi));
+  ggd_profile(lx, *beta, alpha);
+  return 0;
+}
+
+int fit_alpha_t(const double* t, const double* y, const double* w, int n, double* p) {
+  if (n < 4) return -1;
+  std::vector<double> m(16, 0.0), r(4, 0.0);
+  for (int i = 0; i < n; ++i) {
+    if (!(t[i] >= 0.0)) return -1;
+    const double wi = w ? w[i] * w[i] : 1.0;
+    const double f[4] = {1.0, std::sqrt(t[i]), t[i], t[i] * t[i]};
+    for (int a = 0; a < 4; ++a) {
+      r[a] += wi * f[a] * y[i];
+      for (int b = 0; b < 4; ++b) m[a * 4 + b] += wi * f[a] * f[b];
+    }
+  }
+  return solve_small(m, r, 4, p) ? 0 : -1;
+}
+
+// Levenberg-Marquardt (Marquardt 1963) for Eq. 11 from the starting point p,
+// with forward-difference derivatives; sigma weights the residuals.
+int fit_beta_t(const double* t, const double* y, const double* sigma, int n, double* p) {
+  if (n < 5) return -1;
+  auto cost = [&](const double* q) {
+    double c = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double e = (y[i] - beta_of_t(q, t[i])) / (sigma ? sigma[i] : 1.0);
+      c += e * e;
+    }
+    return c;
+  };
+  double c0 = cost(p), lambda = 1e-3;
+  if (!std::isfinite(c0)) return -1;
+  std::vector<double> J((size_t)n * 5), e((size_t)n);
+  for (int it = 0; it < 500; ++it) {
+    for (int i = 0; i < n; ++i) {
+      const double s = sigma ? sigma[i] : 1.0;
+      const double f0 = beta_of_t(p, t[i]);
+      e[(size_t)i] = (y[i] - f0) / s;
+      for (int k = 0; k < 5; ++k) {
+        double q[5] = {p[0], p[1], p[2], p[3], p[4]};
+        const double h = 1e-7 * std::max(1.0, std::fabs(p[k]));
+        q[k] += h;
+        J[(size_t)i * 5 + k] = (beta_of_t(q, t[i]) - f0) / (h * s);
+      }
+    }
+    std::vector<double> A(25, 0.0), g(5, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int a = 0; a < 5; ++a) {
+        g[a] += J[(size_t)i * 5 + a] * e[(size_t)i];
+        for (int b = 0; b < 5; ++b) A[a * 5 + b] += J[(size_t)i * 5 + a] * J[(size_t)i * 5 + b];
+      }
+    bool improved = false;
+    for (int tries = 0; tries < 30 && !improved; ++tries) {
+      std::vector<double> M = A;
+      for (int a = 0; a < 5; ++a) M[a * 5 + a] *= 1.0 + lambda;
+      double d[5];
+      if (solve_small(M, g, 5, d)) {
+        double q[5];
+        for (int k = 0; k < 5; ++k) q[k] = p[k] + d[k];
+        const double c1 = cost(q);
+        if (std::isfinite(c1) && c1 < c0) {
+          const double rel = (c0 - c1) / std::max(c0, 1e-300);
+          for (int k = 0; k < 5; ++k) p[k] = q[k];
+          c0 = c1;
+          lambda = std::max(lambda * 0.3, 1e-12);
+          improved = true;
+          if (rel < 1e-15) return 0;
+          break;
+        }
+      }
+      lambda *= 10.0;
+    }
+    if (!improved) return 0;  // no step lowers the cost: a minimum
+  }
+  return 0;
+}
+
 }  // namespace cts
 
 extern "C" {
@@ -355,6 +515,31 @@ int cts_fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double f
   if (!n_pairs || !(energy_keV > 0.0) || !(fano >= 0.0)) return -1;
   *n_pairs = cts::fano_pairs(seed, event_id, energy_keV, fano);
   return 0;
+}
+
+int cts_fit_ggd(const double* x, int64_t n, double* alpha, double* beta) {
+  if (!alpha || !beta) return -1;
+  return cts::fit_ggd(x, n, alpha, beta);
+}
+
+int cts_fit_alpha_t(const double* t, const double* alpha, const double* w, int32_t n,
+                    double* p_alpha) {
+  if (!t || !alpha || !p_alpha) return -1;
+  return cts::fit_alpha_t(t, alpha, w, n, p_alpha);
+}
+
+int cts_fit_beta_t(const double* t, const double* beta, const double* sigma, int32_t n,
+                   double* p_beta) {
+  if (!t || !beta || !p_beta) return -1;
+  return cts::fit_beta_t(t, beta, sigma, n, p_beta);
+}
+
+int cts_ggd_params_at(const double* p_alpha, const double* p_beta, double t, double* alpha,
+                      double* beta) {
+  if (!p_alpha || !p_beta || !alpha || !beta || !(t >= 0.0)) return -1;
+  *alpha = cts::alpha_of_t(p_alpha, t);
+  *beta = cts::beta_of_t(p_beta, t);
+  return (*alpha > 0.0 && *beta > 0.0) ? 0 : -2;
 }
 
 double cts_estimate_steps(double thickness_um, double bias_V, double depletion_V, double mu0_cm2,

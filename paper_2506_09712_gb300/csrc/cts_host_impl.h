@@ -30,6 +30,13 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
 // Fano-distributed carrier-pair count of one photon (see cts_fano_pairs).
 int fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano);
 
+// Generalised Gaussian model (see the cts_fit_* entry points).
+double alpha_of_t(const double* p, double t);
+double beta_of_t(const double* p, double t);
+int fit_ggd(const double* x, int64_t n, double* alpha, double* beta);
+int fit_alpha_t(const double* t, const double* y, const double* w, int n, double* p);
+int fit_beta_t(const double* t, const double* y, const double* sigma, int n, double* p);
+
 class ArenaAllocator {
  public:
   explicit ArenaAllocator(int64_t capacity = 0);

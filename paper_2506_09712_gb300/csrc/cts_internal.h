@@ -187,6 +187,16 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
 constexpr int kSphMax = 16384;
 cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s);
 
+// Fast generation from the generalised Gaussian model: one CTA per event.
+struct GenEvent {
+  unsigned long long seed, id;
+  int32_t n_pairs, pad;
+  double x0, y0, alpha, beta;
+};
+static_assert(sizeof(GenEvent) == 56, "generation record layout");
+cudaError_t launch_generate(const GenEvent* ev, int n_events, double pitch_um, int grid_n,
+                            int32_t* pixels, unsigned long long* outside, cudaStream_t s);
+
 // Readout of pixel-count maps: one CTA per event (grid_n <= 32).  ClusterRec
 // has the layout of the public sim_cluster_t.
 struct ClusterRec {

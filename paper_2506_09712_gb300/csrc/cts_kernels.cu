@@ -1231,6 +1231,68 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
 }
 
 // ---------------------------------------------------------------------------
+// Fast event generation (Sec. 4.2) from the generalised Gaussian model
+// (Eq. 8): x and y of every carrier drawn independently as alpha G^(1/beta)
+// with a random sign, G ~ Gamma(1/beta) = Gamma(1/beta + 1) U^beta, the
+// Gamma(shape >= 1) variate by Marsaglia and Tsang's rejection method (ACM
+// TOMS 26, 2000).  Attempt k of axis a draws from counter (carrier, 4k + 2a),
+// the boost and the sign from (carrier, 256 + a), purpose 4.  FP32 arithmetic;
+// one CTA per event bins its carriers in shared memory.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ggd_variate(uint64_t seed, uint64_t ev, uint32_t carrier,
+                                             uint32_t axis, float alpha, float beta) {
+  const float shape = 1.0f / beta;
+  const float d = shape + 1.0f - 1.0f / 3.0f, c = rsqrtf(9.0f * d);
+  float g = d;
+  for (uint32_t k = 0; k < 64; ++k) {
+    const uint4 w = stream_words(seed, ev, 4u, carrier, 4u * k + 2u * axis);
+    const float z = sqrtf(-2.0f * logf(uniform_f(w.x))) * cospif(2.0f * uniform_f(w.y));
+    const float v1 = fmaf(c, z, 1.0f);
+    if (v1 <= 0.0f) continue;
+    const float v = v1 * v1 * v1;
+    if (logf(uniform_f(w.z)) < 0.5f * z * z + d - d * v + d * logf(v)) {
+      g = d * v;
+      break;
+    }
+  }
+  const uint4 b = stream_words(seed, ev, 4u, carrier, 256u + axis);
+  g *= powf(uniform_f(b.x), beta);
+  const float m = alpha * powf(g, beta == 0.0f ? 1.0f : 1.0f / beta);
+  return (b.y >> 31) ? -m : m;
+}
+
+__global__ void __launch_bounds__(256) generate_kernel(const GenEvent* __restrict__ evs,
+                                                       double pitch_um, int grid_n,
+                                                       int32_t* pixels,
+                                                       unsigned long long* outside) {
+  __shared__ int hist[kReadoutMaxGrid * kReadoutMaxGrid];
+  __shared__ int out_count;
+  const GenEvent e = evs[blockIdx.x];
+  const int np = grid_n * grid_n;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) hist[p] = 0;
+  if (threadIdx.x == 0) out_count = 0;
+  __syncthreads();
+  const float a = (float)e.alpha, be = (float)e.beta;
+  const float inv_pitch = (float)(1.0 / pitch_um), half = 0.5f * (float)grid_n;
+  int lost = 0;
+  for (int c = threadIdx.x; c < e.n_pairs; c += blockDim.x) {
+    const float x = (float)e.x0 + ggd_variate(e.seed, e.id, (uint32_t)c, 0u, a, be);
+    const float y = (float)e.y0 + ggd_variate(e.seed, e.id, (uint32_t)c, 1u, a, be);
+    const float fx = floorf(x * inv_pitch + half), fy = floorf(y * inv_pitch + half);
+    if (fx < 0.0f || fy < 0.0f || fx >= (float)grid_n || fy >= (float)grid_n) {
+      ++lost;
+      continue;
+    }
+    atomicAdd(&hist[(int)fy * grid_n + (int)fx], 1);
+  }
+  if (lost) atomicAdd(&out_count, lost);
+  __syncthreads();
+  for (int p = threadIdx.x; p < np; p += blockDim.x)
+    pixels[(int64_t)blockIdx.x * np + p] = hist[p];
+  if (threadIdx.x == 0) outside[blockIdx.x] = (unsigned long long)out_count;
+}
+
+// ---------------------------------------------------------------------------
 // Detector readout of pixel-count maps (Sec. 4.1 selection, Sec. 4.2 noise):
 // one CTA per event.  Pixel energies with Gaussian noise from the event's
 // stream (purpose 3, carrier = pixel), the centre at the largest pixel (first
@@ -1482,6 +1544,12 @@ cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s) 
     attr_set = true;
   }
   if (a.S > 0) spherical_kernel<<<a.S, 1024, smem, s>>>(a, k0, nk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_generate(const GenEvent* ev, int n_events, double pitch_um, int grid_n,
+                            int32_t* pixels, unsigned long long* outside, cudaStream_t s) {
+  if (n_events > 0) generate_kernel<<<n_events, 256, 0, s>>>(ev, pitch_um, grid_n, pixels, outside);
   return cudaGetLastError();
 }
 

@@ -1666,6 +1666,53 @@ int sim_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32
   return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
 }
 
+int sim_generate(const sim_gen_event_t* events, int32_t n_events, double pitch_um, int32_t grid_n,
+                 int32_t device, int32_t* pixels, int64_t* outside) {
+  static_assert(sizeof(sim_gen_event_t) == sizeof(GenEvent), "generation record layout");
+  if (n_events < 0 || device < 0 || grid_n < 1 || grid_n > kReadoutMaxGrid ||
+      !(pitch_um > 0.0) || !std::isfinite(pitch_um))
+    return SIM_EINVAL;
+  if (n_events > 0 && (!events || !pixels)) return SIM_EINVAL;
+  for (int32_t k = 0; k < n_events; ++k) {
+    const sim_gen_event_t& e = events[k];
+    if (e.n_pairs < 0 || !(e.alpha > 0.0) || !(e.beta >= 0.3 && e.beta <= 20.0) ||
+        !std::isfinite(e.alpha) || !std::isfinite(e.x_um) || !std::isfinite(e.y_um))
+      return SIM_EINVAL;
+  }
+  int sms = 0;
+  if (check_device(device, &sms)) return SIM_ENODEV;
+  cudaSetDevice(device);
+  if (n_events == 0) return SIM_OK;
+  const size_t ne = (size_t)n_events, np = (size_t)grid_n * grid_n;
+  GenEvent* dev = nullptr;
+  int32_t* dp = nullptr;
+  unsigned long long* dout = nullptr;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaSuccess;
+  std::vector<unsigned long long> hout(outside ? ne : 0);
+  do {
+    if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking))) break;
+    if ((e = cudaMalloc(&dev, ne * sizeof(GenEvent)))) break;
+    if ((e = cudaMalloc(&dp, ne * np * sizeof(int32_t)))) break;
+    if ((e = cudaMalloc(&dout, ne * sizeof(unsigned long long)))) break;
+    if ((e = cudaMemcpyAsync(dev, events, ne * sizeof(GenEvent), cudaMemcpyHostToDevice, st)))
+      break;
+    if ((e = launch_generate(dev, n_events, pitch_um, grid_n, dp, dout, st))) break;
+    if ((e = cudaMemcpyAsync(pixels, dp, ne * np * sizeof(int32_t), cudaMemcpyDeviceToHost, st)))
+      break;
+    if (outside && (e = cudaMemcpyAsync(hout.data(), dout, ne * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, st)))
+      break;
+    if ((e = cudaStreamSynchronize(st))) break;
+    for (size_t k = 0; k < hout.size(); ++k) outside[k] = (int64_t)hout[k];
+  } while (0);
+  cudaFree(dev);
+  cudaFree(dp);
+  cudaFree(dout);
+  if (st) cudaStreamDestroy(st);
+  return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
 int sim_readout(const sim_readout_params_t* prm, const int32_t* counts, const uint64_t* seeds,
                 const uint64_t* event_ids, int32_t n_events, int32_t device, double* pixel_keV,
                 sim_cluster_t* clusters, int64_t* spectrum) {

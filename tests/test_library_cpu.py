@@ -280,3 +280,51 @@ def test_spherical_model_needs_holes_only(lib):
     with pytest.raises(cts.SimError) as e:
         cts.Simulator(p["sensor"], p["mobility"], field=dict(W.field_switches(), spherical=2))
     assert e.value.code == cts.SIM_EINVAL
+
+
+def test_ggd_fits_match_the_oracle():
+    import numpy as np
+    import oracle
+    x = oracle.ggd_samples(9, 2, 30000, 4.1, 2.6)
+    a, b = cts.cts_fit_ggd(x)
+    oa, ob = oracle.fit_ggd(x)
+    assert a == pytest.approx(oa, rel=1e-8) and b == pytest.approx(ob, rel=1e-8)
+    with pytest.raises(ValueError):
+        cts.cts_fit_ggd(np.zeros(5))
+    # Eq. 10: weighted linear least squares
+    rng = np.random.default_rng(4)
+    t = np.linspace(0.1, 15.0, 40)
+    pa = [1.0, 1.8, 0.2, -0.004]
+    y = oracle.alpha_of_t(pa, t) + 0.01 * rng.standard_normal(t.size)
+    w = rng.uniform(0.5, 2.0, t.size)
+    assert np.allclose(cts.cts_fit_alpha_t(t, y, w), oracle.fit_alpha_of_t(t, y, w), atol=1e-9)
+    # Eq. 11: noise-free data give back the parameters; on noisy data the
+    # library's Levenberg-Marquardt and scipy's solver agree
+    pb = [0.35, 1.5, 0.6, 1.1, -0.7]
+    start = [0.3, 1.3, 0.5, 0.9, -0.5]
+    assert np.allclose(cts.cts_fit_beta_t(t, oracle.beta_of_t(pb, t), start), pb,
+                       rtol=1e-5, atol=1e-7)
+    yb = oracle.beta_of_t(pb, t) + 0.005 * rng.standard_normal(t.size)
+    q = cts.cts_fit_beta_t(t, yb, start)
+    qo = oracle.fit_beta_of_t(t, yb, start)
+    cost = lambda p: ((yb - oracle.beta_of_t(p, t)) ** 2).sum()
+    assert cost(q) == pytest.approx(cost(qo), rel=1e-4)
+    for tt in (0.5, 3.0, 12.0):
+        a1, b1 = cts.cts_ggd_params_at(pa, pb, tt)
+        assert a1 == pytest.approx(float(oracle.alpha_of_t(pa, tt)), rel=1e-14)
+        assert b1 == pytest.approx(float(oracle.beta_of_t(pb, tt)), rel=1e-14)
+
+
+def test_generate_checks_arguments_before_the_device(lib):
+    ev = dict(seed=1, event_id=0, n_pairs=10, x_um=0.0, y_um=0.0, alpha=2.0, beta=2.5)
+    with pytest.raises(cts.SimError) as e:
+        cts.sim_generate([dict(ev, beta=50.0)], 25.0, 9)
+    assert e.value.code == cts.SIM_EINVAL
+    with pytest.raises(cts.SimError) as e:
+        cts.sim_generate([ev], 25.0, 40)
+    assert e.value.code == cts.SIM_EINVAL
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(cts.SimError) as e:
+            cts.sim_generate([ev], 25.0, 9)
+        assert e.value.code == cts.SIM_ENODEV
