@@ -322,6 +322,35 @@ def spherical_leg(cts, W, torch, device, stream, events, p):
             "statuses_ok": all(r["status"] == 0 for r in res)}
 
 
+def uneven_leg(cts, W, torch, device, stream, n_events=500):
+    """Uneven batching: the first n_events of the 1e4-event set (E ~ U(5, 25)
+    keV, 1381-6906 carriers, 450 um Si), all resident in one batch."""
+    name = "uneven_5_25keV_450um"
+    p = W.preset(name)
+    evs = W.make_events(name, n=n_events)
+    with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_BATCHED, device=device,
+                       max_slots=n_events, stream=stream.cuda_stream, time_launches=1,
+                       hbm_budget_bytes=2 << 30) as sim:
+        sim.stage(evs)
+        torch.cuda.synchronize()
+        s0 = sim.stats()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.execute()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s1 = sim.stats()
+        res = sim.collect(n_events)
+    ms = e0.elapsed_time(e1)
+    inter = sum(r["interactions"] for r in res)
+    kms = s1["step_kernel_ms"] - s0["step_kernel_ms"]
+    return {"workload": name, "events": n_events, "ms": ms, "events_per_s": n_events / (ms * 1e-3),
+            "interactions_per_s": inter / (ms * 1e-3),
+            "step_kernel_tflops": FLOPS_PER_PAIR * inter / (kms * 1e-3) / 1e12,
+            "statuses_ok": all(r["status"] == 0 for r in res)}
+
+
 def mip_leg(cts, W, device):
     """The MIP study of Sec. 4.3: per-axis RMS of the collected electrons of
     perpendicular 50 um tracks with and without repulsion (paper: 1.24 ->
@@ -577,6 +606,11 @@ def run_ours(args, rank, world, local):
                                 "paper": "1e6 events in about 2 min on a 16-core CPU"}
         except Exception as e:  # reported, never fatal for the bench line
             line["generate"] = {"error": repr(e)}
+        try:
+            line["uneven"] = uneven_leg(cts, W, torch, local, stream)
+            line["uneven"]["frac"] = line["uneven"]["step_kernel_tflops"] / peak_tflops
+        except Exception as e:  # reported, never fatal for the bench line
+            line["uneven"] = {"error": repr(e)}
         try:
             line["mip"] = mip_leg(cts, W, local)
         except Exception as e:  # reported, never fatal for the bench line
