@@ -79,6 +79,13 @@ typedef struct sim_sensor_t {
   int64_t max_steps;
   int32_t grid_n;
   int32_t species;
+  /* Optional non-uniform drift field replacing Eq. 6: drift_table_n (2 ..
+   * 4096) samples of the field magnitude (V/um, > 0, pointing toward the
+   * collecting surface like Eq. 6) at z = k H / (n - 1) from the collecting
+   * surface, linearly interpolated; copied at sim_init.  n = 0 (and NULL)
+   * keeps Eq. 6.  The drift-time estimate used to order work stays Eq. 6. */
+  const double* drift_table_Vum;
+  int32_t drift_table_n;
 } sim_sensor_t;
 
 /* Switches of the three transport terms (1 = on); all on reproduces Eqs. 3, 5.

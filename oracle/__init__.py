@@ -53,6 +53,7 @@ class _Params(C.Structure):
         ("mu0_h", C.c_double), ("vsat_h", C.c_double), ("beta_h", C.c_double),
         ("mu0_e", C.c_double), ("vsat_e", C.c_double), ("beta_e", C.c_double),
         ("spherical", C.c_int32),
+        ("drift_table", C.POINTER(C.c_double)), ("drift_table_n", C.c_int32),
     ]
 
 
@@ -155,6 +156,12 @@ def make_params(sensor: dict, field: dict | None = None, mobility: dict | None =
     p.vsat_e = mobility.get("vsat_e", 1.0)
     p.beta_e = mobility.get("beta_e", 1.0)
     p.spherical = field.get("spherical", 0)
+    tab = sensor.get("drift_table_Vum")
+    if tab is not None:
+        tab = np.ascontiguousarray(tab, dtype=np.float64)
+        p._drift_table = tab            # kept alive with the parameters
+        p.drift_table = tab.ctypes.data_as(C.POINTER(C.c_double))
+        p.drift_table_n = tab.size
     return p
 
 

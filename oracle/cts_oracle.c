@@ -69,6 +69,8 @@ typedef struct {
   double mu0_h, vsat_h, beta_h; /* holes: cm^2/Vs, cm/s, - */
   double mu0_e, vsat_e, beta_e; /* electrons */
   int32_t spherical;     /* 1: repulsion by the simplified spherical model (Eq. 7) */
+  const double* drift_table; /* optional E(z) samples (V/um) at z = k H / (n - 1) */
+  int32_t drift_table_n;     /* 0: Eq. 6 */
 } or_params_t;
 
 typedef struct {
@@ -181,6 +183,18 @@ double or_sigma_um(double energy_keV) {
 /* Drift-field magnitude, Eq. 6, with z measured from the pixel side. */
 double or_drift_field(const or_params_t* P, double z) {
   double H = P->thickness_um;
+  if (P->drift_table_n >= 2) {
+    /* a non-uniform profile given as samples, linearly interpolated, the
+     * ends held beyond [0, H] */
+    const int32_t n = P->drift_table_n;
+    double u = z / H * (double)(n - 1);
+    if (u < 0.0) u = 0.0;
+    if (u > (double)(n - 1)) u = (double)(n - 1);
+    int32_t k = (int32_t)floor(u);
+    if (k > n - 2) k = n - 2;
+    const double w = u - (double)k;
+    return P->drift_table[k] + w * (P->drift_table[k + 1] - P->drift_table[k]);
+  }
   return (P->bias_V - P->depletion_V) / H +
          2.0 * P->depletion_V * (H - z) / (H * H);
 }

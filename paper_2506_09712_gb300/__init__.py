@@ -30,7 +30,8 @@ class sim_sensor_t(C.Structure):
                 ("depletion_V", C.c_double), ("temperature_K", C.c_double),
                 ("eps_r", C.c_double), ("pitch_um", C.c_double), ("dt_ps", C.c_double),
                 ("softening_um", C.c_double), ("max_steps", C.c_int64),
-                ("grid_n", C.c_int32), ("species", C.c_int32)]
+                ("grid_n", C.c_int32), ("species", C.c_int32),
+                ("drift_table_Vum", C.POINTER(C.c_double)), ("drift_table_n", C.c_int32)]
 
 
 class sim_field_t(C.Structure):
@@ -526,6 +527,12 @@ def make_sensor(d: dict) -> sim_sensor_t:
     s.pitch_um = d.get("pitch_um", 25.0); s.dt_ps = d["dt_ps"]
     s.softening_um = d.get("softening_um", 1e-6); s.max_steps = d.get("max_steps", 200_000)
     s.grid_n = d.get("grid_n", 9); s.species = d.get("species", CTS_HOLES)
+    tab = d.get("drift_table_Vum")
+    if tab is not None:
+        tab = np.ascontiguousarray(tab, dtype=np.float64)
+        s._drift_table = tab            # kept alive until sim_init has copied it
+        s.drift_table_Vum = tab.ctypes.data_as(C.POINTER(C.c_double))
+        s.drift_table_n = tab.size
     return s
 
 

@@ -49,6 +49,11 @@ struct Phys {
   int32_t mob_model, repulsion, drift, diffusion;
   int32_t species, grid_n;
   int64_t max_steps;
+  // optional non-uniform drift field: drift_n samples (device memory) at
+  // z = k H / (drift_n - 1), linearly interpolated; drift_n = 0 keeps Eq. 6
+  const float* drift_tab;
+  int32_t drift_n;
+  float f_drift_inv_dz;
 };
 
 // Per-slot state, resident in device memory.

@@ -89,12 +89,21 @@ __device__ __forceinline__ double mobility_d(const Phys& ph, int spec, double E)
   return __ddiv_rn(mu0, pow(__dadd_rn(1.0, pow(x, ph.beta[spec])), __drcp_rn(ph.beta[spec])));
 }
 
+// Drift-field magnitude at depth z (Eq. 6, or the handle's sampled profile).
+__device__ __forceinline__ float drift_E(const Phys& ph, float z) {
+  if (ph.drift_n < 2) return ph.f_ea - ph.f_eb * z;
+  const float u = fminf(fmaxf(z * ph.f_drift_inv_dz, 0.0f), (float)(ph.drift_n - 1));
+  const int k = min((int)u, ph.drift_n - 2);
+  const float e0 = __ldg(ph.drift_tab + k), e1 = __ldg(ph.drift_tab + k + 1);
+  return fmaf(u - (float)k, e1 - e0, e0);
+}
+
 // Frame anchor of a species for the next step: the drift-only motion of the
 // cloud centre (its displacement in FP32, accumulated in FP64).  One body
 // (noinline) so every CTA that evaluates it for a slot gets the same bits.
 __device__ __noinline__ double anchor_next(const Phys& ph, int spec, double z) {
   if (!ph.drift) return z;
-  const float E = ph.f_ea - ph.f_eb * (float)z;
+  const float E = drift_E(ph, (float)z);
   const float dz = mobility_f(ph, spec, E) * E * ph.f_dt;
   const double zn = spec == 0 ? __dsub_rn(z, (double)dz) : __dadd_rn(z, (double)dz);
   return fmin(fmax(zn, 0.0), ph.H);
@@ -316,7 +325,7 @@ __device__ __forceinline__ void update_carrier(const StepArgs& a, SlotDev* S, in
     return;
   }
   double x = __ldcg(a.A.px + idx), y = __ldcg(a.A.py + idx), z = __ldcg(a.A.pz + idx);
-  if (ph.drift) Ez -= ph.f_ea - ph.f_eb * (float)z;
+  if (ph.drift) Ez -= drift_E(ph, (float)z);
   const float Em = sqrtf(Ex * Ex + Ey * Ey + Ez * Ez);
   const float mu = mobility_f(ph, spec, Em);
   const float c = (spec ? -mu : mu) * ph.f_dt;

@@ -105,6 +105,8 @@ struct sim_t {
   double* d_partial = nullptr;
   int32_t* d_combine = nullptr;
   int32_t* d_tiles_done = nullptr;
+  float* d_drift = nullptr;           // sampled drift field (optional)
+  std::vector<double> drift_host;     // the caller's samples, copied at init
   int32_t* d_err = nullptr;
   float* d_field = nullptr;
   ExplicitRec* d_explicit = nullptr;
@@ -201,6 +203,13 @@ int validate_params(const sim_sensor_t* se, const sim_field_t* f, const sim_mobi
   // the simplified spherical model moves holes only (Sec. 2.2)
   if (f->spherical != 0 && f->spherical != 1) return SIM_EINVAL;
   if (f->spherical && se->species != CTS_HOLES) return SIM_EINVAL;
+  if (se->drift_table_n != 0) {
+    if (se->drift_table_n < 2 || se->drift_table_n > 4096 || !se->drift_table_Vum)
+      return SIM_EINVAL;
+    for (int32_t k = 0; k < se->drift_table_n; ++k)
+      if (!std::isfinite(se->drift_table_Vum[k]) || !(se->drift_table_Vum[k] > 0.0))
+        return SIM_EINVAL;
+  }
   if (m->model != CTS_MOB_CT && m->model != CTS_MOB_CONST) return SIM_EINVAL;
   if (!(m->mu0_h > 0) || !(m->vsat_h > 0) || !(m->beta_h > 0)) return SIM_EINVAL;
   if (se->species == CTS_BOTH && (!(m->mu0_e > 0) || !(m->vsat_e > 0) || !(m->beta_e > 0)))
@@ -906,7 +915,7 @@ void free_all(sim_t* s) {
                  s->A.rstep, s->A.cstate, s->d_slots, s->d_summary, s->d_readout, s->d_pixels,
                  s->d_units, s->d_cta_begin, s->d_unit_counter, s->d_ret, s->d_partial,
                  s->d_combine, s->d_tiles_done, s->d_err, s->d_field, s->d_explicit,
-                 s->d_list};
+                 s->d_list, s->d_drift};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {s->h_summary, s->h_units, s->h_cta_begin, s->h_list, s->h_slotdev, s->h_readout,
@@ -989,6 +998,10 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
   sim_t* s = new sim_t();
   s->sensor = *sensor;
   if (!(s->sensor.softening_um > 0)) s->sensor.softening_um = 1e-6;
+  if (sensor->drift_table_n >= 2)
+    s->drift_host.assign(sensor->drift_table_Vum, sensor->drift_table_Vum + sensor->drift_table_n);
+  s->sensor.drift_table_Vum = s->drift_host.empty() ? nullptr : s->drift_host.data();
+  s->sensor.drift_table_n = (int32_t)s->drift_host.size();
   s->field = *field;
   s->mob = *mobility;
   s->opt = opt;
@@ -1018,6 +1031,18 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
   s->occ_cache.assign(variant_count(), 0);
   s->variant = -1;
   rc = alloc_all(s);
+  if (!rc && !s->drift_host.empty()) {
+    const size_t n = s->drift_host.size();
+    std::vector<float> f(s->drift_host.begin(), s->drift_host.end());
+    if (cudaMalloc(&s->d_drift, n * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(s->d_drift, f.data(), n * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = SIM_ECUDA;
+    } else {
+      s->ph.drift_tab = s->d_drift;
+      s->ph.drift_n = (int32_t)n;
+      s->ph.f_drift_inv_dz = (float)((double)(n - 1) / s->ph.H);
+    }
+  }
   if (!rc) rc = set_variant(s, choose_variant(s));
   s->base_variant = s->variant;
   if (rc) {

@@ -433,3 +433,34 @@ def test_fma_chain_probe_is_within_the_nominal_peak():
     for packed in (True, False):
         f = cts.sim_debug_fma_peak(0, packed)
         assert 0.3 * nominal < f < 1.02 * nominal, (packed, f, nominal)
+
+
+@pytest.mark.gpu
+def test_sampled_drift_field_matches_the_oracle():
+    # a non-uniform profile (strong near the pixels, weak at the back) given as
+    # 64 samples replaces Eq. 6 on both sides
+    name = "plain_3keV_100um"
+    p = W.preset(name)
+    H = p["sensor"]["thickness_um"]
+    z = np.linspace(0.0, H, 64)
+    table = 0.15 + 0.9 * np.exp(-z / 30.0)
+    sensor = dict(p["sensor"], drift_table_Vum=table)
+    evs = W.make_events(name, n=6, first_id=90)
+    refs = oracle.run_events(oracle.make_params(sensor, W.field_switches(), p["mobility"]), evs)
+    with cts.Simulator(sensor, p["mobility"]) as sim:
+        got = sim.run(evs)
+    for g, r in zip(got, refs):
+        _compare_events(g, r, g["n_carriers"])
+    # the profile changes the result: the plain Eq. 6 run takes other steps
+    with cts.Simulator(p["sensor"], p["mobility"]) as sim:
+        plain = sim.run(evs)
+    assert any(a["n_steps"] != b["n_steps"] for a, b in zip(got, plain))
+    # two samples on Eq. 6 reproduce Eq. 6
+    s = p["sensor"]
+    e0 = (s["bias_V"] + s["depletion_V"]) / H
+    eh = (s["bias_V"] - s["depletion_V"]) / H
+    with cts.Simulator(dict(s, drift_table_Vum=[e0, eh]), p["mobility"]) as sim:
+        two = sim.run(evs)
+    for a, b in zip(two, plain):
+        assert abs(a["n_steps"] - b["n_steps"]) <= 1
+        assert np.abs(a["pixels"] - b["pixels"]).max() <= 1

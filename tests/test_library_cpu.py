@@ -328,3 +328,12 @@ def test_generate_checks_arguments_before_the_device(lib):
         with pytest.raises(cts.SimError) as e:
             cts.sim_generate([ev], 25.0, 9)
         assert e.value.code == cts.SIM_ENODEV
+
+
+@pytest.mark.parametrize("table", [[1.0], [1.0, -0.5], [1.0, float("nan")], [0.0, 1.0]])
+def test_bad_drift_tables_are_rejected(lib, table):
+    import workloads as W
+    p = W.preset("plain_3keV_100um")
+    with pytest.raises(cts.SimError) as e:
+        cts.Simulator(dict(p["sensor"], drift_table_Vum=table), p["mobility"])
+    assert e.value.code == cts.SIM_EINVAL
