@@ -190,6 +190,9 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
 // Simplified spherical model: one CTA per slot for steps k0 .. k0 + nk - 1;
 // events of at most kSphMax holes (sorted in shared memory).
 constexpr int kSphMax = 16384;
+// spherical_prepare raises the kernel's shared-memory limit on the current
+// device (once per handle, at sim_init, outside any stream capture).
+cudaError_t spherical_prepare();
 cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s);
 
 // Fast generation from the generalised Gaussian model: one CTA per event.

@@ -1542,17 +1542,15 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
   return cudaGetLastError();
 }
 
+constexpr size_t kSphSmem = (size_t)kSphMax * (sizeof(unsigned long long) + sizeof(int32_t));
+
+cudaError_t spherical_prepare() {
+  return cudaFuncSetAttribute(spherical_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kSphSmem);
+}
+
 cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s) {
-  static bool attr_set = false;
-  const size_t smem = (size_t)kSphMax * (sizeof(unsigned long long) + sizeof(int32_t));
-  if (!attr_set) {
-    const cudaError_t e = cudaFuncSetAttribute(spherical_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  if (a.S > 0) spherical_kernel<<<a.S, 1024, smem, s>>>(a, k0, nk);
+  if (a.S > 0) spherical_kernel<<<a.S, 1024, kSphSmem, s>>>(a, k0, nk);
   return cudaGetLastError();
 }
 

@@ -844,6 +844,19 @@ int halloc(sim_t* s, T** p, size_t count) {
   return SIM_OK;
 }
 
+// Makes `device` current for a stateless entry point and restores the
+// caller's current device when the call returns.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(device);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 int check_device(int device, int* sms) {
   int n = 0;
   if (cudaGetDeviceCount(&n) != cudaSuccess || n <= device || device < 0) return SIM_ENODEV;
@@ -1044,6 +1057,7 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
     }
   }
   if (!rc) rc = set_variant(s, choose_variant(s));
+  if (!rc && s->field.spherical && spherical_prepare() != cudaSuccess) rc = SIM_ECUDA;
   s->base_variant = s->variant;
   if (rc) {
     free_all(s);
@@ -1706,7 +1720,7 @@ int sim_generate(const sim_gen_event_t* events, int32_t n_events, double pitch_u
   }
   int sms = 0;
   if (check_device(device, &sms)) return SIM_ENODEV;
-  cudaSetDevice(device);
+  DeviceGuard guard(device);
   if (n_events == 0) return SIM_OK;
   const size_t ne = (size_t)n_events, np = (size_t)grid_n * grid_n;
   GenEvent* dev = nullptr;
@@ -1751,7 +1765,7 @@ int sim_readout(const sim_readout_params_t* prm, const int32_t* counts, const ui
   if (n_events > 0 && (!counts || !seeds || !event_ids || !clusters)) return SIM_EINVAL;
   int sms = 0;
   if (check_device(device, &sms)) return SIM_ENODEV;
-  cudaSetDevice(device);
+  DeviceGuard guard(device);
   if (n_events == 0) return SIM_OK;
   const size_t np = (size_t)g * g, ne = (size_t)n_events;
   ReadoutArgs r{};
@@ -1820,7 +1834,7 @@ int sim_debug_fma_peak(int32_t device, int32_t packed, double* flops_per_s) {
   if (!flops_per_s || device < 0) return SIM_EINVAL;
   int sms = 0;
   if (check_device(device, &sms)) return SIM_ENODEV;
-  cudaSetDevice(device);
+  DeviceGuard guard(device);
   const int grid = sms * 8;  // 2048 threads per SM
   const int iters = 1 << 11;
   float* d = nullptr;
