@@ -75,6 +75,7 @@ class _Result(C.Structure):
         ("final_y", C.POINTER(C.c_double)), ("retire_step", C.POINTER(C.c_int32)),
         ("pos_out", C.POINTER(C.c_double)), ("state_out", C.POINTER(C.c_int8)),
         ("sign_out", C.POINTER(C.c_int8)),
+        ("induced", C.POINTER(C.c_double)), ("induced_capacity", C.c_int64),
     ]
 
 
@@ -414,10 +415,15 @@ class EventResult:
     pos: np.ndarray
     state: np.ndarray
     sign: np.ndarray
+    induced: np.ndarray = None    # charge on the collecting surface after each step (e)
+
+
+INDUCED_CAPACITY = 20000   # steps of the induced-charge record the oracle keeps
 
 
 def _alloc_result(params, n):
-    bufs = dict(pixels=np.zeros(params.grid_n * params.grid_n, dtype=np.int32),
+    bufs = dict(induced=np.zeros(int(min(params.max_steps, INDUCED_CAPACITY)) or 1),
+                pixels=np.zeros(params.grid_n * params.grid_n, dtype=np.int32),
                 fx=np.zeros(max(n, 1)), fy=np.zeros(max(n, 1)),
                 rs=np.zeros(max(n, 1), dtype=np.int32), pos=np.zeros(3 * max(n, 1)),
                 st=np.zeros(max(n, 1), dtype=np.int8), sg=np.zeros(max(n, 1), dtype=np.int8))
@@ -429,6 +435,8 @@ def _alloc_result(params, n):
     r.pos_out = _ptr(bufs["pos"], C.c_double)
     r.state_out = _ptr(bufs["st"], C.c_int8)
     r.sign_out = _ptr(bufs["sg"], C.c_int8)
+    r.induced = _ptr(bufs["induced"], C.c_double)
+    r.induced_capacity = bufs["induced"].size
     return r, bufs
 
 
@@ -439,7 +447,8 @@ def _wrap(params, r, bufs, n):
         pixels=bufs["pixels"].reshape(params.grid_n, params.grid_n).copy(),
         final_xy=np.stack([bufs["fx"][:n], bufs["fy"][:n]], axis=1),
         retire_step=bufs["rs"][:n].copy(), pos=bufs["pos"][:3 * n].reshape(n, 3).copy(),
-        state=bufs["st"][:n].copy(), sign=bufs["sg"][:n].copy())
+        state=bufs["st"][:n].copy(), sign=bufs["sg"][:n].copy(),
+        induced=bufs["induced"][:min(r.n_steps, bufs["induced"].size)].copy())
 
 
 def run_events(params: _Params, events: list[dict]) -> list[EventResult]:

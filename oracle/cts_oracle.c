@@ -96,6 +96,9 @@ typedef struct {
   double* pos_out;      /* 3 * n_carriers, positions when the run stopped */
   int8_t* state_out;    /* per carrier */
   int8_t* sign_out;     /* per carrier */
+  double* induced;      /* optional: charge induced on the collecting surface
+                           after each step, in units of e */
+  int64_t induced_capacity;
 } or_result_t;
 
 /* ------------------------------------------------------------------------ */
@@ -450,6 +453,7 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
   or_boundaries(P, n, x, y, z, sign, state, -1, R);
 
   int64_t step = 0;
+  double induced_q = 0.0;
   for (;; ++step) {
     int64_t holes_active = 0, n_act = 0;
     for (int64_t c = 0; c < n; ++c) {
@@ -493,9 +497,19 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
     }
     for (int64_t r = 0; r < n_act; ++r) {
       int64_t c = rows[r];
+      ez[r] = z[c];  /* the depth before the move, for the induced charge */
       x[c] = nx[r]; y[c] = ny[r]; z[c] = nz[r];
     }
     or_boundaries(P, n, x, y, z, sign, state, step, R);
+    /* Shockley-Ramo with the weighting potential 1 - z / H of the whole
+     * collecting surface (a planar sensor): a charge q moving from z_a to z_b
+     * induces q (z_a - z_b) / H; carriers that left stop at the surface. */
+    for (int64_t r = 0; r < n_act; ++r) {
+      int64_t c = rows[r];
+      double zb = z[c] < 0.0 ? 0.0 : (z[c] > P->thickness_um ? P->thickness_um : z[c]);
+      induced_q += (double)sign[c] * (ez[r] - zb) / P->thickness_um;
+    }
+    if (R->induced && step < R->induced_capacity) R->induced[step] = induced_q;
   }
   R->n_steps = step;
 

@@ -239,3 +239,26 @@ def test_repulsion_flattens_the_profile(orc):
     assert abs(k_free) < 0.2, k_free
     # repulsion also widens the profile
     assert xy.std() > 1.2 * xy0.std()
+
+
+def test_induced_charge_on_the_collecting_surface(orc):
+    # Shockley-Ramo with the planar weighting potential 1 - z/H: one hole
+    # drifting at constant speed induces v t / H, and z0 / H in total
+    H, Vb, dt_ps = 200.0, 100.0, 10.0
+    P = _params(orc, thickness=H, bias=Vb, vdep=0.0, dt_ps=dt_ps, repulsion=0, diffusion=0,
+                mob=dict(W.HOLE_MOBILITY, model=1))
+    z0 = 120.0
+    r = orc.run_event(P, W.explicit_event(np.array([[0.0, 0.0, z0]])))
+    v = 48.0 * Vb / H                            # um/ns (480 cm^2/Vs)
+    k = np.arange(1, r.n_steps + 1)
+    expect = np.minimum(k * v * dt_ps * 1e-3, z0) / H
+    assert np.allclose(r.induced, expect, rtol=1e-12, atol=1e-12)
+    # a whole cloud with repulsion, diffusion and the Eq. 6 field: once every
+    # hole is in, the sum telescopes to sum(z0) / H whatever the paths were
+    P = _params(orc, thickness=H, bias=Vb, vdep=40.0, dt_ps=dt_ps)
+    rng = np.random.default_rng(8)
+    pts = rng.normal([0.0, 0.0, 150.0], 2.0, (300, 3))
+    r = orc.run_event(P, W.explicit_event(pts))
+    assert r.status == 0
+    assert r.induced[-1] == pytest.approx(pts[:, 2].sum() / H, rel=1e-12)
+    assert len(r.induced) == r.n_steps
