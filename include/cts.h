@@ -124,6 +124,7 @@ typedef struct sim_options_t {
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
   int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */
   int32_t time_launches;   /* 1 = time every step-kernel launch with CUDA events */
+  int32_t keep_induced;    /* 1 = record the induced charge per step (sim_result_t) */
   int32_t step_launches;   /* 1 = one step-kernel launch per step; 0 = one launch
                               per chunk with dynamic-queue variants: a slot's
                               next step starts as soon as all of its tiles are
@@ -172,6 +173,15 @@ typedef struct sim_result_t {
   double* final_xy;      /* 2 * capacity */
   int32_t* retire_step;  /* capacity */
   int64_t capacity;      /* entries available in final_xy / retire_step */
+  /* Transient signal (options.keep_induced): the charge (units of e) induced
+   * on the whole collecting surface after each executed step, by the
+   * Shockley-Ramo theorem with the planar weighting potential 1 - z/H (a
+   * carrier of charge q moving from z_a to z_b adds q (z_a - z_b) / H;
+   * carriers that leave stop at the surface).  The paper names the weighting
+   * field as an extension (Sec. 5.3); pixel weighting fields are not modelled.
+   * Entries beyond n_steps are NaN; NULL skips. */
+  double* induced_e;
+  int64_t induced_capacity;
 } sim_result_t;
 
 typedef struct sim_stats_t {

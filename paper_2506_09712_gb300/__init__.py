@@ -51,7 +51,7 @@ class sim_options_t(C.Structure):
                 ("hbm_budget_bytes", C.c_int64), ("queue_capacity", C.c_int32),
                 ("variant", C.c_int32), ("disable_graphs", C.c_int32),
                 ("keep_final_xy", C.c_int32), ("time_launches", C.c_int32),
-                ("step_launches", C.c_int32),
+                ("keep_induced", C.c_int32), ("step_launches", C.c_int32),
                 ("stream", C.c_void_p)]
 
 
@@ -89,7 +89,8 @@ class sim_result_t(C.Structure):
                 ("t_submit_ns", C.c_double), ("t_start_ns", C.c_double),
                 ("t_done_ns", C.c_double), ("pixels", C.POINTER(C.c_int32)),
                 ("final_xy", C.POINTER(C.c_double)), ("retire_step", C.POINTER(C.c_int32)),
-                ("capacity", C.c_int64)]
+                ("capacity", C.c_int64), ("induced_e", C.POINTER(C.c_double)),
+                ("induced_capacity", C.c_int64)]
 
 
 class sim_stats_t(C.Structure):
@@ -586,8 +587,10 @@ def make_events(events: list[dict]):
 class Results:
     """Caller-owned result buffers for n events."""
 
-    def __init__(self, n: int, grid_n: int, capacity: int = 0):
+    def __init__(self, n: int, grid_n: int, capacity: int = 0, induced_capacity: int = 0):
         self.n, self.grid_n, self.capacity = n, grid_n, capacity
+        self.induced_capacity = induced_capacity
+        self.induced = np.zeros((max(n, 1), max(induced_capacity, 1)), dtype=np.float64)
         self.pixels = np.zeros((max(n, 1), grid_n, grid_n), dtype=np.int32)
         self.final_xy = np.zeros((max(n, 1), max(capacity, 1), 2), dtype=np.float64)
         self.retire_step = np.zeros((max(n, 1), max(capacity, 1)), dtype=np.int32)
@@ -599,6 +602,9 @@ class Results:
                 r.final_xy = _ptr(self.final_xy[k], C.c_double)
                 r.retire_step = _ptr(self.retire_step[k], C.c_int32)
                 r.capacity = capacity
+            if induced_capacity:
+                r.induced_e = _ptr(self.induced[k], C.c_double)
+                r.induced_capacity = induced_capacity
 
     def record(self, k: int) -> dict:
         r = self.arr[k]
@@ -608,7 +614,9 @@ class Results:
                     t_start_ns=r.t_start_ns, t_done_ns=r.t_done_ns,
                     pixels=self.pixels[k].copy(),
                     final_xy=self.final_xy[k, :r.n_carriers].copy() if self.capacity else None,
-                    retire_step=self.retire_step[k, :r.n_carriers].copy() if self.capacity else None)
+                    retire_step=self.retire_step[k, :r.n_carriers].copy() if self.capacity else None,
+                    induced=(self.induced[k, :min(r.n_steps, self.induced_capacity)].copy()
+                             if self.induced_capacity else None))
 
 
 class Simulator:
@@ -642,9 +650,10 @@ class Simulator:
         except Exception:
             pass
 
-    def run(self, events: list[dict], keep_xy_capacity: int = 0) -> list[dict]:
+    def run(self, events: list[dict], keep_xy_capacity: int = 0,
+            induced_capacity: int = 0) -> list[dict]:
         evs = make_events(events)
-        res = Results(len(events), self.grid_n, keep_xy_capacity)
+        res = Results(len(events), self.grid_n, keep_xy_capacity, induced_capacity)
         _check(sim_run(self.h, evs, len(events), res.arr), "sim_run")
         return [res.record(k) for k in range(len(events))]
 
@@ -655,8 +664,8 @@ class Simulator:
     def execute(self):
         _check(sim_execute(self.h), "sim_execute")
 
-    def collect(self, n: int, keep_xy_capacity: int = 0) -> list[dict]:
-        res = Results(n, self.grid_n, keep_xy_capacity)
+    def collect(self, n: int, keep_xy_capacity: int = 0, induced_capacity: int = 0) -> list[dict]:
+        res = Results(n, self.grid_n, keep_xy_capacity, induced_capacity)
         rc, got = sim_collect(self.h, res.arr, n)
         _check(rc, "sim_collect")
         return [res.record(k) for k in range(got)]
@@ -665,8 +674,9 @@ class Simulator:
         evs = make_events(events)
         return sim_submit(self.h, evs, len(events))
 
-    def poll(self, max_out: int, timeout_ms: int, keep_xy_capacity: int = 0) -> list[dict]:
-        res = Results(max_out, self.grid_n, keep_xy_capacity)
+    def poll(self, max_out: int, timeout_ms: int, keep_xy_capacity: int = 0,
+             induced_capacity: int = 0) -> list[dict]:
+        res = Results(max_out, self.grid_n, keep_xy_capacity, induced_capacity)
         rc, n = sim_poll(self.h, res.arr, max_out, timeout_ms)
         if rc == SIM_ETIMEOUT:
             return []

@@ -151,6 +151,7 @@ struct StepArgs {
   double* partial;           // FP64 accumulators of split tiles (3 x tile_i each, kept zero)
   int32_t* combine_count;    // per i-block
   int32_t* tiles_done;       // [K][S]: tiles of each slot updated at each chunk step
+  double* induced;           // [K][S]: charge induced at each chunk step (e); NULL = off
   float* field_out;          // FIELD_ONLY output, SoA [3][capacity]
   int32_t* err;              // global error bits
   unsigned long long* trace; // optional: per CTA {smid, t_start, t_end, pairs, units,

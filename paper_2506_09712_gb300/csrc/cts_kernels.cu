@@ -311,8 +311,10 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float t) {
 }
 
 // Position update of one carrier (Eqs. 3, 5, 6; Sec. 2.1) with the field E
-// (V/um) of its step, collection/exit and the next shadow entry.
-__device__ __forceinline__ void update_carrier(const StepArgs& a, SlotDev* S, int slot, int spec,
+// (V/um) of its step, collection/exit and the next shadow entry.  Returns the
+// charge (units of e) the move induces on the collecting surface
+// (Shockley-Ramo, weighting potential 1 - z/H, the end point held on [0, H]).
+__device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, int slot, int spec,
                                                int64_t idx, int step, int p, int k, float Ex,
                                                float Ey, float Ez, double azn) {
   const Phys& ph = a.ph;
@@ -322,9 +324,10 @@ __device__ __forceinline__ void update_carrier(const StepArgs& a, SlotDev* S, in
   const int8_t st = __ldcg(a.A.cstate + rid);
   if ((st & kStateMask) != kStateActive) {
     shout[idx] = make_float4(kParked, kParked, kParked, 0.0f);
-    return;
+    return 0.0;
   }
   double x = __ldcg(a.A.px + idx), y = __ldcg(a.A.py + idx), z = __ldcg(a.A.pz + idx);
+  const double z_start = z;
   if (ph.drift) Ez -= drift_E(ph, (float)z);
   const float Em = sqrtf(Ex * Ex + Ey * Ey + Ez * Ez);
   const float mu = mobility_f(ph, spec, Em);
@@ -364,6 +367,16 @@ __device__ __forceinline__ void update_carrier(const StepArgs& a, SlotDev* S, in
   } else {
     shout[idx] = make_float4((float)(x - S->ax), (float)(y - S->ay), (float)(z - azn), 0.0f);
   }
+  const double zb = fmin(fmax(z, 0.0), ph.H);
+  return (spec ? zb - z_start : z_start - zb) / ph.H;
+}
+
+// Adds a warp's induced charges to the slot's per-step total (all 32 lanes
+// of the warp call this).
+__device__ __forceinline__ void add_induced(const StepArgs& a, int k, int slot, double q) {
+  if (!a.induced) return;
+  for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
+  if ((threadIdx.x & 31) == 0 && q != 0.0) atomicAdd(a.induced + (int64_t)k * a.S + slot, q);
 }
 
 // Per-slot duties of a step, done once per slot: interaction count, step
@@ -738,13 +751,15 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
       const float kc = a.ph.f_kc;
       if (skip) {
       } else if (a.fused) {
+        double q = 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int li = r * NT + tid;
           if (li < U.ni)
-            update_carrier(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
-                           kc * vy[r], kc * vz[r], s_azn[spec]);
+            q += update_carrier(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
+                                kc * vy[r], kc * vz[r], s_azn[spec]);
         }
+        add_induced(a, k, U.slot, q);
       } else {
         const int64_t cap = a.A.capacity;
 #pragma unroll
@@ -800,12 +815,15 @@ __global__ void update_kernel(StepArgs a, int k, const int32_t* slot_list, int n
     if (blockIdx.x == 0 && threadIdx.x == 0) slot_duties(a, S, step, p, nah, nae, azn0, azn1);
     const int n = S->n_h + S->n_e;
     const int64_t cap = a.A.capacity;
+    double qi = 0.0;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
       const int spec = t < S->n_h ? 0 : 1;
       const int64_t idx = S->base + (spec ? S->cap_h + (t - S->n_h) : t);
-      update_carrier(a, S, slot, spec, idx, step, p, k, a.field_out[idx], a.field_out[cap + idx],
-                     a.field_out[2 * cap + idx], spec ? azn1 : azn0);
+      qi += update_carrier(a, S, slot, spec, idx, step, p, k, a.field_out[idx],
+                           a.field_out[cap + idx], a.field_out[2 * cap + idx],
+                           spec ? azn1 : azn0);
     }
+    add_induced(a, k, slot, qi);
   }
 }
 
@@ -1212,6 +1230,7 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
     // holes (parked shadow only) and padding entries (skipped)
     const float kcf = ph.f_kc;
     const double azn = s_azn;
+    double qi = 0.0;
     for (int j = tid; j < p2; j += nt) {
       const int t = idx[j];
       if (t >= nh) continue;
@@ -1233,8 +1252,9 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
           ez = f * dz;
         }
       }
-      update_carrier(a, S, slot, 0, ai, step, p, k, ex, ey, ez, azn);
+      qi += update_carrier(a, S, slot, 0, ai, step, p, k, ex, ey, ez, azn);
     }
+    add_induced(a, k, slot, qi);
     __syncthreads();
   }
 }

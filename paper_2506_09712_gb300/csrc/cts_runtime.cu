@@ -60,6 +60,7 @@ struct Done {
   std::vector<int32_t> pixels;
   std::vector<double> final_xy;
   std::vector<int32_t> rstep;
+  std::vector<double> induced;  // charge on the collecting surface after each step (e)
   int64_t order = 0;
 };
 
@@ -74,6 +75,8 @@ struct HostSlot {
   int32_t n_h = 0, n_e = 0;
   int32_t status = 0;
   int64_t n_steps = 0, interactions = 0;
+  std::vector<double> induced;  // per executed step (options.keep_induced)
+  double induced_q = 0.0;
 };
 
 }  // namespace
@@ -106,6 +109,8 @@ struct sim_t {
   int32_t* d_combine = nullptr;
   int32_t* d_tiles_done = nullptr;
   float* d_drift = nullptr;           // sampled drift field (optional)
+  double* d_induced = nullptr;        // [K][S] induced charge per chunk step (keep_induced)
+  double* h_induced = nullptr;
   std::vector<double> drift_host;     // the caller's samples, copied at init
   int32_t* d_err = nullptr;
   float* d_field = nullptr;
@@ -431,6 +436,7 @@ StepArgs step_args(sim_t* s, bool fused) {
   a.partial = s->d_partial;
   a.combine_count = s->d_combine;
   a.tiles_done = s->d_tiles_done;
+  a.induced = s->d_induced;
   a.field_out = s->d_field;
   a.err = s->d_err;
   a.ph = s->ph;
@@ -518,6 +524,8 @@ int issue_chunk(sim_t* s, int K, bool multi) {
   CK(cudaMemsetAsync(s->d_unit_counter, 0, K * sizeof(int32_t), s->stream));
   CK(cudaMemsetAsync(s->d_ret, 0, (size_t)K * s->S * 2 * sizeof(int32_t), s->stream));
   CK(cudaMemsetAsync(s->d_tiles_done, 0, (size_t)K * s->S * sizeof(int32_t), s->stream));
+  if (s->d_induced)
+    CK(cudaMemsetAsync(s->d_induced, 0, (size_t)K * s->S * sizeof(double), s->stream));
   if (s->field.spherical) {
     // the spherical model: one CTA per slot runs all K steps of its event
     const StepArgs a = step_args(s, true);
@@ -560,6 +568,7 @@ int issue_chunk(sim_t* s, int K, bool multi) {
                   s->stream));
   s->st_launch += 1;
   CK(d2h(s, s->h_summary, s->d_summary, s->S * sizeof(SlotSummary)));
+  if (s->d_induced) CK(d2h(s, s->h_induced, s->d_induced, (size_t)K * s->S * sizeof(double)));
   CK(d2h(s, s->h_err, s->d_err, sizeof(int32_t)));
   return SIM_OK;
 }
@@ -711,6 +720,7 @@ int fetch_results(sim_t* s, const std::vector<int>& fin) {
       }
       d.rstep = std::move(rs[q]);
     }
+    d.induced = std::move(h.induced);
     s->st_events += 1;
     s->st_inter += d.interactions;
     out.push_back(std::move(d));
@@ -752,6 +762,15 @@ int pump(sim_t* s, bool defer, bool* progressed) {
     HostSlot& h = s->slots[k];
     if (!h.used || !h.running) continue;
     const SlotSummary& m = s->h_summary[k];
+    if (s->h_induced) {
+      // the steps this chunk executed for the slot, in order
+      const int K = s->opt.mode == CTS_MODE_PLAIN ? 1 : s->K;
+      const int64_t ran = std::min<int64_t>(std::max<int64_t>(m.n_steps - h.n_steps, 0), K);
+      for (int64_t kk = 0; kk < ran; ++kk) {
+        h.induced_q += s->h_induced[kk * s->S + k];
+        h.induced.push_back(h.induced_q);
+      }
+    }
     h.n_h = m.n_h;
     h.n_e = m.n_e;
     h.n_steps = m.n_steps;
@@ -807,6 +826,11 @@ void copy_out(const Done& d, sim_result_t* r, int grid_n) {
   }
   if (r->retire_step)
     for (int64_t c = 0; c < n; ++c) r->retire_step[c] = d.rstep.empty() ? -2 : d.rstep[c];
+  if (r->induced_e) {
+    const int64_t m = std::min<int64_t>(r->induced_capacity, (int64_t)d.induced.size());
+    for (int64_t k = 0; k < m; ++k) r->induced_e[k] = d.induced[(size_t)k];
+    for (int64_t k = m; k < r->induced_capacity; ++k) r->induced_e[k] = NAN;
+  }
 }
 
 void engine_main(sim_t* s) {
@@ -896,6 +920,7 @@ int alloc_all(sim_t* s) {
   AL(s->d_partial, s->partial_cap);
   AL(s->d_combine, kMaxUnits);
   AL(s->d_tiles_done, (int64_t)kMaxK * s->S);
+  if (s->opt.keep_induced) AL(s->d_induced, (int64_t)kMaxK * s->S);
   AL(s->d_err, 1);
   AL(s->d_explicit, C);
   AL(s->d_list, s->S);
@@ -908,6 +933,7 @@ int alloc_all(sim_t* s) {
   HL(s->h_readout, s->S);
   HL(s->h_pixels, (int64_t)s->S * s->sensor.grid_n * s->sensor.grid_n);
   HL(s->h_err, 1);
+  if (s->opt.keep_induced) HL(s->h_induced, (int64_t)kMaxK * s->S);
 #undef AL
 #undef HL
   CK(cudaMemset(s->d_slots, 0, s->S * sizeof(SlotDev)));
@@ -927,12 +953,12 @@ void free_all(sim_t* s) {
   void* dev[] = {s->A.px, s->A.py, s->A.pz, s->A.sh[0], s->A.sh[1], s->A.cid, s->A.fx, s->A.fy,
                  s->A.rstep, s->A.cstate, s->d_slots, s->d_summary, s->d_readout, s->d_pixels,
                  s->d_units, s->d_cta_begin, s->d_unit_counter, s->d_ret, s->d_partial,
-                 s->d_combine, s->d_tiles_done, s->d_err, s->d_field, s->d_explicit,
+                 s->d_combine, s->d_tiles_done, s->d_induced, s->d_err, s->d_field, s->d_explicit,
                  s->d_list, s->d_drift};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {s->h_summary, s->h_units, s->h_cta_begin, s->h_list, s->h_slotdev, s->h_readout,
-                  s->h_pixels, s->h_err};
+                  s->h_pixels, s->h_err, s->h_induced};
   for (void* p : host)
     if (p) cudaFreeHost(p);
   if (s->ev0) cudaEventDestroy(s->ev0);

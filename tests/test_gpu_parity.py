@@ -464,3 +464,29 @@ def test_sampled_drift_field_matches_the_oracle():
     for a, b in zip(two, plain):
         assert abs(a["n_steps"] - b["n_steps"]) <= 1
         assert np.abs(a["pixels"] - b["pixels"]).max() <= 1
+
+
+@pytest.mark.gpu
+def test_induced_charge_matches_the_oracle():
+    # the transient signal on the collecting surface, step by step
+    name = "plain_3keV_100um"
+    evs = W.make_events(name, n=4, first_id=120)
+    refs = oracle.run_events(oracle_params(name), evs)
+    outs = []
+    for mode in (cts.CTS_MODE_BATCHED, cts.CTS_MODE_PLAIN):
+        with sim_for(name, mode=mode, keep_induced=1) as sim:
+            outs.append(sim.run(evs, induced_capacity=4096))
+    for g, r in zip(outs[0], refs):
+        q, qr = g["induced"], r.induced
+        assert len(q) == g["n_steps"]
+        m = min(len(q), len(qr))
+        assert np.abs(q[:m] - qr[:m]).max() <= 1e-3 * g["n_carriers"]
+        # every hole collected: the total telescopes to sum(z0) / H on both sides
+        assert q[-1] == pytest.approx(qr[-1], rel=1e-9)
+    # PLAIN computes the field in a separate launch with its own summation
+    # order: the waveforms agree to FP32 rounding of the fields, the totals
+    # exactly
+    for a, b in zip(outs[0], outs[1]):
+        m = min(len(a["induced"]), len(b["induced"]))
+        assert np.allclose(a["induced"][:m], b["induced"][:m], rtol=1e-6, atol=1e-6)
+        assert a["induced"][-1] == pytest.approx(b["induced"][-1], rel=1e-9)
