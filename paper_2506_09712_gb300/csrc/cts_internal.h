@@ -151,7 +151,6 @@ struct StepArgs {
   double* partial;           // FP64 accumulators of split tiles (3 x tile_i each, kept zero)
   int32_t* combine_count;    // per i-block
   int32_t* tiles_done;       // [K][S]: tiles of each slot updated at each chunk step
-  double* induced;           // [K][S]: charge induced at each chunk step (e); NULL = off
   float* field_out;          // FIELD_ONLY output, SoA [3][capacity]
   int32_t* err;              // global error bits
   unsigned long long* trace; // optional: per CTA {smid, t_start, t_end, pairs, units,
@@ -159,6 +158,7 @@ struct StepArgs {
   Phys ph;
   int32_t S;                 // slot count
   int32_t fused;             // 1: update positions; 0: write field_out
+  double* induced;           // [K][S]: charge induced at each chunk step (e); NULL = off
 };
 
 // ---- kernel launchers (cts_kernels.cu) ----------------------------------

@@ -311,9 +311,11 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float t) {
 }
 
 // Position update of one carrier (Eqs. 3, 5, 6; Sec. 2.1) with the field E
-// (V/um) of its step, collection/exit and the next shadow entry.  Returns the
-// charge (units of e) the move induces on the collecting surface
-// (Shockley-Ramo, weighting potential 1 - z/H, the end point held on [0, H]).
+// (V/um) of its step, collection/exit and the next shadow entry.  When the
+// induced charge is recorded, returns H times the charge (units of e) the
+// move induces on the collecting surface (Shockley-Ramo, weighting potential
+// 1 - z/H, the end point held on [0, H]); else 0.
+template <bool IND = true>
 __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, int slot, int spec,
                                                int64_t idx, int step, int p, int k, float Ex,
                                                float Ey, float Ez, double azn) {
@@ -327,7 +329,7 @@ __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, 
     return 0.0;
   }
   double x = __ldcg(a.A.px + idx), y = __ldcg(a.A.py + idx), z = __ldcg(a.A.pz + idx);
-  const double z_start = z;
+  [[maybe_unused]] const double z_start = z;
   if (ph.drift) Ez -= drift_E(ph, (float)z);
   const float Em = sqrtf(Ex * Ex + Ey * Ey + Ez * Ez);
   const float mu = mobility_f(ph, spec, Em);
@@ -367,16 +369,22 @@ __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, 
   } else {
     shout[idx] = make_float4((float)(x - S->ax), (float)(y - S->ay), (float)(z - azn), 0.0f);
   }
-  const double zb = fmin(fmax(z, 0.0), ph.H);
-  return (spec ? zb - z_start : z_start - zb) / ph.H;
+  if constexpr (!IND) {
+    return 0.0;
+  } else {
+    if (!a.induced) return 0.0;
+    const double zb = fmin(fmax(z, 0.0), ph.H);
+    return spec ? zb - z_start : z_start - zb;
+  }
 }
 
-// Adds a warp's induced charges to the slot's per-step total (all 32 lanes
-// of the warp call this).
+// Adds a warp's induced charges (H times, from update_carrier) to the slot's
+// per-step total (all 32 lanes of the warp call this).
 __device__ __forceinline__ void add_induced(const StepArgs& a, int k, int slot, double q) {
   if (!a.induced) return;
   for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
-  if ((threadIdx.x & 31) == 0 && q != 0.0) atomicAdd(a.induced + (int64_t)k * a.S + slot, q);
+  if ((threadIdx.x & 31) == 0 && q != 0.0)
+    atomicAdd(a.induced + (int64_t)k * a.S + slot, q / a.ph.H);
 }
 
 // Per-slot duties of a step, done once per slot: interaction count, step
@@ -406,7 +414,9 @@ __device__ __forceinline__ void active_counts(const StepArgs& a, const SlotDev* 
 // ---------------------------------------------------------------------------
 // MODE 0: scalar FP32 pair loop; 1: packed over pairs of i's; 2: packed over
 // pairs of sources (struct-of-arrays copy of each chunk in shared memory).
-template <int NT, int R, int MODE, int JU, int MINB>
+// IND: the instantiation that records the induced charge (keep_induced); the
+// other one carries none of that code.
+template <int NT, int R, int MODE, int JU, int MINB, bool IND>
 __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int nk) {
   constexpr int TI = NT * R;
   static_assert(MODE != 1 || R % 2 == 0, "packed-i variants pair i's two by two");
@@ -751,15 +761,25 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
       const float kc = a.ph.f_kc;
       if (skip) {
       } else if (a.fused) {
-        double q = 0.0;
+        if constexpr (IND) {
+          double q = 0.0;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int li = r * NT + tid;
-          if (li < U.ni)
-            q += update_carrier(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
-                                kc * vy[r], kc * vz[r], s_azn[spec]);
+          for (int r = 0; r < R; ++r) {
+            const int li = r * NT + tid;
+            if (li < U.ni)
+              q += update_carrier(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
+                                  kc * vy[r], kc * vz[r], s_azn[spec]);
+          }
+          add_induced(a, k, U.slot, q);
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const int li = r * NT + tid;
+            if (li < U.ni)
+              update_carrier<false>(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
+                                    kc * vy[r], kc * vz[r], s_azn[spec]);
+          }
         }
-        add_induced(a, k, U.slot, q);
       } else {
         const int64_t cap = a.A.capacity;
 #pragma unroll
@@ -1473,6 +1493,7 @@ struct VariantEntry {
   const char* name;
   void (*fn)(StepArgs, int, int);
   int ctas_per_sm, dynamic, mode;
+  void (*fn_ind)(StepArgs, int, int);  // the same kernel recording the induced charge
 };
 
 // (threads, i's per thread, packed f32x2, j unroll, min CTAs per SM [register
@@ -1480,7 +1501,8 @@ struct VariantEntry {
 // the default: sources paired in packed FP32 lanes, 512-carrier tiles, guided
 // dynamic queue (fastest on the 64 x 20 keV batch).
 #define CTS_V(NT, R, MODE, JU, MB, CPS, DYN, NAME) \
-  {NT, R, NAME, step_kernel<NT, R, MODE, JU, MB>, CPS, DYN, MODE}
+  {NT, R, NAME, step_kernel<NT, R, MODE, JU, MB, false>, CPS, DYN, MODE, \
+   step_kernel<NT, R, MODE, JU, MB, true>}
 const VariantEntry kVariants[] = {
     CTS_V(256, 2, 2, 4, 3, 0, 1, "nt256_r2_jpair_dyn"),
     CTS_V(256, 4, 2, 4, 2, 0, 1, "nt256_r4_jpair_dyn"),
@@ -1516,12 +1538,15 @@ cudaError_t variant_occupancy(int v, int* blocks_per_sm) {
   cudaError_t err = cudaFuncSetAttribute(e.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem_of(e));
   if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(e.fn_ind, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_of(e));
+  if (err != cudaSuccess) return err;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.nt, smem_of(e));
 }
 
 cudaError_t launch_step(int v, const StepArgs& a, int k0, int nk, int grid, cudaStream_t s) {
   const VariantEntry& e = kVariants[v];
-  e.fn<<<grid, e.nt, smem_of(e), s>>>(a, k0, nk);
+  (a.induced ? e.fn_ind : e.fn)<<<grid, e.nt, smem_of(e), s>>>(a, k0, nk);
   return cudaGetLastError();
 }
 
