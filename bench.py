@@ -581,24 +581,14 @@ def run_ours(args, rank, world, local):
         try:
             rng = np.random.default_rng(1)
             n_gen = 200_000
-            gen = (cts.sim_gen_event_t * n_gen)()
-            for k in range(n_gen):
-                gen[k] = cts.sim_gen_event_t(W.MASTER_SEED, k, 5525, 0,
-                                             float(rng.uniform(-12.5, 12.5)),
-                                             float(rng.uniform(-12.5, 12.5)),
-                                             float(rng.uniform(3.0, 12.0)),
-                                             float(rng.uniform(2.0, 3.0)))
-            pix = np.zeros((n_gen, 9, 9), np.int32)
-            outs = np.zeros(n_gen, np.int64)
-            lib = cts.load()
-            def _gen():
-                return lib.sim_generate(gen, n_gen, 25.0, 9, local,
-                                        pix.ctypes.data_as(cts.C.POINTER(cts.C.c_int32)),
-                                        outs.ctypes.data_as(cts.C.POINTER(cts.C.c_int64)))
-            _gen()
+            gen = cts.gen_events(W.MASTER_SEED, np.arange(n_gen), 5525,
+                                 rng.uniform(-12.5, 12.5, n_gen), rng.uniform(-12.5, 12.5, n_gen),
+                                 rng.uniform(3.0, 12.0, n_gen), rng.uniform(2.0, 3.0, n_gen))
+            cts.sim_generate(gen[:1000], 25.0, 9, device=local)
             t0 = time.perf_counter()
-            rc = _gen()
+            pix, outs = cts.sim_generate(gen, 25.0, 9, device=local)
             dt = time.perf_counter() - t0
+            rc = 0
             line["generate"] = {"events": n_gen, "carriers_per_event": 5525, "rc": rc,
                                 "events_per_s": n_gen / dt,
                                 "samples_per_s": 2 * 5525 * n_gen / dt,

@@ -326,18 +326,39 @@ def cts_fano_pairs(seed, event_id, energy_keV, fano=0.13):
     return n.value
 
 
+# numpy record layout of sim_gen_event_t (56 bytes)
+GEN_EVENT_DTYPE = np.dtype([("seed", "<u8"), ("event_id", "<u8"), ("n_pairs", "<i4"),
+                            ("reserved", "<i4"), ("x_um", "<f8"), ("y_um", "<f8"),
+                            ("alpha", "<f8"), ("beta", "<f8")])
+
+
+def gen_events(seed, event_id, n_pairs, x_um, y_um, alpha, beta):
+    """A GEN_EVENT_DTYPE record array from per-event columns (or scalars)."""
+    cols = [np.asarray(c) for c in (seed, event_id, n_pairs, x_um, y_um, alpha, beta)]
+    n = max(c.size for c in cols)
+    rec = np.zeros(n, dtype=GEN_EVENT_DTYPE)
+    for name, c in zip(("seed", "event_id", "n_pairs", "x_um", "y_um", "alpha", "beta"), cols):
+        rec[name] = np.broadcast_to(c, (n,))
+    return rec
+
+
 def sim_generate(events, pitch_um, grid_n, device=0):
-    """Fast generation on the GPU from dicts with seed, event_id, n_pairs,
-    x_um, y_um, alpha, beta: pixel counts (n_ev x g x g) and off-grid counts."""
-    n = len(events)
-    arr = (sim_gen_event_t * max(n, 1))()
-    for k, e in enumerate(events):
-        arr[k] = sim_gen_event_t(int(e["seed"]), int(e["event_id"]), int(e["n_pairs"]), 0,
-                                 float(e["x_um"]), float(e["y_um"]), float(e["alpha"]),
-                                 float(e["beta"]))
+    """Fast generation on the GPU from a GEN_EVENT_DTYPE record array or dicts
+    with seed, event_id, n_pairs, x_um, y_um, alpha, beta: pixel counts
+    (n_ev x g x g) and off-grid counts."""
+    if isinstance(events, np.ndarray) and events.dtype == GEN_EVENT_DTYPE:
+        rec = np.ascontiguousarray(events)
+    else:
+        ev = list(events)
+        rec = gen_events(*[[e[k] for e in ev] for k in
+                           ("seed", "event_id", "n_pairs", "x_um", "y_um", "alpha", "beta")]) \
+            if ev else np.zeros(0, dtype=GEN_EVENT_DTYPE)
+    n = rec.size
     pix = np.zeros((n, grid_n, grid_n), np.int32)
     out = np.zeros(max(n, 1), np.int64)
-    _check(load().sim_generate(arr, n, float(pitch_um), int(grid_n), int(device),
+    buf = rec if n else np.zeros(1, dtype=GEN_EVENT_DTYPE)
+    _check(load().sim_generate(buf.ctypes.data_as(C.POINTER(sim_gen_event_t)), n,
+                               float(pitch_um), int(grid_n), int(device),
                                _ptr(pix, C.c_int32), _ptr(out, C.c_int64)), "sim_generate")
     return pix, out[:n]
 
