@@ -337,3 +337,26 @@ def test_bad_drift_tables_are_rejected(lib, table):
     with pytest.raises(cts.SimError) as e:
         cts.Simulator(dict(p["sensor"], drift_table_Vum=table), p["mobility"])
     assert e.value.code == cts.SIM_EINVAL
+
+
+def test_host_model_entry_points_reject_bad_input(lib):
+    import ctypes as C
+    import numpy as np
+    L = cts.load()
+    d = C.POINTER(C.c_double)
+    one = np.ones(3)
+    # too few points, null outputs
+    assert L.cts_fit_ggd(one.ctypes.data_as(d), 1, None, None) == -1
+    assert L.cts_fit_alpha_t(one.ctypes.data_as(d), one.ctypes.data_as(d), None, 3,
+                             np.zeros(4).ctypes.data_as(d)) == -1
+    assert L.cts_fit_beta_t(one.ctypes.data_as(d), one.ctypes.data_as(d), None, 3,
+                            np.zeros(5).ctypes.data_as(d)) == -1
+    # parameters that make alpha non-positive, and a negative drift time
+    with pytest.raises(ValueError):
+        cts.cts_ggd_params_at([-1.0, 0, 0, 0], [0, 0, 1, 0, 0], 1.0)
+    with pytest.raises(ValueError):
+        cts.cts_ggd_params_at([1.0, 0, 0, 0], [0, 0, 1, 0, 0], -1.0)
+    # the launch log needs a handle
+    n = C.c_int32(0)
+    assert L.sim_debug_launch_log(None, None, 0, C.byref(n)) == cts.SIM_EINVAL
+    assert L.sim_debug_fma_peak(-1, 1, None) == cts.SIM_EINVAL
