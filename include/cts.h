@@ -130,6 +130,9 @@ typedef struct sim_options_t {
                               next step starts as soon as all of its tiles are
                               updated, without a device-wide barrier */
   void* stream;            /* cudaStream_t to launch on; NULL = own stream */
+  const char* autotune_cache; /* file of a variant table (cts_host.h): loaded by
+                              sim_init when it matches this device and build,
+                              written by sim_autotune; NULL = none */
 } sim_options_t;
 
 /* One event (Algorithm 1 inputs: E, absorption depth h, plus the entry point).

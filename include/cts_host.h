@@ -58,6 +58,18 @@ double cts_estimate_steps(double thickness_um, double bias_V, double depletion_V
                           double mu0_cm2, double vsat_cms, double beta, double dt_ps,
                           double depth_um);
 
+/* Autotune cache (sim_options_t.autotune_cache): a text file holding a
+ * variant table (sim_set_variants) with the name of the device and the
+ * number of kernel variants it was measured against.  save returns 0, -1 for
+ * bad arguments, -3 if the file cannot be written.  load fills up to cap
+ * entries and *n; returns 0, -1 for bad arguments, -2 for a malformed file,
+ * -3 if it cannot be opened, -4 if it was measured on another device or
+ * library build (then *n = 0). */
+int cts_variant_table_save(const char* path, const char* device, int32_t n_variants,
+                           const int64_t* min_pairs, const int32_t* variants, int32_t n);
+int cts_variant_table_load(const char* path, const char* device, int32_t n_variants,
+                           int64_t* min_pairs, int32_t* variants, int32_t cap, int32_t* n);
+
 /* Carrier-pair count of one photon with Fano statistics (Sec. 4.2 applies a
  * Fano factor of 0.13 to the number of carriers): mean E / 3.62 eV, variance
  * fano times the mean, drawn as round(mean + sqrt(fano * mean) * g) with g the

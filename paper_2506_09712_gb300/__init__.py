@@ -52,7 +52,7 @@ class sim_options_t(C.Structure):
                 ("variant", C.c_int32), ("disable_graphs", C.c_int32),
                 ("keep_final_xy", C.c_int32), ("time_launches", C.c_int32),
                 ("keep_induced", C.c_int32), ("step_launches", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("autotune_cache", C.c_char_p)]
 
 
 class sim_readout_params_t(C.Structure):
@@ -114,6 +114,7 @@ EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_e
             "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_debug_launch_log",
             "sim_debug_fma_peak", "sim_readout", "cts_fano_pairs", "sim_generate",
             "cts_fit_ggd", "cts_fit_alpha_t", "cts_fit_beta_t", "cts_ggd_params_at",
+            "cts_variant_table_save", "cts_variant_table_load",
             "sim_set_variants",
             "sim_get_variants", "sim_autotune", "sim_reset", "cts_field_noalloc", "cts_plan_units", "cts_arena_replay",
             "cts_estimate_steps"]
@@ -172,6 +173,8 @@ def load(build_if_missing: bool = True):
         "cts_fit_alpha_t": [P(d), P(d), P(d), i32, P(d)],
         "cts_fit_beta_t": [P(d), P(d), P(d), i32, P(d)],
         "cts_ggd_params_at": [P(d), P(d), d, P(d), P(d)],
+        "cts_variant_table_save": [C.c_char_p, C.c_char_p, i32, P(i64), P(i32), i32],
+        "cts_variant_table_load": [C.c_char_p, C.c_char_p, i32, P(i64), P(i32), i32, P(i32)],
         "sim_set_variants": [C.c_void_p, P(i64), P(i32), i32],
         "sim_reset": [C.c_void_p],
         "sim_get_variants": [C.c_void_p, P(i64), P(i32), i32, P(i32)],
@@ -576,6 +579,8 @@ def make_options(mode=CTS_MODE_BATCHED, **kw) -> sim_options_t:
     o = sim_options_t()
     o.mode = mode
     for k, v in kw.items():
+        if k == "autotune_cache" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 

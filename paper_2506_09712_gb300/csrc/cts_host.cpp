@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
 #include <map>
 #include <vector>
 
@@ -469,6 +471,56 @@ int fit_beta_t(const double* t, const double* y, const double* sigma, int n, dou
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Variant-table cache file: "cts-variant-table 1", the device name, the
+// number of kernel variants the table was measured against, then one
+// "min_pairs variant" line per entry.
+// ---------------------------------------------------------------------------
+int table_save(const char* path, const char* device, int32_t n_variants, const int64_t* mins,
+               const int32_t* vars, int32_t n) {
+  if (!path || !device || n < 0 || (n > 0 && (!mins || !vars))) return -1;
+  FILE* f = std::fopen(path, "w");
+  if (!f) return -3;
+  bool ok = std::fprintf(f, "cts-variant-table 1\n%s\n%d %d\n", device, n_variants, n) > 0;
+  for (int32_t q = 0; q < n && ok; ++q)
+    ok = std::fprintf(f, "%lld %d\n", (long long)mins[q], vars[q]) > 0;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? 0 : -3;
+}
+
+int table_load(const char* path, const char* device, int32_t n_variants, int64_t* mins,
+               int32_t* vars, int32_t cap, int32_t* n) {
+  if (!path || !device || !n || cap < 0) return -1;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return -3;
+  char line[512];
+  int rc = 0;
+  int nv = 0, cnt = 0;
+  if (!std::fgets(line, sizeof line, f) || std::strcmp(line, "cts-variant-table 1\n") != 0) rc = -2;
+  if (!rc && !std::fgets(line, sizeof line, f)) rc = -2;
+  if (!rc) {
+    line[std::strcspn(line, "\n")] = 0;
+    if (std::strcmp(line, device) != 0) rc = -4;  // measured on another device
+  }
+  if (!rc && std::fscanf(f, "%d %d", &nv, &cnt) != 2) rc = -2;
+  if (!rc && (nv != n_variants || cnt < 0 || cnt > cap)) rc = nv != n_variants ? -4 : -2;
+  long long prev = -1;
+  for (int q = 0; !rc && q < cnt; ++q) {
+    long long m = 0;
+    int v = 0;
+    if (std::fscanf(f, "%lld %d", &m, &v) != 2 || m < 0 || m < prev || v < 1 || v > n_variants)
+      rc = -2;
+    else {
+      mins[q] = m;
+      vars[q] = v;
+      prev = m;
+    }
+  }
+  std::fclose(f);
+  *n = rc ? 0 : cnt;
+  return rc;
+}
+
 }  // namespace cts
 
 extern "C" {
@@ -540,6 +592,16 @@ int cts_ggd_params_at(const double* p_alpha, const double* p_beta, double t, dou
   *alpha = cts::alpha_of_t(p_alpha, t);
   *beta = cts::beta_of_t(p_beta, t);
   return (*alpha > 0.0 && *beta > 0.0) ? 0 : -2;
+}
+
+int cts_variant_table_save(const char* path, const char* device, int32_t n_variants,
+                           const int64_t* min_pairs, const int32_t* variants, int32_t n) {
+  return cts::table_save(path, device, n_variants, min_pairs, variants, n);
+}
+
+int cts_variant_table_load(const char* path, const char* device, int32_t n_variants,
+                           int64_t* min_pairs, int32_t* variants, int32_t cap, int32_t* n) {
+  return cts::table_load(path, device, n_variants, min_pairs, variants, cap, n);
 }
 
 double cts_estimate_steps(double thickness_um, double bias_V, double depletion_V, double mu0_cm2,

@@ -37,6 +37,12 @@ int fit_ggd(const double* x, int64_t n, double* alpha, double* beta);
 int fit_alpha_t(const double* t, const double* y, const double* w, int n, double* p);
 int fit_beta_t(const double* t, const double* y, const double* sigma, int n, double* p);
 
+// Variant-table cache file (see cts_variant_table_save / _load).
+int table_save(const char* path, const char* device, int32_t n_variants, const int64_t* mins,
+               const int32_t* vars, int32_t n);
+int table_load(const char* path, const char* device, int32_t n_variants, int64_t* mins,
+               int32_t* vars, int32_t cap, int32_t* n);
+
 class ArenaAllocator {
  public:
   explicit ArenaAllocator(int64_t capacity = 0);

@@ -158,6 +158,8 @@ struct sim_t {
   std::vector<int64_t> table_min;
   std::vector<int> table_var;
   int base_variant = 0;
+  std::string autotune_cache;  // copied from the options
+  std::string device_name;
 
   // stats
   int64_t st_events = 0, st_inter = 0, st_steps = 0, st_launch = 0, st_chunks = 0,
@@ -1085,6 +1087,24 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
   if (!rc) rc = set_variant(s, choose_variant(s));
   if (!rc && s->field.spherical && spherical_prepare() != cudaSuccess) rc = SIM_ECUDA;
   s->base_variant = s->variant;
+  {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, opt.device) == cudaSuccess) s->device_name = prop.name;
+  }
+  if (opt.autotune_cache) s->autotune_cache = opt.autotune_cache;
+  s->opt.autotune_cache = nullptr;  // the caller's string is not kept
+  if (!rc && !s->autotune_cache.empty()) {
+    // a cached table measured on this device and build, if there is one
+    std::vector<int64_t> mins(64);
+    std::vector<int32_t> vars(64);
+    int32_t n = 0;
+    if (table_load(s->autotune_cache.c_str(), s->device_name.c_str(), variant_count(),
+                   mins.data(), vars.data(), 64, &n) == 0 && n > 0) {
+      s->table_min.assign(mins.begin(), mins.begin() + n);
+      s->table_var.assign((size_t)n, 0);
+      for (int q = 0; q < n; ++q) s->table_var[q] = vars[q] - 1;
+    }
+  }
   if (rc) {
     free_all(s);
     delete s;
@@ -1659,6 +1679,9 @@ int sim_autotune(sim_t* s, const sim_event_t* ev, int32_t n, int32_t reps, int32
   }
   rc = sim_set_variants(s, mins.data(), vars.data(), (int32_t)mins.size());
   *n_buckets = (int32_t)mins.size();
+  if (!rc && !s->autotune_cache.empty())
+    table_save(s->autotune_cache.c_str(), s->device_name.c_str(), variant_count(), mins.data(),
+               vars.data(), (int32_t)mins.size());
   return rc;
 }
 

@@ -407,10 +407,12 @@ def test_every_kernel_variant_matches_the_oracle():
             _compare_events(sim.run(ev)[0], ref, 829)
 
 
-def test_autotuned_variant_table_runs_and_matches():
+def test_autotuned_variant_table_runs_and_matches(tmp_path):
     name = "plain_3keV_100um"
     evs = W.make_events(name)
-    with sim_for(name) as sim:
+    cache = str(tmp_path / "variants.txt")
+    with sim_for(name, autotune_cache=cache) as sim:
+        assert sim.variants() == []                 # no cache file yet
         table = sim.autotune(W.make_events(name, n=8, first_id=900), reps=2)
         assert len(table) >= 1 and table[0][0] == 0
         assert all(1 <= v <= len(_variants()) for _, v in table)
@@ -418,6 +420,9 @@ def test_autotuned_variant_table_runs_and_matches():
         res = sim.run(evs)
         sim.set_variants([])
         assert sim.variants() == []
+    # a new handle on the same device picks the measured table up from the file
+    with sim_for(name, autotune_cache=cache) as sim:
+        assert sim.variants() == table
     refs = oracle.run_events(oracle_params(name), evs)
     for g, r in zip(res, refs):
         _compare_events(g, r, 829)

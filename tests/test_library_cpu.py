@@ -360,3 +360,69 @@ def test_host_model_entry_points_reject_bad_input(lib):
     n = C.c_int32(0)
     assert L.sim_debug_launch_log(None, None, 0, C.byref(n)) == cts.SIM_EINVAL
     assert L.sim_debug_fma_peak(-1, 1, None) == cts.SIM_EINVAL
+
+
+def test_public_struct_layouts_match_the_binding(tmp_path):
+    # the ctypes mirrors of include/cts.h must agree field by field
+    import ctypes as C
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    structs = {"sim_sensor_t": cts.sim_sensor_t, "sim_field_t": cts.sim_field_t,
+               "sim_mobility_t": cts.sim_mobility_t, "sim_options_t": cts.sim_options_t,
+               "sim_event_t": cts.sim_event_t, "sim_result_t": cts.sim_result_t,
+               "sim_stats_t": cts.sim_stats_t, "sim_readout_params_t": cts.sim_readout_params_t,
+               "sim_cluster_t": cts.sim_cluster_t, "sim_gen_event_t": cts.sim_gen_event_t}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cts.h"', "int main(void) {"]
+    for name, py in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            parts = ln.split()
+            got[tuple(parts[:-1])] = int(parts[-1])
+    for name, py in structs.items():
+        assert got[(name, "size")] == C.sizeof(py), name
+        for f, _ in py._fields_:
+            assert got[(name, f)] == getattr(py, f).offset, (name, f)
+
+
+def test_autotune_cache_file_roundtrip(tmp_path):
+    import ctypes as C
+    import numpy as np
+    L = cts.load()
+    path = str(tmp_path / "table.txt").encode()
+    mins = np.array([0, 1000, 50000], dtype=np.int64)
+    vars_ = np.array([2, 1, 4], dtype=np.int32)
+    p64, p32 = C.POINTER(C.c_int64), C.POINTER(C.c_int32)
+    assert L.cts_variant_table_save(path, b"GPU X", 11, mins.ctypes.data_as(p64),
+                                    vars_.ctypes.data_as(p32), 3) == 0
+    m2, v2, n = np.zeros(8, np.int64), np.zeros(8, np.int32), C.c_int32(0)
+    assert L.cts_variant_table_load(path, b"GPU X", 11, m2.ctypes.data_as(p64),
+                                    v2.ctypes.data_as(p32), 8, C.byref(n)) == 0
+    assert n.value == 3 and np.array_equal(m2[:3], mins) and np.array_equal(v2[:3], vars_)
+    # another device or another set of variants: not used
+    assert L.cts_variant_table_load(path, b"GPU Y", 11, m2.ctypes.data_as(p64),
+                                    v2.ctypes.data_as(p32), 8, C.byref(n)) == -4 and n.value == 0
+    assert L.cts_variant_table_load(path, b"GPU X", 12, m2.ctypes.data_as(p64),
+                                    v2.ctypes.data_as(p32), 8, C.byref(n)) == -4
+    # too small a buffer, a missing file, a damaged file
+    assert L.cts_variant_table_load(path, b"GPU X", 11, m2.ctypes.data_as(p64),
+                                    v2.ctypes.data_as(p32), 2, C.byref(n)) == -2
+    assert L.cts_variant_table_load(str(tmp_path / "none").encode(), b"GPU X", 11,
+                                    m2.ctypes.data_as(p64), v2.ctypes.data_as(p32), 8,
+                                    C.byref(n)) == -3
+    bad = tmp_path / "bad.txt"
+    bad.write_text("cts-variant-table 1\nGPU X\n11 2\n0 3\n5 99\n")
+    assert L.cts_variant_table_load(str(bad).encode(), b"GPU X", 11, m2.ctypes.data_as(p64),
+                                    v2.ctypes.data_as(p32), 8, C.byref(n)) == -2
