@@ -63,7 +63,7 @@ def build(force: bool = False, extra: list[str] | None = None) -> str:
             objs = list(ex.map(lambda s: _compile(s, extra), SOURCES))
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.run([nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs,
-                        "-lpthread"], check=True, capture_output=True, text=True)
+                        "-lpthread", "-ldl"], check=True, capture_output=True, text=True)
     except subprocess.CalledProcessError as e:
         raise RuntimeError(f"libcts build failed:\n{' '.join(e.cmd)}\n{e.stdout}\n{e.stderr}") from e
     os.replace(tmp, LIB)

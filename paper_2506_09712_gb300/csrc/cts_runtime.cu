@@ -18,6 +18,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cts.h"
 #include "cts_host_impl.h"
 #include "cts_internal.h"
@@ -169,6 +171,13 @@ struct sim_t {
 };
 
 namespace {
+
+// An NVTX range for the scope (named phases in nsys / ncu timelines; inert
+// without a profiler attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define CK(call)                                                                   \
   do {                                                                             \
@@ -387,6 +396,7 @@ int place_event(sim_t* s, int slot, EventRec&& r, int64_t base) {
 
 // Admit queued events while slots and arena space allow (FIFO).
 int admit(sim_t* s) {
+  NvtxRange range("cts admit");
   std::lock_guard<std::mutex> lk(s->qmu);
   while (!s->queue.empty()) {
     if (count_used(s) >= running_limit(s)) break;
@@ -578,6 +588,7 @@ int issue_chunk(sim_t* s, int K, bool multi) {
 int set_variant(sim_t* s, int v);
 
 int run_chunk(sim_t* s) {
+  NvtxRange range("cts chunk");
   const bool plain = s->opt.mode == CTS_MODE_PLAIN;
   const int K = plain ? 1 : s->K;
   if (plain) {
@@ -671,6 +682,7 @@ int run_chunk(sim_t* s) {
 // Collect results of slots finished on the device (readout already binned).
 int fetch_results(sim_t* s, const std::vector<int>& fin) {
   if (fin.empty()) return SIM_OK;
+  NvtxRange range("cts readout");
   const int npix = s->sensor.grid_n * s->sensor.grid_n;
   const bool keep = s->opt.keep_final_xy != 0;
   std::vector<std::vector<double>> fx(fin.size()), fy(fin.size());
