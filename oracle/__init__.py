@@ -76,6 +76,7 @@ class _Result(C.Structure):
         ("pos_out", C.POINTER(C.c_double)), ("state_out", C.POINTER(C.c_int8)),
         ("sign_out", C.POINTER(C.c_int8)),
         ("induced", C.POINTER(C.c_double)), ("induced_capacity", C.c_int64),
+        ("induced_px", C.POINTER(C.c_double)),
     ]
 
 
@@ -120,6 +121,11 @@ def lib():
                                           P(i32), P(i32), P(d), P(i32)]
         _lib.or_readout_event.restype = C.c_int
         _lib.or_spectrum_add.argtypes = [P(d), i32, d, d, i32, P(i64)]
+        _lib.or_rect_solid_angle.argtypes = [d, d, d, d, d, d, d]
+        _lib.or_rect_solid_angle.restype = d
+        _lib.or_weighting_potential.argtypes = [d, d, d, d, d, d, d, d, i32]
+        _lib.or_weighting_potential.restype = d
+        _lib.or_window_potentials.argtypes = [P(_Params), d, d, d, P(d)]
     return _lib
 
 
@@ -416,13 +422,15 @@ class EventResult:
     state: np.ndarray
     sign: np.ndarray
     induced: np.ndarray = None    # charge on the collecting surface after each step (e)
+    induced_px: np.ndarray = None  # (steps, 3, 3): charge on the 3 x 3 centre pixels (e)
 
 
 INDUCED_CAPACITY = 20000   # steps of the induced-charge record the oracle keeps
 
 
-def _alloc_result(params, n):
-    bufs = dict(induced=np.zeros(int(min(params.max_steps, INDUCED_CAPACITY)) or 1),
+def _alloc_result(params, n, induced_px=False):
+    cap = int(min(params.max_steps, INDUCED_CAPACITY)) or 1
+    bufs = dict(induced=np.zeros(cap), induced_px=np.zeros(9 * cap) if induced_px else None,
                 pixels=np.zeros(params.grid_n * params.grid_n, dtype=np.int32),
                 fx=np.zeros(max(n, 1)), fy=np.zeros(max(n, 1)),
                 rs=np.zeros(max(n, 1), dtype=np.int32), pos=np.zeros(3 * max(n, 1)),
@@ -437,6 +445,7 @@ def _alloc_result(params, n):
     r.sign_out = _ptr(bufs["sg"], C.c_int8)
     r.induced = _ptr(bufs["induced"], C.c_double)
     r.induced_capacity = bufs["induced"].size
+    r.induced_px = _ptr(bufs["induced_px"], C.c_double)
     return r, bufs
 
 
@@ -448,11 +457,16 @@ def _wrap(params, r, bufs, n):
         final_xy=np.stack([bufs["fx"][:n], bufs["fy"][:n]], axis=1),
         retire_step=bufs["rs"][:n].copy(), pos=bufs["pos"][:3 * n].reshape(n, 3).copy(),
         state=bufs["st"][:n].copy(), sign=bufs["sg"][:n].copy(),
-        induced=bufs["induced"][:min(r.n_steps, bufs["induced"].size)].copy())
+        induced=bufs["induced"][:min(r.n_steps, bufs["induced"].size)].copy(),
+        induced_px=(None if bufs["induced_px"] is None else
+                    bufs["induced_px"].reshape(-1, 3, 3)[:min(r.n_steps, r.induced_capacity)]
+                    .copy()))
 
 
-def run_events(params: _Params, events: list[dict]) -> list[EventResult]:
-    """Run independent events (OpenMP across events when there are several)."""
+def run_events(params: _Params, events: list[dict], induced_px: bool = False) -> list[EventResult]:
+    """Run independent events (OpenMP across events when there are several).
+    induced_px: also record the charge induced on the 3 x 3 pixels around the
+    grid's centre pixel after every step (pixel weighting potentials)."""
     keep = []
     evs = (_Event * max(len(events), 1))()
     for k, ev in enumerate(events):
@@ -461,7 +475,7 @@ def run_events(params: _Params, events: list[dict]) -> list[EventResult]:
     sizes, bufl = [], []
     for k in range(len(events)):
         n = lib().or_event_carriers(C.byref(params), C.byref(evs[k]))
-        r, b = _alloc_result(params, n)
+        r, b = _alloc_result(params, n, induced_px)
         results[k] = r
         sizes.append(n); bufl.append(b)
     if len(events) == 1:
@@ -471,8 +485,32 @@ def run_events(params: _Params, events: list[dict]) -> list[EventResult]:
     return [_wrap(params, results[k], bufl[k], sizes[k]) for k in range(len(events))]
 
 
-def run_event(params: _Params, ev: dict) -> EventResult:
-    return run_events(params, [ev])[0]
+def run_event(params: _Params, ev: dict, induced_px: bool = False) -> EventResult:
+    return run_events(params, [ev], induced_px)[0]
+
+
+WEIGHT_PAIRS = 32   # image pairs the oracle sums before the two-term tail
+
+
+def rect_solid_angle(x, y, zeta, rect) -> float:
+    """Half-space potential (solid angle / 2 pi, signed like zeta) of the
+    rectangle rect = (x1, x2, y1, y2) on the plane zeta = 0 seen from (x, y, zeta)."""
+    return lib().or_rect_solid_angle(float(x), float(y), float(zeta), *map(float, rect))
+
+
+def weighting_potential(x, y, z, rect, thickness_um, n_pairs: int = WEIGHT_PAIRS) -> float:
+    """Weighting potential of the pixel rect = (x1, x2, y1, y2) on the
+    collecting surface z = 0 of a sensor of thickness H, at (x, y, z)."""
+    return lib().or_weighting_potential(float(x), float(y), float(z), *map(float, rect),
+                                        float(thickness_um), int(n_pairs))
+
+
+def window_potentials(params: _Params, x, y, z) -> np.ndarray:
+    """Weighting potentials (3 x 3, [row][col]) of the pixels around the grid's
+    centre pixel at (x, y, z), as the transport run records them."""
+    out = np.zeros(9)
+    lib().or_window_potentials(C.byref(params), float(x), float(y), float(z), _ptr(out, C.c_double))
+    return out.reshape(3, 3)
 
 
 def max_threads() -> int:

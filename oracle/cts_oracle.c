@@ -21,8 +21,10 @@
  *   -E(z) e_z with E(z) = (Vb - Vd)/H + 2 Vd (H - z)/H^2.
  *
  * Parity status: pinned (closed forms, invariants, a library Philox, exact
- * small configurations, hand-built readout maps and the statistics of the
- * Fano and noise draws) -- see tests/test_oracle_*.py.  The paper's own
+ * small configurations, hand-built readout maps, the statistics of the Fano
+ * and noise draws, and for the pixel weighting potential the Fourier-integral
+ * solution, quadrature of the Poisson kernel and the sum over all pixels) --
+ * see tests/test_oracle_*.py.  The paper's own
  * printed physics numbers (Table 1, GGD betas) depend on unprinted mobility
  * parameters and are checked only qualitatively.
  */
@@ -99,6 +101,9 @@ typedef struct {
   double* induced;      /* optional: charge induced on the collecting surface
                            after each step, in units of e */
   int64_t induced_capacity;
+  double* induced_px;   /* optional: 9 * induced_capacity, the charge induced on
+                           the 3 x 3 pixels around the grid's centre pixel after
+                           each step, [step][row-major 3 x 3] */
 } or_result_t;
 
 /* ------------------------------------------------------------------------ */
@@ -411,6 +416,95 @@ static void or_boundaries(const or_params_t* P, int64_t n, double* x, double* y,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Pixel weighting potential (Shockley-Ramo; the weighting field that the    */
+/* paper names as the extension towards transient signals, Sec. 5.3).       */
+/* The weighting potential phi of a pixel solves Laplace's equation in the   */
+/* sensor slab 0 < z < H with phi = 1 on the pixel's rectangle of the        */
+/* collecting surface z = 0, phi = 0 on the rest of that surface and on the  */
+/* back surface z = H (pixels tile the surface; no gaps).                    */
+/*                                                                           */
+/* Half space: the Dirichlet Poisson kernel zeta / (2 pi r^3) integrated     */
+/* over a rectangle is the solid angle / 2 pi; for the corner offsets        */
+/* u = X - x, v = Y - y it is the signed sum over the four corners of        */
+/*   F(u, v, zeta) = atan(u v / (zeta sqrt(u^2 + v^2 + zeta^2))) / (2 pi),   */
+/* an odd function of zeta (zeta -> 0+: 1 inside, 0 outside).                */
+/* Slab: images at z + 2 n H (n over all integers) make phi vanish on z = H; */
+/* the series converges when the terms n and -n are taken together, and a    */
+/* pair n behaves for large n like                                           */
+/*   -A z / (4 pi H^3 n^3) + A z (3 <r^2> - 2 z^2) / (16 pi H^5 n^5),        */
+/* A the pixel's area and <r^2> the mean square lateral distance from the    */
+/* point to the pixel's area.  The oracle sums the pairs up to n = 32 and   */
+/* the rest by these two terms (zeta(3) and zeta(5) less the partial sums);  */
+/* the next term is of order A z r^4 / (H^7 n^7): below 1e-10 for points     */
+/* over the pixel grids used here.                                           */
+/* ------------------------------------------------------------------------ */
+#define OR_WEIGHT_PAIRS 32
+static const double OR_ZETA3 = 1.2020569031595942854;
+static const double OR_ZETA5 = 1.0369277551433699263;
+
+static double or_corner(double u, double v, double zeta) {
+  double r = sqrt(u * u + v * v + zeta * zeta);
+  if (zeta == 0.0) {  /* the limit zeta -> 0+ */
+    double uv = u * v;
+    return uv > 0.0 ? 0.25 : (uv < 0.0 ? -0.25 : 0.0);
+  }
+  return atan(u * v / (zeta * r)) / (2.0 * OR_PI);
+}
+
+/* Half-space potential of the rectangle [x1, x2] x [y1, y2] at height zeta. */
+double or_rect_solid_angle(double x, double y, double zeta, double x1, double x2,
+                           double y1, double y2) {
+  return or_corner(x2 - x, y2 - y, zeta) - or_corner(x1 - x, y2 - y, zeta) -
+         or_corner(x2 - x, y1 - y, zeta) + or_corner(x1 - x, y1 - y, zeta);
+}
+
+/* Weighting potential of the pixel [x1, x2) x [y1, y2) at (x, y, z) of a
+ * sensor of thickness H (n_pairs image pairs, then the two-term tail). */
+double or_weighting_potential(double x, double y, double z, double x1, double x2,
+                              double y1, double y2, double H, int32_t n_pairs) {
+  if (z >= H) return 0.0;
+  if (z <= 0.0) return (x >= x1 && x < x2 && y >= y1 && y < y2) ? 1.0 : 0.0;
+  double phi = or_rect_solid_angle(x, y, z, x1, x2, y1, y2);
+  double s3 = OR_ZETA3, s5 = OR_ZETA5;
+  for (int32_t n = 1; n <= n_pairs; ++n) {
+    phi += or_rect_solid_angle(x, y, z + 2.0 * n * H, x1, x2, y1, y2);
+    phi += or_rect_solid_angle(x, y, z - 2.0 * n * H, x1, x2, y1, y2);
+    s3 -= 1.0 / ((double)n * n * n);
+    s5 -= 1.0 / ((double)n * n * n * n * n);
+  }
+  double a = x2 - x1, b = y2 - y1, A = a * b;
+  double cx = 0.5 * (x1 + x2) - x, cy = 0.5 * (y1 + y2) - y;
+  double r2 = cx * cx + cy * cy + (a * a + b * b) / 12.0;
+  phi += -A * z / (4.0 * OR_PI * H * H * H) * s3 +
+         A * z * (3.0 * r2 - 2.0 * z * z) / (16.0 * OR_PI * pow(H, 5.0)) * s5;
+  return phi;
+}
+
+/* The 3 x 3 pixels around the grid's centre pixel (grid_n / 2, grid_n / 2),
+ * row-major [b][a] for the grid pixel (c - 1 + a, c - 1 + b).  On the
+ * collecting surface (z <= 0) a pixel's potential is 1 exactly when the point
+ * is read out in it (the readout's own pixel rule), on the back surface 0. */
+void or_window_potentials(const or_params_t* P, double x, double y, double z,
+                          double phi[9]) {
+  int32_t c = P->grid_n / 2;
+  double p = P->pitch_um, half = 0.5 * (double)P->grid_n;
+  for (int k = 0; k < 9; ++k) phi[k] = 0.0;
+  if (z >= P->thickness_um) return;
+  if (z <= 0.0) {
+    int32_t ix, iy;
+    if (or_pixel_of(P, x, y, &ix, &iy) && abs(ix - c) <= 1 && abs(iy - c) <= 1)
+      phi[(iy - c + 1) * 3 + (ix - c + 1)] = 1.0;
+    return;
+  }
+  for (int b = 0; b < 3; ++b)
+    for (int a = 0; a < 3; ++a) {
+      double x1 = ((double)(c - 1 + a) - half) * p, y1 = ((double)(c - 1 + b) - half) * p;
+      phi[b * 3 + a] = or_weighting_potential(x, y, z, x1, x1 + p, y1, y1 + p,
+                                              P->thickness_um, OR_WEIGHT_PAIRS);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One event, Algorithm 1: repeat {repulsion field of every carrier from the */
 /* positions at the start of the step; drift field Eq. 6; mobility from     */
 /* |E_drift + E_repulsion|; D = mu kT/e; x, y by Eq. 3 and z by Eq. 5 with  */
@@ -451,6 +545,15 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
   or_init_event(P, ev, x, y, z, sign);
   for (int64_t c = 0; c < n; ++c) state[c] = OR_ACTIVE;
   or_boundaries(P, n, x, y, z, sign, state, -1, R);
+
+  double* ox = NULL;  /* step-start positions, for the pixel signals */
+  double* oy = NULL;
+  double induced_px[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  if (R->induced_px) {
+    ox = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    oy = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int64_t k = 0; k < 9 * R->induced_capacity; ++k) R->induced_px[k] = NAN;
+  }
 
   int64_t step = 0;
   double induced_q = 0.0;
@@ -498,6 +601,7 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
     for (int64_t r = 0; r < n_act; ++r) {
       int64_t c = rows[r];
       ez[r] = z[c];  /* the depth before the move, for the induced charge */
+      if (ox) { ox[r] = x[c]; oy[r] = y[c]; }
       x[c] = nx[r]; y[c] = ny[r]; z[c] = nz[r];
     }
     or_boundaries(P, n, x, y, z, sign, state, step, R);
@@ -510,6 +614,25 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
       induced_q += (double)sign[c] * (ez[r] - zb) / P->thickness_um;
     }
     if (R->induced && step < R->induced_capacity) R->induced[step] = induced_q;
+    /* The same theorem per pixel: q (phi_p(end) - phi_p(start)) with each
+     * pixel's weighting potential (end point held on [0, H]). */
+    if (R->induced_px) {
+      double* d = (double*)malloc(sizeof(double) * 9 * (size_t)(n_act > 0 ? n_act : 1));
+#pragma omp parallel for schedule(static) if (parallel)
+      for (int64_t r = 0; r < n_act; ++r) {
+        int64_t c = rows[r];
+        double zb = z[c] < 0.0 ? 0.0 : (z[c] > P->thickness_um ? P->thickness_um : z[c]);
+        double pa[9], pb[9];
+        or_window_potentials(P, ox[r], oy[r], ez[r], pa);
+        or_window_potentials(P, x[c], y[c], zb, pb);
+        for (int k = 0; k < 9; ++k) d[9 * r + k] = (double)sign[c] * (pb[k] - pa[k]);
+      }
+      for (int64_t r = 0; r < n_act; ++r)
+        for (int k = 0; k < 9; ++k) induced_px[k] += d[9 * r + k];
+      free(d);
+      if (step < R->induced_capacity)
+        for (int k = 0; k < 9; ++k) R->induced_px[9 * step + k] = induced_px[k];
+    }
   }
   R->n_steps = step;
 
@@ -541,6 +664,7 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
   free(x); free(y); free(z); free(ex); free(ey); free(ez);
   free(nx); free(ny); free(nz);
   free(rows); free(sign); free(state);
+  free(ox); free(oy);
   return R->status;
 }
 
