@@ -112,6 +112,11 @@ typedef struct sim_mobility_t {
 } sim_mobility_t;
 
 /* Execution options.  Zero fields select defaults. */
+/* options.keep_induced flags (may be combined). */
+#define SIM_INDUCED_TOTAL 1  /* the whole collecting surface (sim_result_t.induced_e) */
+#define SIM_INDUCED_PIXELS 2 /* the 3 x 3 pixels around the grid's centre pixel
+                                (sim_result_t.induced_px); needs grid_n >= 3 */
+
 typedef struct sim_options_t {
   int32_t mode;            /* CTS_MODE_* */
   int32_t device;          /* CUDA device ordinal */
@@ -124,7 +129,8 @@ typedef struct sim_options_t {
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
   int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */
   int32_t time_launches;   /* 1 = time every step-kernel launch with CUDA events */
-  int32_t keep_induced;    /* 1 = record the induced charge per step (sim_result_t) */
+  int32_t keep_induced;    /* SIM_INDUCED_* flags: record the induced charge per
+                              step (sim_result_t); 0 = off */
   int32_t step_launches;   /* 1 = one step-kernel launch per step; 0 = one launch
                               per chunk with dynamic-queue variants: a slot's
                               next step starts as soon as all of its tiles are
@@ -176,15 +182,24 @@ typedef struct sim_result_t {
   double* final_xy;      /* 2 * capacity */
   int32_t* retire_step;  /* capacity */
   int64_t capacity;      /* entries available in final_xy / retire_step */
-  /* Transient signal (options.keep_induced): the charge (units of e) induced
-   * on the whole collecting surface after each executed step, by the
-   * Shockley-Ramo theorem with the planar weighting potential 1 - z/H (a
-   * carrier of charge q moving from z_a to z_b adds q (z_a - z_b) / H;
-   * carriers that leave stop at the surface).  The paper names the weighting
-   * field as an extension (Sec. 5.3); pixel weighting fields are not modelled.
-   * Entries beyond n_steps are NaN; NULL skips. */
+  /* Transient signal (options.keep_induced & SIM_INDUCED_TOTAL): the charge
+   * (units of e) induced on the whole collecting surface after each executed
+   * step, by the Shockley-Ramo theorem with the planar weighting potential
+   * 1 - z/H (a carrier of charge q moving from z_a to z_b adds
+   * q (z_a - z_b) / H; carriers that leave stop at the surface).  The paper
+   * names the weighting field as the extension towards transient signals
+   * (Sec. 5.3).  Entries beyond n_steps are NaN; NULL skips. */
   double* induced_e;
-  int64_t induced_capacity;
+  int64_t induced_capacity;  /* steps available in induced_e and induced_px */
+  /* Per-pixel transient signals (options.keep_induced & SIM_INDUCED_PIXELS):
+   * 9 * induced_capacity doubles, [step][b][a], the charge induced on grid
+   * pixel (c - 1 + a, c - 1 + b), c = grid_n / 2, after each executed step:
+   * q (phi(end) - phi(start)) summed over moves, phi the pixel's weighting
+   * potential in the planar sensor (Laplace's equation, 1 on the pixel and 0
+   * on the rest of the collecting surface and on the back surface, pixels
+   * tiling the surface).  A collected carrier ends with phi = 1 on the pixel
+   * that reads it out, an exited one with 0.  NaN beyond n_steps; NULL skips. */
+  double* induced_px;
 } sim_result_t;
 
 typedef struct sim_stats_t {

@@ -23,6 +23,7 @@ CTS_HOLES, CTS_BOTH = 1, 3
 CTS_MOB_CT, CTS_MOB_CONST = 0, 1
 CTS_PHOTON, CTS_TRACK, CTS_EXPLICIT = 0, 1, 2
 CTS_MODE_PLAIN, CTS_MODE_BATCHED, CTS_MODE_SERVE = 0, 1, 2
+SIM_INDUCED_TOTAL, SIM_INDUCED_PIXELS = 1, 2   # options.keep_induced flags
 
 
 class sim_sensor_t(C.Structure):
@@ -90,7 +91,7 @@ class sim_result_t(C.Structure):
                 ("t_done_ns", C.c_double), ("pixels", C.POINTER(C.c_int32)),
                 ("final_xy", C.POINTER(C.c_double)), ("retire_step", C.POINTER(C.c_int32)),
                 ("capacity", C.c_int64), ("induced_e", C.POINTER(C.c_double)),
-                ("induced_capacity", C.c_int64)]
+                ("induced_capacity", C.c_int64), ("induced_px", C.POINTER(C.c_double))]
 
 
 class sim_stats_t(C.Structure):
@@ -613,10 +614,14 @@ def make_events(events: list[dict]):
 class Results:
     """Caller-owned result buffers for n events."""
 
-    def __init__(self, n: int, grid_n: int, capacity: int = 0, induced_capacity: int = 0):
+    def __init__(self, n: int, grid_n: int, capacity: int = 0, induced_capacity: int = 0,
+                 induced_px: bool = False):
         self.n, self.grid_n, self.capacity = n, grid_n, capacity
         self.induced_capacity = induced_capacity
+        self.has_px = bool(induced_px and induced_capacity)
         self.induced = np.zeros((max(n, 1), max(induced_capacity, 1)), dtype=np.float64)
+        self.induced_px = (np.zeros((max(n, 1), induced_capacity, 3, 3), dtype=np.float64)
+                           if self.has_px else None)
         self.pixels = np.zeros((max(n, 1), grid_n, grid_n), dtype=np.int32)
         self.final_xy = np.zeros((max(n, 1), max(capacity, 1), 2), dtype=np.float64)
         self.retire_step = np.zeros((max(n, 1), max(capacity, 1)), dtype=np.int32)
@@ -631,6 +636,8 @@ class Results:
             if induced_capacity:
                 r.induced_e = _ptr(self.induced[k], C.c_double)
                 r.induced_capacity = induced_capacity
+            if self.has_px:
+                r.induced_px = _ptr(self.induced_px[k], C.c_double)
 
     def record(self, k: int) -> dict:
         r = self.arr[k]
@@ -642,7 +649,9 @@ class Results:
                     final_xy=self.final_xy[k, :r.n_carriers].copy() if self.capacity else None,
                     retire_step=self.retire_step[k, :r.n_carriers].copy() if self.capacity else None,
                     induced=(self.induced[k, :min(r.n_steps, self.induced_capacity)].copy()
-                             if self.induced_capacity else None))
+                             if self.induced_capacity else None),
+                    induced_px=(self.induced_px[k, :min(r.n_steps, self.induced_capacity)].copy()
+                                if self.has_px else None))
 
 
 class Simulator:
@@ -656,6 +665,7 @@ class Simulator:
         self._field = make_field(field)
         self._mob = make_mobility(mobility)
         self._opt = make_options(mode, **options)
+        self._px = bool(self._opt.keep_induced & SIM_INDUCED_PIXELS)
         rc, self.h = sim_init(self._sensor, self._field, self._mob, self._opt)
         _check(rc, "sim_init")
 
@@ -679,7 +689,7 @@ class Simulator:
     def run(self, events: list[dict], keep_xy_capacity: int = 0,
             induced_capacity: int = 0) -> list[dict]:
         evs = make_events(events)
-        res = Results(len(events), self.grid_n, keep_xy_capacity, induced_capacity)
+        res = Results(len(events), self.grid_n, keep_xy_capacity, induced_capacity, self._px)
         _check(sim_run(self.h, evs, len(events), res.arr), "sim_run")
         return [res.record(k) for k in range(len(events))]
 
@@ -691,7 +701,7 @@ class Simulator:
         _check(sim_execute(self.h), "sim_execute")
 
     def collect(self, n: int, keep_xy_capacity: int = 0, induced_capacity: int = 0) -> list[dict]:
-        res = Results(n, self.grid_n, keep_xy_capacity, induced_capacity)
+        res = Results(n, self.grid_n, keep_xy_capacity, induced_capacity, self._px)
         rc, got = sim_collect(self.h, res.arr, n)
         _check(rc, "sim_collect")
         return [res.record(k) for k in range(got)]
@@ -702,7 +712,7 @@ class Simulator:
 
     def poll(self, max_out: int, timeout_ms: int, keep_xy_capacity: int = 0,
              induced_capacity: int = 0) -> list[dict]:
-        res = Results(max_out, self.grid_n, keep_xy_capacity, induced_capacity)
+        res = Results(max_out, self.grid_n, keep_xy_capacity, induced_capacity, self._px)
         rc, n = sim_poll(self.h, res.arr, max_out, timeout_ms)
         if rc == SIM_ETIMEOUT:
             return []

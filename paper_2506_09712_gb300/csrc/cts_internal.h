@@ -54,6 +54,12 @@ struct Phys {
   const float* drift_tab;
   int32_t drift_n;
   float f_drift_inv_dz;
+  // pixel weighting potentials of the 3 x 3 window around the centre pixel:
+  // the window's lower-left corner, the image pairs summed term by term and
+  // the coefficients of the remaining pairs' expansion in 1/n
+  double wp_x0, wp_y0;
+  float wp_c3, wp_c5;
+  int32_t wp_pairs;
 };
 
 // Per-slot state, resident in device memory.
@@ -159,6 +165,7 @@ struct StepArgs {
   int32_t S;                 // slot count
   int32_t fused;             // 1: update positions; 0: write field_out
   double* induced;           // [K][S]: charge induced at each chunk step (e); NULL = off
+  double* induced_px;        // [K][S][9]: the same per pixel of the 3 x 3 window; NULL = off
 };
 
 // ---- kernel launchers (cts_kernels.cu) ----------------------------------

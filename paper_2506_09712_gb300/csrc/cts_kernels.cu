@@ -310,15 +310,101 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float t) {
   s = u;
 }
 
+// The readout's pixel of a collected carrier: floor(x / pitch + n/2) per axis
+// in FP64 (row-major key), -1 outside the grid.
+__device__ __forceinline__ int pixel_at(double pitch, int grid_n, double x, double y) {
+  const double half = 0.5 * (double)grid_n;
+  const double fx = floor(__dadd_rn(__ddiv_rn(x, pitch), half));
+  const double fy = floor(__dadd_rn(__ddiv_rn(y, pitch), half));
+  if (!(fx >= 0.0 && fy >= 0.0 && fx < (double)grid_n && fy < (double)grid_n)) return -1;
+  return (int)fy * grid_n + (int)fx;
+}
+
+__device__ __forceinline__ int pixel_key(const Phys& ph, double x, double y) {
+  return pixel_at(ph.pitch, ph.grid_n, x, y);
+}
+
+// Weighting potentials (Shockley-Ramo) of the 3 x 3 pixels around the grid's
+// centre pixel c = grid_n / 2 at (x, y, z), z on [0, H]; w[b * 3 + a] is grid
+// pixel (c - 1 + a, c - 1 + b).  A pixel's potential solves Laplace's
+// equation in the slab with 1 on the pixel and 0 on the rest of both
+// surfaces.  Half space: the solid angle of the pixel / 2 pi, the signed sum
+// over its corners (offsets u, v) of F = sign(zeta) atan2(u v, |zeta| r) / 2 pi,
+// r = |(u, v, zeta)|; slab: images at z + 2 n H, n = -M..M (a corner shared by
+// neighbouring pixels is evaluated once), the pairs beyond M by their
+// expansion z (c3 + c5 (3 <r^2> - 2 z^2)), <r^2> the mean square lateral
+// distance to the pixel's area.  On the collecting surface a pixel's
+// potential is 1 where the readout puts the point, on the back surface 0.
+// FP32 (the offsets from FP64 positions).  Not inlined: every position goes
+// through the same code, so a carrier's potential at the end of a step equals
+// the one at the start of the next bit for bit and the signals telescope.
+__device__ __noinline__ void window_potentials(double x, double y, double z, double wx0,
+                                               double wy0, double pitch, int grid_n, double H,
+                                               int M, float c3, float c5, float* w) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) w[k] = 0.0f;
+  if (z >= H) return;
+  if (z <= 0.0) {
+    const int key = pixel_at(pitch, grid_n, x, y);
+    if (key < 0) return;
+    const int c = grid_n / 2;
+    const int a = key % grid_n - c + 1, b = key / grid_n - c + 1;
+    if (a >= 0 && a < 3 && b >= 0 && b < 3) w[b * 3 + a] = 1.0f;
+    return;
+  }
+  float u[4], v[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    u[i] = (float)(wx0 + (double)i * pitch - x);
+    v[i] = (float)(wy0 + (double)i * pitch - y);
+  }
+  float acc[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc[k] = 0.0f;
+  const float zf = (float)z, h2 = (float)(2.0 * H);
+  for (int n = -M; n <= M; ++n) {
+    const float zeta = fmaf((float)n, h2, zf);
+    const float az = fabsf(zeta), sg = zeta < 0.0f ? -1.0f : 1.0f, z2 = zeta * zeta;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float r = sqrtf(fmaf(u[i], u[i], fmaf(v[j], v[j], z2)));
+        const float f = sg * atan2f(u[i] * v[j], az * r);
+        // corner (i, j) is the upper-right corner of pixel (i-1, j-1), the
+        // upper-left of (i, j-1), the lower-right of (i-1, j), the lower-left of (i, j)
+        if (i >= 1 && j >= 1) acc[(j - 1) * 3 + (i - 1)] += f;
+        if (i <= 2 && j >= 1) acc[(j - 1) * 3 + i] -= f;
+        if (i >= 1 && j <= 2) acc[j * 3 + (i - 1)] -= f;
+        if (i <= 2 && j <= 2) acc[j * 3 + i] += f;
+      }
+    }
+  }
+  const float inv2pi = 0.159154943091895336f, q2 = (float)(pitch * pitch / 6.0);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float cx = (float)(wx0 + ((double)a + 0.5) * pitch - x);
+      const float cy = (float)(wy0 + ((double)b + 0.5) * pitch - y);
+      const float r2 = fmaf(cx, cx, fmaf(cy, cy, q2));
+      w[b * 3 + a] = fmaf(acc[b * 3 + a], inv2pi, zf * fmaf(c5, fmaf(3.0f, r2, -2.0f * zf * zf), c3));
+    }
+  }
+}
+
 // Position update of one carrier (Eqs. 3, 5, 6; Sec. 2.1) with the field E
 // (V/um) of its step, collection/exit and the next shadow entry.  When the
 // induced charge is recorded, returns H times the charge (units of e) the
 // move induces on the collecting surface (Shockley-Ramo, weighting potential
-// 1 - z/H, the end point held on [0, H]); else 0.
-template <bool IND = true>
+// 1 - z/H, the end point held on [0, H]); else 0.  IND: 0 records nothing,
+// 1 the whole surface, 2 also adds q (phi(end) - phi(start)) of the 3 x 3
+// window's pixels to qpx.
+template <int IND>
 __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, int slot, int spec,
                                                int64_t idx, int step, int p, int k, float Ex,
-                                               float Ey, float Ez, double azn) {
+                                               float Ey, float Ez, double azn,
+                                               double* qpx = nullptr) {
   const Phys& ph = a.ph;
   float4* __restrict__ shout = a.A.sh[p ^ 1];
   const int id = a.A.cid[idx];
@@ -329,7 +415,7 @@ __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, 
     return 0.0;
   }
   double x = __ldcg(a.A.px + idx), y = __ldcg(a.A.py + idx), z = __ldcg(a.A.pz + idx);
-  [[maybe_unused]] const double z_start = z;
+  [[maybe_unused]] const double x_start = x, y_start = y, z_start = z;
   if (ph.drift) Ez -= drift_E(ph, (float)z);
   const float Em = sqrtf(Ex * Ex + Ey * Ey + Ez * Ez);
   const float mu = mobility_f(ph, spec, Em);
@@ -369,11 +455,21 @@ __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, 
   } else {
     shout[idx] = make_float4((float)(x - S->ax), (float)(y - S->ay), (float)(z - azn), 0.0f);
   }
-  if constexpr (!IND) {
+  if constexpr (IND == 0) {
     return 0.0;
   } else {
-    if (!a.induced) return 0.0;
     const double zb = fmin(fmax(z, 0.0), ph.H);
+    if constexpr (IND == 2) {
+      float w0[9], w1[9];
+      window_potentials(x_start, y_start, z_start, ph.wp_x0, ph.wp_y0, ph.pitch, ph.grid_n, ph.H,
+                        ph.wp_pairs, ph.wp_c3, ph.wp_c5, w0);
+      window_potentials(x, y, zb, ph.wp_x0, ph.wp_y0, ph.pitch, ph.grid_n, ph.H, ph.wp_pairs,
+                        ph.wp_c3, ph.wp_c5, w1);
+#pragma unroll
+      for (int j = 0; j < 9; ++j)
+        qpx[j] += spec ? (double)w0[j] - (double)w1[j] : (double)w1[j] - (double)w0[j];
+    }
+    if (!a.induced) return 0.0;
     return spec ? zb - z_start : z_start - zb;
   }
 }
@@ -385,6 +481,20 @@ __device__ __forceinline__ void add_induced(const StepArgs& a, int k, int slot, 
   for (int o = 16; o > 0; o >>= 1) q += __shfl_down_sync(0xffffffffu, q, o);
   if ((threadIdx.x & 31) == 0 && q != 0.0)
     atomicAdd(a.induced + (int64_t)k * a.S + slot, q / a.ph.H);
+}
+
+// Adds a warp's per-pixel induced charges (from update_carrier) to the slot's
+// per-step record of the 3 x 3 window (all 32 lanes of the warp call this).
+__device__ __forceinline__ void add_induced_px(const StepArgs& a, int k, int slot,
+                                               const double (&q)[9]) {
+  if (!a.induced_px) return;
+  double* out = a.induced_px + ((int64_t)k * a.S + slot) * 9;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    double v = q[j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(out + j, v);
+  }
 }
 
 // Per-slot duties of a step, done once per slot: interaction count, step
@@ -414,9 +524,9 @@ __device__ __forceinline__ void active_counts(const StepArgs& a, const SlotDev* 
 // ---------------------------------------------------------------------------
 // MODE 0: scalar FP32 pair loop; 1: packed over pairs of i's; 2: packed over
 // pairs of sources (struct-of-arrays copy of each chunk in shared memory).
-// IND: the instantiation that records the induced charge (keep_induced); the
-// other one carries none of that code.
-template <int NT, int R, int MODE, int JU, int MINB, bool IND>
+// IND: 0 records no induced charge (none of that code is compiled in), 1 the
+// whole collecting surface, 2 also the pixels of the 3 x 3 window.
+template <int NT, int R, int MODE, int JU, int MINB, int IND>
 __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int nk) {
   constexpr int TI = NT * R;
   static_assert(MODE != 1 || R % 2 == 0, "packed-i variants pair i's two by two");
@@ -761,23 +871,25 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
       const float kc = a.ph.f_kc;
       if (skip) {
       } else if (a.fused) {
-        if constexpr (IND) {
+        if constexpr (IND > 0) {
           double q = 0.0;
+          double qpx[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int li = r * NT + tid;
             if (li < U.ni)
-              q += update_carrier(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
-                                  kc * vy[r], kc * vz[r], s_azn[spec]);
+              q += update_carrier<IND>(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
+                                       kc * vy[r], kc * vz[r], s_azn[spec], qpx);
           }
           add_induced(a, k, U.slot, q);
+          if constexpr (IND == 2) add_induced_px(a, k, U.slot, qpx);
         } else {
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const int li = r * NT + tid;
             if (li < U.ni)
-              update_carrier<false>(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
-                                    kc * vy[r], kc * vz[r], s_azn[spec]);
+              update_carrier<0>(a, S, U.slot, spec, U.ioff + li, step, p, k, kc * vx[r],
+                                kc * vy[r], kc * vz[r], s_azn[spec]);
           }
         }
       } else {
@@ -821,6 +933,8 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
 }
 
 // Update alone: reads the field written by a FIELD_ONLY step launch.
+// PX: the instantiation that records the 3 x 3 window's pixels too.
+template <bool PX>
 __global__ void update_kernel(StepArgs a, int k, const int32_t* slot_list, int n_slots) {
   for (int q = 0; q < n_slots; ++q) {
     const int slot = slot_list[q];
@@ -836,14 +950,16 @@ __global__ void update_kernel(StepArgs a, int k, const int32_t* slot_list, int n
     const int n = S->n_h + S->n_e;
     const int64_t cap = a.A.capacity;
     double qi = 0.0;
+    double qpx[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
       const int spec = t < S->n_h ? 0 : 1;
       const int64_t idx = S->base + (spec ? S->cap_h + (t - S->n_h) : t);
-      qi += update_carrier(a, S, slot, spec, idx, step, p, k, a.field_out[idx],
-                           a.field_out[cap + idx], a.field_out[2 * cap + idx],
-                           spec ? azn1 : azn0);
+      qi += update_carrier<PX ? 2 : 1>(a, S, slot, spec, idx, step, p, k, a.field_out[idx],
+                                       a.field_out[cap + idx], a.field_out[2 * cap + idx],
+                                       spec ? azn1 : azn0, qpx);
     }
     add_induced(a, k, slot, qi);
+    if constexpr (PX) add_induced_px(a, k, slot, qpx);
   }
 }
 
@@ -1064,15 +1180,9 @@ __global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, Slo
 }
 
 // ---------------------------------------------------------------------------
-// Readout: pixel = floor(x / pitch + n/2) per axis, warp-aggregated counts.
+// Readout: pixel = floor(x / pitch + n/2) per axis (pixel_key), warp-aggregated
+// counts.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int pixel_key(const Phys& ph, double x, double y) {
-  const double half = 0.5 * (double)ph.grid_n;
-  const double fx = floor(__dadd_rn(__ddiv_rn(x, ph.pitch), half));
-  const double fy = floor(__dadd_rn(__ddiv_rn(y, ph.pitch), half));
-  if (!(fx >= 0.0 && fy >= 0.0 && fx < (double)ph.grid_n && fy < (double)ph.grid_n)) return -1;
-  return (int)fy * ph.grid_n + (int)fx;
-}
 
 // key >= 0: pixel; -1: outside; -2: nothing.  Lanes with equal keys add once.
 __device__ __forceinline__ void warp_count(int key, int32_t* pix, int* outside) {
@@ -1165,6 +1275,7 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
   return t;
 }
 
+template <bool PX>
 __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, int nk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSphMax]
@@ -1251,6 +1362,7 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
     const float kcf = ph.f_kc;
     const double azn = s_azn;
     double qi = 0.0;
+    double qpx[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int j = tid; j < p2; j += nt) {
       const int t = idx[j];
       if (t >= nh) continue;
@@ -1272,9 +1384,10 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
           ez = f * dz;
         }
       }
-      qi += update_carrier(a, S, slot, 0, ai, step, p, k, ex, ey, ez, azn);
+      qi += update_carrier<PX ? 2 : 1>(a, S, slot, 0, ai, step, p, k, ex, ey, ez, azn, qpx);
     }
     add_induced(a, k, slot, qi);
+    if constexpr (PX) add_induced_px(a, k, slot, qpx);
     __syncthreads();
   }
 }
@@ -1494,6 +1607,7 @@ struct VariantEntry {
   void (*fn)(StepArgs, int, int);
   int ctas_per_sm, dynamic, mode;
   void (*fn_ind)(StepArgs, int, int);  // the same kernel recording the induced charge
+  void (*fn_px)(StepArgs, int, int);   // ... and the 3 x 3 window's pixel signals
 };
 
 // (threads, i's per thread, packed f32x2, j unroll, min CTAs per SM [register
@@ -1501,8 +1615,8 @@ struct VariantEntry {
 // the default: sources paired in packed FP32 lanes, 512-carrier tiles, guided
 // dynamic queue (fastest on the 64 x 20 keV batch).
 #define CTS_V(NT, R, MODE, JU, MB, CPS, DYN, NAME) \
-  {NT, R, NAME, step_kernel<NT, R, MODE, JU, MB, false>, CPS, DYN, MODE, \
-   step_kernel<NT, R, MODE, JU, MB, true>}
+  {NT, R, NAME, step_kernel<NT, R, MODE, JU, MB, 0>, CPS, DYN, MODE, \
+   step_kernel<NT, R, MODE, JU, MB, 1>, step_kernel<NT, R, MODE, JU, MB, 2>}
 const VariantEntry kVariants[] = {
     CTS_V(256, 2, 2, 4, 3, 0, 1, "nt256_r2_jpair_dyn"),
     CTS_V(256, 4, 2, 4, 2, 0, 1, "nt256_r4_jpair_dyn"),
@@ -1541,18 +1655,25 @@ cudaError_t variant_occupancy(int v, int* blocks_per_sm) {
   err = cudaFuncSetAttribute(e.fn_ind, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_of(e));
   if (err != cudaSuccess) return err;
+  err = cudaFuncSetAttribute(e.fn_px, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_of(e));
+  if (err != cudaSuccess) return err;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, e.fn, e.nt, smem_of(e));
 }
 
 cudaError_t launch_step(int v, const StepArgs& a, int k0, int nk, int grid, cudaStream_t s) {
   const VariantEntry& e = kVariants[v];
-  (a.induced ? e.fn_ind : e.fn)<<<grid, e.nt, smem_of(e), s>>>(a, k0, nk);
+  (a.induced_px ? e.fn_px : (a.induced ? e.fn_ind : e.fn))<<<grid, e.nt, smem_of(e), s>>>(
+      a, k0, nk);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update(const StepArgs& a, int k, int n_slots_list, const int32_t* slot_list,
                           int grid, cudaStream_t s) {
-  update_kernel<<<grid, 256, 0, s>>>(a, k, slot_list, n_slots_list);
+  if (a.induced_px)
+    update_kernel<true><<<grid, 256, 0, s>>>(a, k, slot_list, n_slots_list);
+  else
+    update_kernel<false><<<grid, 256, 0, s>>>(a, k, slot_list, n_slots_list);
   return cudaGetLastError();
 }
 
@@ -1590,12 +1711,19 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
 constexpr size_t kSphSmem = (size_t)kSphMax * (sizeof(unsigned long long) + sizeof(int32_t));
 
 cudaError_t spherical_prepare() {
-  return cudaFuncSetAttribute(spherical_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const cudaError_t e = cudaFuncSetAttribute(
+      spherical_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSphSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(spherical_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kSphSmem);
 }
 
 cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s) {
-  if (a.S > 0) spherical_kernel<<<a.S, 1024, kSphSmem, s>>>(a, k0, nk);
+  if (a.S <= 0) return cudaSuccess;
+  if (a.induced_px)
+    spherical_kernel<true><<<a.S, 1024, kSphSmem, s>>>(a, k0, nk);
+  else
+    spherical_kernel<false><<<a.S, 1024, kSphSmem, s>>>(a, k0, nk);
   return cudaGetLastError();
 }
 

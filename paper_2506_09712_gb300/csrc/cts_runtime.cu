@@ -63,6 +63,7 @@ struct Done {
   std::vector<double> final_xy;
   std::vector<int32_t> rstep;
   std::vector<double> induced;  // charge on the collecting surface after each step (e)
+  std::vector<double> induced_px;  // [step][9]: the same on the 3 x 3 centre pixels
   int64_t order = 0;
 };
 
@@ -79,6 +80,8 @@ struct HostSlot {
   int64_t n_steps = 0, interactions = 0;
   std::vector<double> induced;  // per executed step (options.keep_induced)
   double induced_q = 0.0;
+  std::vector<double> induced_px;  // [step][9] per executed step
+  double induced_pxq[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 }  // namespace
@@ -113,6 +116,8 @@ struct sim_t {
   float* d_drift = nullptr;           // sampled drift field (optional)
   double* d_induced = nullptr;        // [K][S] induced charge per chunk step (keep_induced)
   double* h_induced = nullptr;
+  double* d_induced_px = nullptr;     // [K][S][9] the same per pixel of the 3 x 3 window
+  double* h_induced_px = nullptr;
   std::vector<double> drift_host;     // the caller's samples, copied at init
   int32_t* d_err = nullptr;
   float* d_field = nullptr;
@@ -271,6 +276,29 @@ Phys make_phys(const sim_sensor_t& se, const sim_field_t& f, const sim_mobility_
   p.species = se.species;
   p.grid_n = se.grid_n;
   p.max_steps = se.max_steps;
+  // Pixel weighting potentials of the 3 x 3 window around the centre pixel
+  // c = grid_n / 2: its lower-left corner, then the image pairs.  A pair n of
+  // images of a pixel of area A behaves for large n like
+  //   -A z / (4 pi H^3 n^3) + A z (3 <r^2> - 2 z^2) / (16 pi H^5 n^5),
+  // which holds while the lateral distance r stays well below 2 n H: M pairs
+  // are summed term by term, M from the grid's half-diagonal (2.5 r / H,
+  // at least 4), and the rest by these two terms with zeta(3) and zeta(5)
+  // less their partial sums.
+  {
+    const int c = se.grid_n / 2;
+    p.wp_x0 = p.wp_y0 = ((double)(c - 1) - 0.5 * (double)se.grid_n) * se.pitch_um;
+    const double rho = 0.5 * std::sqrt(2.0) * (double)se.grid_n * se.pitch_um;
+    const int M = (int)std::min(64.0, std::max(4.0, std::ceil(2.5 * rho / se.thickness_um)));
+    double s3 = 1.2020569031595942854, s5 = 1.0369277551433699263;
+    for (int n = 1; n <= M; ++n) {
+      s3 -= 1.0 / ((double)n * n * n);
+      s5 -= 1.0 / ((double)n * n * n * n * n);
+    }
+    const double A = se.pitch_um * se.pitch_um, H = se.thickness_um;
+    p.wp_pairs = M;
+    p.wp_c3 = (float)(-A * s3 / (4.0 * M_PI * H * H * H));
+    p.wp_c5 = (float)(A * s5 / (16.0 * M_PI * H * H * H * H * H));
+  }
   return p;
 }
 
@@ -449,6 +477,7 @@ StepArgs step_args(sim_t* s, bool fused) {
   a.combine_count = s->d_combine;
   a.tiles_done = s->d_tiles_done;
   a.induced = s->d_induced;
+  a.induced_px = s->d_induced_px;
   a.field_out = s->d_field;
   a.err = s->d_err;
   a.ph = s->ph;
@@ -538,6 +567,8 @@ int issue_chunk(sim_t* s, int K, bool multi) {
   CK(cudaMemsetAsync(s->d_tiles_done, 0, (size_t)K * s->S * sizeof(int32_t), s->stream));
   if (s->d_induced)
     CK(cudaMemsetAsync(s->d_induced, 0, (size_t)K * s->S * sizeof(double), s->stream));
+  if (s->d_induced_px)
+    CK(cudaMemsetAsync(s->d_induced_px, 0, (size_t)K * s->S * 9 * sizeof(double), s->stream));
   if (s->field.spherical) {
     // the spherical model: one CTA per slot runs all K steps of its event
     const StepArgs a = step_args(s, true);
@@ -581,6 +612,8 @@ int issue_chunk(sim_t* s, int K, bool multi) {
   s->st_launch += 1;
   CK(d2h(s, s->h_summary, s->d_summary, s->S * sizeof(SlotSummary)));
   if (s->d_induced) CK(d2h(s, s->h_induced, s->d_induced, (size_t)K * s->S * sizeof(double)));
+  if (s->d_induced_px)
+    CK(d2h(s, s->h_induced_px, s->d_induced_px, (size_t)K * s->S * 9 * sizeof(double)));
   CK(d2h(s, s->h_err, s->d_err, sizeof(int32_t)));
   return SIM_OK;
 }
@@ -735,6 +768,7 @@ int fetch_results(sim_t* s, const std::vector<int>& fin) {
       d.rstep = std::move(rs[q]);
     }
     d.induced = std::move(h.induced);
+    d.induced_px = std::move(h.induced_px);
     s->st_events += 1;
     s->st_inter += d.interactions;
     out.push_back(std::move(d));
@@ -776,13 +810,20 @@ int pump(sim_t* s, bool defer, bool* progressed) {
     HostSlot& h = s->slots[k];
     if (!h.used || !h.running) continue;
     const SlotSummary& m = s->h_summary[k];
-    if (s->h_induced) {
+    if (s->h_induced || s->h_induced_px) {
       // the steps this chunk executed for the slot, in order
       const int K = s->opt.mode == CTS_MODE_PLAIN ? 1 : s->K;
       const int64_t ran = std::min<int64_t>(std::max<int64_t>(m.n_steps - h.n_steps, 0), K);
       for (int64_t kk = 0; kk < ran; ++kk) {
-        h.induced_q += s->h_induced[kk * s->S + k];
-        h.induced.push_back(h.induced_q);
+        if (s->h_induced) {
+          h.induced_q += s->h_induced[kk * s->S + k];
+          h.induced.push_back(h.induced_q);
+        }
+        if (s->h_induced_px)
+          for (int j = 0; j < 9; ++j) {
+            h.induced_pxq[j] += s->h_induced_px[(kk * s->S + k) * 9 + j];
+            h.induced_px.push_back(h.induced_pxq[j]);
+          }
       }
     }
     h.n_h = m.n_h;
@@ -844,6 +885,11 @@ void copy_out(const Done& d, sim_result_t* r, int grid_n) {
     const int64_t m = std::min<int64_t>(r->induced_capacity, (int64_t)d.induced.size());
     for (int64_t k = 0; k < m; ++k) r->induced_e[k] = d.induced[(size_t)k];
     for (int64_t k = m; k < r->induced_capacity; ++k) r->induced_e[k] = NAN;
+  }
+  if (r->induced_px) {
+    const int64_t m = std::min<int64_t>(r->induced_capacity, (int64_t)d.induced_px.size() / 9);
+    for (int64_t k = 0; k < 9 * m; ++k) r->induced_px[k] = d.induced_px[(size_t)k];
+    for (int64_t k = 9 * m; k < 9 * r->induced_capacity; ++k) r->induced_px[k] = NAN;
   }
 }
 
@@ -934,7 +980,8 @@ int alloc_all(sim_t* s) {
   AL(s->d_partial, s->partial_cap);
   AL(s->d_combine, kMaxUnits);
   AL(s->d_tiles_done, (int64_t)kMaxK * s->S);
-  if (s->opt.keep_induced) AL(s->d_induced, (int64_t)kMaxK * s->S);
+  if (s->opt.keep_induced & SIM_INDUCED_TOTAL) AL(s->d_induced, (int64_t)kMaxK * s->S);
+  if (s->opt.keep_induced & SIM_INDUCED_PIXELS) AL(s->d_induced_px, (int64_t)kMaxK * s->S * 9);
   AL(s->d_err, 1);
   AL(s->d_explicit, C);
   AL(s->d_list, s->S);
@@ -947,7 +994,8 @@ int alloc_all(sim_t* s) {
   HL(s->h_readout, s->S);
   HL(s->h_pixels, (int64_t)s->S * s->sensor.grid_n * s->sensor.grid_n);
   HL(s->h_err, 1);
-  if (s->opt.keep_induced) HL(s->h_induced, (int64_t)kMaxK * s->S);
+  if (s->opt.keep_induced & SIM_INDUCED_TOTAL) HL(s->h_induced, (int64_t)kMaxK * s->S);
+  if (s->opt.keep_induced & SIM_INDUCED_PIXELS) HL(s->h_induced_px, (int64_t)kMaxK * s->S * 9);
 #undef AL
 #undef HL
   CK(cudaMemset(s->d_slots, 0, s->S * sizeof(SlotDev)));
@@ -968,11 +1016,11 @@ void free_all(sim_t* s) {
                  s->A.rstep, s->A.cstate, s->d_slots, s->d_summary, s->d_readout, s->d_pixels,
                  s->d_units, s->d_cta_begin, s->d_unit_counter, s->d_ret, s->d_partial,
                  s->d_combine, s->d_tiles_done, s->d_induced, s->d_err, s->d_field, s->d_explicit,
-                 s->d_list, s->d_drift};
+                 s->d_list, s->d_drift, s->d_induced_px};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {s->h_summary, s->h_units, s->h_cta_begin, s->h_list, s->h_slotdev, s->h_readout,
-                  s->h_pixels, s->h_err, s->h_induced};
+                  s->h_pixels, s->h_err, s->h_induced, s->h_induced_px};
   for (void* p : host)
     if (p) cudaFreeHost(p);
   if (s->ev0) cudaEventDestroy(s->ev0);
@@ -1043,6 +1091,10 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
       opt.max_carriers < 0 || opt.hbm_budget_bytes < 0 || opt.queue_capacity < 0 ||
       opt.variant < 0 || opt.variant > variant_count())
     return SIM_EINVAL;
+  if (opt.keep_induced < 0 || opt.keep_induced > (SIM_INDUCED_TOTAL | SIM_INDUCED_PIXELS))
+    return SIM_EINVAL;
+  // the 3 x 3 window around the centre pixel must lie inside the grid
+  if ((opt.keep_induced & SIM_INDUCED_PIXELS) && sensor->grid_n < 3) return SIM_EINVAL;
   int sms = 0;
   rc = check_device(opt.device, &sms);
   if (rc) return rc;

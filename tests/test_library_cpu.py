@@ -339,6 +339,27 @@ def test_bad_drift_tables_are_rejected(lib, table):
     assert e.value.code == cts.SIM_EINVAL
 
 
+@pytest.mark.parametrize("flags,grid_n", [(-1, 9), (4, 9), (7, 9),
+                                          (cts.SIM_INDUCED_PIXELS, 2),
+                                          (cts.SIM_INDUCED_TOTAL | cts.SIM_INDUCED_PIXELS, 1)])
+def test_induced_recording_flags_are_checked_before_the_device(lib, flags, grid_n):
+    # unknown flags, and a 3 x 3 pixel window that does not fit the grid
+    import workloads as W
+    p = W.preset("plain_3keV_100um")
+    with pytest.raises(cts.SimError) as e:
+        cts.Simulator(dict(p["sensor"], grid_n=grid_n), p["mobility"], keep_induced=flags)
+    assert e.value.code == cts.SIM_EINVAL
+
+
+def test_pixel_signal_buffers_follow_the_option(lib):
+    # the result arrays the binding hands to the library: 9 per step
+    r = cts.Results(2, 5, 0, 7, induced_px=True)
+    assert r.induced_px.shape == (2, 7, 3, 3)
+    assert bool(r.arr[1].induced_px) and r.arr[1].induced_capacity == 7
+    r = cts.Results(2, 5, 0, 7)
+    assert r.induced_px is None and not r.arr[0].induced_px
+
+
 def test_host_model_entry_points_reject_bad_input(lib):
     import ctypes as C
     import numpy as np
