@@ -424,6 +424,16 @@ int sim_generate(const sim_gen_event_t* events, int32_t n_events, double pitch_u
  * SIM_ENODEV or SIM_ECUDA. */
 int sim_debug_fma_peak(int32_t device, int32_t packed, double* flops_per_s);
 
+/* Compile-time options of this library build (no device needed):
+ * SIM_BUILD_BOUNDS_CHECK when it was compiled with -DCTS_BOUNDS_CHECK.  That
+ * build's kernels check the arena index ranges of every slot, unit and
+ * carrier they touch; an index outside its range is recorded and the access
+ * skipped (never made), and the calls that ran the kernel then fail with
+ * SIM_ECUDA ("an index left its slot's range").  A debugging aid in place of
+ * a sanitizer; the default build compiles none of these checks. */
+#define SIM_BUILD_BOUNDS_CHECK 1
+int sim_build_flags(void);
+
 /* Per-launch log of the step kernel, kept while the handle was created with
  * options.time_launches != 0 (at most 1 << 20 entries, oldest dropped).
  * Copies up to `cap` entries, oldest first, as triples (kernel ms from CUDA

@@ -15,7 +15,10 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libcts.so")
+# CTS_CHECKED=1 selects the bounds-checked build (build.build(checked=True))
+CHECKED = os.environ.get("CTS_CHECKED", "") == "1"
+LIB_PATH = (os.path.join(_HERE, "_build_checked", "libcts_checked.so") if CHECKED
+            else os.path.join(_HERE, "_build", "libcts.so"))
 
 SIM_OK, SIM_EINVAL, SIM_ENOMEM_BUDGET, SIM_EAGAIN, SIM_ETIMEOUT = 0, -1, -2, -3, -4
 SIM_ECUDA, SIM_EMAXSTEPS, SIM_ENUMERIC, SIM_ESTATE, SIM_ENODEV = -5, -6, -7, -8, -9
@@ -24,6 +27,7 @@ CTS_MOB_CT, CTS_MOB_CONST = 0, 1
 CTS_PHOTON, CTS_TRACK, CTS_EXPLICIT = 0, 1, 2
 CTS_MODE_PLAIN, CTS_MODE_BATCHED, CTS_MODE_SERVE = 0, 1, 2
 SIM_INDUCED_TOTAL, SIM_INDUCED_PIXELS = 1, 2   # options.keep_induced flags
+SIM_BUILD_BOUNDS_CHECK = 1                       # sim_build_flags()
 
 
 class sim_sensor_t(C.Structure):
@@ -113,7 +117,7 @@ EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_e
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
             "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_debug_launch_log",
-            "sim_debug_fma_peak", "sim_readout", "cts_fano_pairs", "sim_generate",
+            "sim_debug_fma_peak", "sim_build_flags", "sim_readout", "cts_fano_pairs", "sim_generate",
             "cts_fit_ggd", "cts_fit_alpha_t", "cts_fit_beta_t", "cts_ggd_params_at",
             "cts_variant_table_save", "cts_variant_table_load",
             "sim_set_variants",
@@ -136,7 +140,7 @@ def load(build_if_missing: bool = True):
         return _lib
     if not os.path.exists(LIB_PATH) and build_if_missing:
         from . import build as _b
-        _b.build()
+        _b.build(checked=CHECKED)
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"CUDA library not built: {LIB_PATH}")
     lib = C.CDLL(LIB_PATH)
@@ -166,6 +170,7 @@ def load(build_if_missing: bool = True):
         "sim_debug_time_step": [C.c_void_p, i32, i32, P(d)],
         "sim_debug_launch_log": [C.c_void_p, P(d), i32, P(i32)],
         "sim_debug_fma_peak": [i32, i32, P(d)],
+        "sim_build_flags": [],
         "sim_readout": [P(sim_readout_params_t), P(i32), P(u64), P(u64), i32, i32, P(d),
                         P(sim_cluster_t), P(i64)],
         "cts_fano_pairs": [u64, u64, d, d, P(i32)],
@@ -444,6 +449,11 @@ def sim_readout(counts, seeds, event_ids, beam_keV, n_bins=0, device=0, want_pix
     if want_pixels:
         out["e"] = pix
     return out
+
+
+def sim_build_flags() -> int:
+    """SIM_BUILD_BOUNDS_CHECK when the loaded library is the checked build."""
+    return load().sim_build_flags()
 
 
 def sim_debug_fma_peak(device=0, packed=True):

@@ -82,12 +82,6 @@ __device__ __forceinline__ float mobility_f(const Phys& ph, int spec, float E) {
   const float x = mu0 * E / ph.f_vsat[spec];
   return mu0 / powf(1.0f + powf(x, ph.f_beta[spec]), ph.f_ibeta[spec]);
 }
-__device__ __forceinline__ double mobility_d(const Phys& ph, int spec, double E) {
-  const double mu0 = ph.mu0[spec];
-  if (ph.mob_model == 1) return mu0;
-  const double x = __ddiv_rn(__dmul_rn(mu0, E), ph.vsat[spec]);
-  return __ddiv_rn(mu0, pow(__dadd_rn(1.0, pow(x, ph.beta[spec])), __drcp_rn(ph.beta[spec])));
-}
 
 // Drift-field magnitude at depth z (Eq. 6, or the handle's sampled profile).
 __device__ __forceinline__ float drift_E(const Phys& ph, float z) {
@@ -324,6 +318,26 @@ __device__ __forceinline__ int pixel_key(const Phys& ph, double x, double y) {
   return pixel_at(ph.pitch, ph.grid_n, x, y);
 }
 
+#ifdef CTS_BOUNDS_CHECK
+// Checked build (-DCTS_BOUNDS_CHECK): index checks that record kErrBounds and
+// skip the access instead of making it.  A slot owns the arena entries
+// [base, base + cap_h + cap_e), and its carrier ids are below n_total, which
+// does not exceed that count.
+__device__ __forceinline__ bool slot_in_arena(const Arena& A, const SlotDev* S) {
+  const int64_t n = (int64_t)S->cap_h + S->cap_e;
+  return S->base >= 0 && S->cap_h >= 0 && S->cap_e >= 0 && S->base + n <= A.capacity &&
+         S->n_total >= 0 && S->n_total <= n;
+}
+
+// A unit's i range and source ranges lie in the arena, its slot in the table.
+__device__ __forceinline__ bool unit_in_arena(const StepArgs& a, const Unit& U) {
+  const int64_t cap = a.A.capacity;
+  return U.slot >= 0 && U.slot < a.S && U.ni >= 0 && U.len_h >= 0 && U.len_e >= 0 &&
+         U.ioff >= 0 && U.ioff + U.ni <= cap && U.hoff >= 0 && U.hoff + U.len_h <= cap &&
+         U.eoff >= 0 && U.eoff + U.len_e <= cap;
+}
+#endif
+
 // Weighting potentials (Shockley-Ramo) of the 3 x 3 pixels around the grid's
 // centre pixel c = grid_n / 2 at (x, y, z), z on [0, H]; w[b * 3 + a] is grid
 // pixel (c - 1 + a, c - 1 + b).  A pixel's potential solves Laplace's
@@ -407,8 +421,20 @@ __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, 
                                                double* qpx = nullptr) {
   const Phys& ph = a.ph;
   float4* __restrict__ shout = a.A.sh[p ^ 1];
+#ifdef CTS_BOUNDS_CHECK
+  if (idx < 0 || idx >= a.A.capacity || slot < 0 || slot >= a.S || k < 0 || k >= kMaxK) {
+    atomicOr(a.err, kErrBounds);
+    return 0.0;
+  }
+#endif
   const int id = a.A.cid[idx];
   const int64_t rid = S->base + id;
+#ifdef CTS_BOUNDS_CHECK
+  if (id < 0 || id >= S->n_total || rid < 0 || rid >= a.A.capacity) {
+    atomicOr(a.err, kErrBounds);
+    return 0.0;
+  }
+#endif
   const int8_t st = __ldcg(a.A.cstate + rid);
   if ((st & kStateMask) != kStateActive) {
     shout[idx] = make_float4(kParked, kParked, kParked, 0.0f);
@@ -579,6 +605,13 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
     const int k = k0 + kq;
     const Unit U = a.units[a.dynamic ? q - kq * n_u : q];
     if (!a.dynamic) ++q;
+#ifdef CTS_BOUNDS_CHECK
+    if (!unit_in_arena(a, U) || k >= kMaxK || !slot_in_arena(a.A, a.slots + U.slot)) {
+      if (tid == 0) atomicOr(a.err, kErrBounds);
+      failed = true;
+      break;
+    }
+#endif
     SlotDev* S = a.slots + U.slot;
     if (kq > 0) {
       // A later step of the launch starts once every tile of the slot has
@@ -1034,6 +1067,21 @@ __global__ void __launch_bounds__(kAuxThreads) close_kernel(Phys ph, Arena A, Sl
     if (threadIdx.x == 0) summary[slot] = sm;
     return;
   }
+#ifdef CTS_BOUNDS_CHECK
+  if (!slot_in_arena(A, S) || S->n_h < 0 || S->n_h > S->cap_h || S->n_e < 0 ||
+      S->n_e > S->cap_e) {
+    // stop the slot without touching its arena range; the host sees the flag
+    if (threadIdx.x == 0) {
+      S->flags |= kErrBounds;
+      S->running = 0;
+      sm.done = 1;
+      sm.status = -5;
+      sm.flags = S->flags;
+      summary[slot] = sm;
+    }
+    return;
+  }
+#endif
   int nah = S->act_h, nae = S->act_e;
   for (int kk = 0; kk < K; ++kk) {
     nah -= ret[((int64_t)kk * S_count + slot) * 2 + 0];
@@ -1097,7 +1145,6 @@ __global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, Slo
   }
   __syncthreads();
   const int np = S->n_pairs;
-  const int n_tot = S->n_total;
   const double H = ph.H;
   const double sigma = S->sigma_um >= 0.0 ? S->sigma_um : 0.0044 * pow(S->energy_keV, 1.75);
   const double z_entry = H - S->depth_um;
@@ -1110,8 +1157,19 @@ __global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, Slo
   const double ax0 = S->x0 + half * ux, ay0 = S->y0 + half * uy;
   const double az0 = fmin(fmax(S->kind == 1 ? H + half * uz : z_entry, 0.0), H);
   const int total_entries = S->cap_h + S->cap_e;
+#ifdef CTS_BOUNDS_CHECK
+  // the slot's range, the explicit records it reads, and every carrier id
+  __shared__ int bad;
+  if (threadIdx.x == 0)
+    bad = !slot_in_arena(A, S) || S->n_pairs < 0 || S->n_pairs > S->cap_h ||
+          (S->kind == 2 && (S->explicit_off < 0 || S->explicit_off + total_entries > A.capacity));
+  __syncthreads();
+  const int loop_end = bad ? 0 : total_entries;
+#else
+  const int loop_end = total_entries;
+#endif
 
-  for (int e = threadIdx.x; e < total_entries; e += blockDim.x) {
+  for (int e = threadIdx.x; e < loop_end; e += blockDim.x) {
     const int spec = e < S->cap_h ? 0 : 1;
     const int64_t idx = S->base + e;
     double x, y, z;
@@ -1136,6 +1194,12 @@ __global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, Slo
       }
     }
     const int64_t rid = S->base + id;
+#ifdef CTS_BOUNDS_CHECK
+    if (id < 0 || id >= total_entries) {
+      atomicOr(&S->flags, kErrBounds);
+      continue;
+    }
+#endif
     int state = kStateActive;
     if (spec == 0) {
       if (z <= 0.0) state = kStateCollected;
@@ -1159,7 +1223,6 @@ __global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, Slo
       A.sh[0][idx] = make_float4((float)(x - ax0), (float)(y - ay0), (float)(z - az0), 0.0f);
     }
   }
-  (void)n_tot;
   __syncthreads();
   if (threadIdx.x == 0) {
     S->ax = ax0;
@@ -1172,7 +1235,11 @@ __global__ void __launch_bounds__(kAuxThreads) init_kernel(Phys ph, Arena A, Slo
     S->act_e = S->cap_e - ret_e;
     S->step0 = 0;
     S->n_steps = 0;
+#ifdef CTS_BOUNDS_CHECK
+    S->flags = (bad || (S->flags & kErrBounds)) ? kErrBounds : 0;
+#else
     S->flags = 0;
+#endif
     S->status = 0;
     S->interactions = 0ull;
     S->running = 1;
@@ -1205,7 +1272,11 @@ __global__ void __launch_bounds__(kAuxThreads) bin_kernel(Phys ph, Arena A, cons
   for (int t = threadIdx.x; t < npix; t += blockDim.x) pix[t] = 0;
   if (threadIdx.x == 0) outside = collected = lost = 0;
   __syncthreads();
+#ifdef CTS_BOUNDS_CHECK
+  const int n = slot_in_arena(A, S) ? S->n_total : 0;
+#else
   const int n = S->n_total;
+#endif
   const int n_round = (n + blockDim.x - 1) / blockDim.x * blockDim.x;
   for (int id = threadIdx.x; id < n_round; id += blockDim.x) {
     int key = -2;
@@ -1277,7 +1348,7 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
 
 template <bool PX>
 __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, int nk) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSphMax]
   int32_t* idx = reinterpret_cast<int32_t*>(key + kSphMax);                    // [kSphMax]
   __shared__ double red[33];
@@ -1291,6 +1362,12 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
     if (nh > kSphMax && threadIdx.x == 0) atomicOr(a.err, kErrPlan);
     return;
   }
+#ifdef CTS_BOUNDS_CHECK
+  if (!slot_in_arena(a.A, S) || nh > S->cap_h || k0 < 0 || k0 + nk > kMaxK) {
+    if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
+    return;
+  }
+#endif
   int p2 = 2;
   while (p2 < nh) p2 <<= 1;
   const int tid = threadIdx.x, nt = blockDim.x;

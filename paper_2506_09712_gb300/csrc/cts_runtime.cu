@@ -709,6 +709,11 @@ int run_chunk(sim_t* s) {
     s->err = "a unit descriptor disagrees with its slot on the device";
     return SIM_ECUDA;
   }
+  if (*s->h_err & kErrBounds) {
+    s->broken = true;
+    s->err = "an index left its slot's range on the device (checked build)";
+    return SIM_ECUDA;
+  }
   return SIM_OK;
 }
 
@@ -810,6 +815,11 @@ int pump(sim_t* s, bool defer, bool* progressed) {
     HostSlot& h = s->slots[k];
     if (!h.used || !h.running) continue;
     const SlotSummary& m = s->h_summary[k];
+    if (m.flags & kErrBounds) {
+      s->broken = true;
+      s->err = "an index left its slot's range on the device (checked build)";
+      return SIM_ECUDA;
+    }
     if (s->h_induced || s->h_induced_px) {
       // the steps this chunk executed for the slot, in order
       const int K = s->opt.mode == CTS_MODE_PLAIN ? 1 : s->K;
@@ -1941,6 +1951,14 @@ int sim_readout(const sim_readout_params_t* prm, const int32_t* counts, const ui
   if (dh) cudaFree(dh);
   if (st) cudaStreamDestroy(st);
   return e == cudaSuccess ? SIM_OK : SIM_ECUDA;
+}
+
+int sim_build_flags(void) {
+#ifdef CTS_BOUNDS_CHECK
+  return SIM_BUILD_BOUNDS_CHECK;
+#else
+  return 0;
+#endif
 }
 
 int sim_debug_fma_peak(int32_t device, int32_t packed, double* flops_per_s) {

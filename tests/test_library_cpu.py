@@ -40,6 +40,19 @@ def test_exports_every_declared_symbol(lib):
     assert declared == set(cts.EXPORTED)
 
 
+def test_checked_build_loads_and_reports_itself(lib):
+    # the bounds-checked build (-DCTS_BOUNDS_CHECK) exports the same ABI and
+    # says which build it is; the default build compiles no checks
+    import ctypes as C
+    path = cts_build.build(checked=True)
+    assert path.endswith("libcts_checked.so") and os.path.exists(path)
+    checked = C.CDLL(path)
+    for name in _declared_symbols():
+        assert hasattr(checked, name), name
+    assert checked.sim_build_flags() == cts.SIM_BUILD_BOUNDS_CHECK
+    assert lib.sim_build_flags() == 0
+
+
 def test_strerror_names_every_code(lib):
     for code in range(-9, 1):
         assert cts.strerror(code) != "unknown status"
