@@ -322,6 +322,35 @@ def spherical_leg(cts, W, torch, device, stream, events, p):
             "statuses_ok": all(r["status"] == 0 for r in res)}
 
 
+def transient_leg(cts, W, torch, device, stream, events, p):
+    """The same batch recording the transient signals (Shockley-Ramo, the
+    extension of Sec. 5.3): the whole collecting surface and the 3 x 3 centre
+    pixels with their weighting potentials, after every step."""
+    flags = cts.SIM_INDUCED_TOTAL | cts.SIM_INDUCED_PIXELS
+    with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_BATCHED, device=device,
+                       max_slots=len(events), stream=stream.cuda_stream,
+                       keep_induced=flags) as sim:
+        ms = []
+        for _ in range(3):
+            sim.stage(events)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.execute()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res = sim.collect(len(events), induced_capacity=4096)
+            ms.append(e0.elapsed_time(e1))
+    t = min(ms[1:])
+    inter = sum(r["interactions"] for r in res)
+    return {"record": "induced charge per step: whole surface + 3x3 pixels", "events": len(events),
+            "ms_per_batch": t, "events_per_s": len(events) / (t * 1e-3),
+            "interactions_per_s": inter / (t * 1e-3),
+            "statuses_ok": all(r["status"] == 0 for r in res),
+            "steps_recorded": all(len(r["induced_px"]) == r["n_steps"] for r in res)}
+
+
 def uneven_leg(cts, W, torch, device, stream, n_events=500):
     """Uneven batching: the first n_events of the 1e4-event set (E ~ U(5, 25)
     keV, 1381-6906 carriers, 450 um Si), all resident in one batch."""
@@ -596,6 +625,11 @@ def run_ours(args, rank, world, local):
                                 "paper": "1e6 events in about 2 min on a 16-core CPU"}
         except Exception as e:  # reported, never fatal for the bench line
             line["generate"] = {"error": repr(e)}
+        try:
+            line["transient"] = transient_leg(cts, W, torch, local, stream, events, p)
+            line["transient"]["cost_vs_default"] = events_per_s / line["transient"]["events_per_s"]
+        except Exception as e:  # reported, never fatal for the bench line
+            line["transient"] = {"error": repr(e)}
         try:
             line["uneven"] = uneven_leg(cts, W, torch, local, stream)
             line["uneven"]["frac"] = line["uneven"]["step_kernel_tflops"] / peak_tflops

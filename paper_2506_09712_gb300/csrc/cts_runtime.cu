@@ -282,13 +282,14 @@ Phys make_phys(const sim_sensor_t& se, const sim_field_t& f, const sim_mobility_
   //   -A z / (4 pi H^3 n^3) + A z (3 <r^2> - 2 z^2) / (16 pi H^5 n^5),
   // which holds while the lateral distance r stays well below 2 n H: M pairs
   // are summed term by term, M from the grid's half-diagonal (2.5 r / H,
-  // at least 4), and the rest by these two terms with zeta(3) and zeta(5)
-  // less their partial sums.
+  // at least 2; the truncation then stays below 2e-7 within the grid, under
+  // the FP32 evaluation's own error), and the rest by these two terms with
+  // zeta(3) and zeta(5) less their partial sums.
   {
     const int c = se.grid_n / 2;
     p.wp_x0 = p.wp_y0 = ((double)(c - 1) - 0.5 * (double)se.grid_n) * se.pitch_um;
     const double rho = 0.5 * std::sqrt(2.0) * (double)se.grid_n * se.pitch_um;
-    const int M = (int)std::min(64.0, std::max(4.0, std::ceil(2.5 * rho / se.thickness_um)));
+    const int M = (int)std::min(64.0, std::max(2.0, std::ceil(2.5 * rho / se.thickness_um)));
     double s3 = 1.2020569031595942854, s5 = 1.0369277551433699263;
     for (int n = 1; n <= M; ++n) {
       s3 -= 1.0 / ((double)n * n * n);
