@@ -48,7 +48,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="batch_20keV_320um")
+    ap.add_argument("--workload", default="batch_20keV_320um",
+                    help="preset name, or the path of a JSON workload config "
+                         "(workloads/configs/*.json)")
     ap.add_argument("--events", type=int, default=0, help="events per rank (0: preset)")
     ap.add_argument("--variant", type=int, default=0)
     ap.add_argument("--chunk", type=int, default=0)

@@ -51,3 +51,56 @@ def test_serving_mix_and_arrivals():
     assert np.all(gaps >= 0)
     assert gaps.mean() == pytest.approx(1 / 2000.0, rel=0.03)
     assert stats.kstest(gaps * 2000.0, "expon").pvalue > 1e-3
+
+
+def test_committed_json_configs_are_the_presets():
+    # workloads/configs/*.json are written by `python -m workloads`; they must
+    # stay in step with the presets they mirror
+    import glob
+    import os
+    paths = sorted(glob.glob(os.path.join(W.CONFIG_DIR, "*.json")))
+    assert {os.path.basename(p)[:-5] for p in paths} == set(W.PRESETS)
+    for path in paths:
+        name = os.path.basename(path)[:-5]
+        cfg = W.load_config(path)
+        assert cfg.pop("name") == name
+        assert cfg == W.preset(name)
+        a = W.make_events(path, n=5, first_id=3)
+        b = W.make_events(name, n=5, first_id=3)
+        assert a == b
+
+
+def test_config_round_trip_and_edits(tmp_path):
+    path = str(tmp_path / "w.json")
+    W.save_config("plain_3keV_100um", path)
+    cfg = W.load_config(path)
+    cfg["sensor"]["thickness_um"] = 150.0
+    cfg["energies"] = [[8.0, 1.0]]
+    evs = W.make_events(cfg, n=20)
+    assert all(e["energy_keV"] == 8.0 for e in evs)
+    assert all(0.0 <= e["depth_um"] < 150.0 for e in evs)
+    assert W.preset(cfg)["sensor"]["thickness_um"] == 150.0
+
+
+@pytest.mark.parametrize("edit", ["drop_sensor_key", "two_recipes", "unknown_key",
+                                  "track_without_pairs", "negative_events", "not_object"])
+def test_bad_configs_are_rejected(tmp_path, edit):
+    import json
+    cfg = json.loads(json.dumps(W.preset("plain_3keV_100um")))
+    if edit == "drop_sensor_key":
+        del cfg["sensor"]["pitch_um"]
+    elif edit == "two_recipes":
+        cfg["energy_uniform"] = [5.0, 25.0]
+    elif edit == "unknown_key":
+        cfg["energy_keV"] = 20.0
+    elif edit == "track_without_pairs":
+        del cfg["energies"]
+        cfg.update(track=True, track_len_um=10.0, theta_max_deg=0.0)
+    elif edit == "negative_events":
+        cfg["n_events"] = -1
+    else:
+        cfg = [cfg]
+    path = tmp_path / "bad.json"
+    path.write_text(json.dumps(cfg))
+    with pytest.raises(ValueError):
+        W.load_config(str(path))

@@ -26,10 +26,16 @@ Presets (sizes from the paper's sensors and energies, Sec. 2 and Sec. 4):
                         50 um sensor (Vd 20 V, 50 V), 80 pairs/um (4000),
                         lateral sigma 1 nm, both species, dt 5 ps; electrons
                         are the collected species (see MIP_MOBILITY)
+
+Each preset also exists as a JSON config under ``configs/`` (``python -m
+workloads`` rewrites them); an edited copy can be passed wherever a preset
+name is accepted.
 """
 from __future__ import annotations
 
 import copy
+import json
+import os
 
 import numpy as np
 
@@ -93,9 +99,74 @@ PRESETS = {
 }
 
 
-def preset(name: str) -> dict:
-    """A deep copy of a preset (sensor, mobility and event-generation recipe)."""
-    return copy.deepcopy(PRESETS[name])
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs")
+
+# JSON workload configs: the preset's dictionary as it is (sensor, mobility,
+# event recipe).  Exactly one event recipe: energies (a list of [keV, weight]),
+# energy_uniform ([lo, hi] keV) or track (with n_pairs, track_len_um,
+# theta_max_deg).
+_SENSOR_KEYS = {"thickness_um", "bias_V", "depletion_V", "temperature_K", "eps_r", "pitch_um",
+                "grid_n", "dt_ps", "max_steps", "species", "softening_um"}
+_OPTIONAL_KEYS = {"rate_hz", "name"}
+
+
+def _check_config(cfg: dict) -> dict:
+    if not isinstance(cfg, dict):
+        raise ValueError("a workload config is a JSON object")
+    for key in ("sensor", "mobility", "n_events", "sigma_um"):
+        if key not in cfg:
+            raise ValueError(f"workload config lacks {key!r}")
+    missing = _SENSOR_KEYS - set(cfg["sensor"])
+    if missing:
+        raise ValueError(f"sensor lacks {sorted(missing)}")
+    recipes = [k for k in ("energies", "energy_uniform", "track") if k in cfg]
+    if len(recipes) != 1:
+        raise ValueError("give exactly one of energies, energy_uniform, track")
+    known = {"sensor", "mobility", "n_events", "sigma_um", "energies", "energy_uniform", "track",
+             "n_pairs", "track_len_um", "theta_max_deg"} | _OPTIONAL_KEYS
+    extra = set(cfg) - known
+    if extra:
+        raise ValueError(f"unknown workload config keys {sorted(extra)}")
+    if "track" in cfg:
+        for key in ("n_pairs", "track_len_um", "theta_max_deg"):
+            if key not in cfg:
+                raise ValueError(f"a track workload needs {key!r}")
+    if int(cfg["n_events"]) < 0:
+        raise ValueError("n_events must be >= 0")
+    out = copy.deepcopy(cfg)
+    if "energies" in out:
+        out["energies"] = [tuple(map(float, e)) for e in out["energies"]]
+    if "energy_uniform" in out:
+        out["energy_uniform"] = tuple(map(float, out["energy_uniform"]))
+    return out
+
+
+def save_config(name: str, path: str) -> None:
+    """Write a preset as a JSON workload config."""
+    cfg = dict(copy.deepcopy(PRESETS[name]), name=name)
+    with open(path, "w") as fh:
+        json.dump(cfg, fh, indent=1, sort_keys=True)
+        fh.write("\n")
+
+
+def load_config(path: str) -> dict:
+    """Read and check a JSON workload config (the shape of a preset)."""
+    with open(path) as fh:
+        return _check_config(json.load(fh))
+
+
+def _resolve(workload) -> dict:
+    if isinstance(workload, dict):
+        return _check_config(workload)
+    if isinstance(workload, str) and workload.endswith(".json"):
+        return load_config(workload)
+    return PRESETS[workload]
+
+
+def preset(name) -> dict:
+    """A deep copy of a preset (sensor, mobility and event-generation recipe);
+    `name` may also be a config dictionary or the path of a JSON config."""
+    return copy.deepcopy(_resolve(name))
 
 
 def field_switches(repulsion=1, drift=1, diffusion=1, spherical=0) -> dict:
@@ -113,10 +184,11 @@ def sample_depths(rng: np.random.Generator, energy_keV, thickness_um: float) -> 
     return -lam * np.log1p(-u * (-np.expm1(-thickness_um / lam)))
 
 
-def make_events(name: str, n: int | None = None, seed: int = MASTER_SEED,
+def make_events(name, n: int | None = None, seed: int = MASTER_SEED,
                 first_id: int = 0) -> list[dict]:
-    """Event descriptors for a preset (deterministic in `seed` and the ids)."""
-    p = PRESETS[name]
+    """Event descriptors for a preset, a config dictionary or the path of a
+    JSON config (deterministic in `seed` and the ids)."""
+    p = _resolve(name)
     s = p["sensor"]
     n = p["n_events"] if n is None else int(n)
     rng = np.random.default_rng([seed, first_id, 0x5EED])
