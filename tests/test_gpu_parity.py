@@ -11,7 +11,6 @@ Tolerances (derivations in the design notes):
   * Whole events: per-pixel collected charge within 1e-3 of the event total.
 """
 import math
-import os
 
 import numpy as np
 import pytest

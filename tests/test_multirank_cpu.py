@@ -4,7 +4,6 @@ numbers are the slowest rank's time and the summed counts."""
 import os
 import socket
 
-import pytest
 import torch.distributed as dist
 import torch.multiprocessing as mp
 
