@@ -383,7 +383,7 @@ def uneven_leg(cts, W, torch, device, stream, n_events=500):
 
 
 def mip_leg(cts, W, device):
-    """The MIP study of Sec. 4.3: per-axis RMS of the collected electrons of
+    """The MIP study of Sec. 5.1: per-axis RMS of the collected electrons of
     perpendicular 50 um tracks with and without repulsion (paper: 1.24 ->
     1.27 um with its unprinted electron mobility), and with electrons alone."""
     import numpy as np

@@ -182,7 +182,7 @@ def _mip_rms(res, evs):
 
 
 def test_mip_line_source():
-    # Sec. 4.3: a minimum-ionising particle crossing 50 um perpendicularly,
+    # Sec. 5.1: a minimum-ionising particle crossing 50 um perpendicularly,
     # 80 pairs/um, 1 nm wide.  The paper finds repulsion widens the collected
     # electron distribution by only 2.4 % (1.24 -> 1.27 um); its electron
     # mobility is not printed, so the checks here are the parity with the
