@@ -262,6 +262,42 @@ def test_events_parity_20keV_two_events():
         _compare_events(g, r, 5525)
 
 
+def test_benchmark_batch_at_full_size():
+    # The 64 x 20 keV batch in the launch configuration the benchmark times:
+    # every event resident, stage / execute / collect on the caller's stream,
+    # one step-kernel launch per 32-step chunk.  At this size the oracle runs
+    # sampled events one by one; identities cover the whole batch.
+    import torch
+    name = "batch_20keV_320um"
+    p = W.preset(name)
+    evs = W.make_events(name)
+    stream = torch.cuda.Stream()
+    with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_BATCHED, max_slots=256,
+                       time_launches=1, stream=stream.cuda_stream, keep_final_xy=1) as sim:
+        sim.stage(evs)
+        sim.execute()
+        torch.cuda.synchronize()
+        got = sim.collect(len(evs), keep_xy_capacity=5525)
+        st = sim.stats()
+    assert len(got) == len(evs) == 64
+    by_id = {int(g["event_id"]): g for g in got}
+    assert sorted(by_id) == [e["event_id"] for e in evs]
+    assert st["step_kernel_launches"] > 0
+    for g in got:
+        assert g["status"] == 0 and g["n_carriers"] == 5525
+        assert g["n_collected"] == 5525 and g["n_lost"] == 0
+        assert g["pixels"].sum() + g["n_outside"] == g["n_collected"]
+        rs = g["retire_step"]
+        assert (rs >= -1).all() and rs.max() == g["n_steps"] - 1
+        # the interaction counter is the sum over steps of N_act (N_act - 1)
+        assert g["interactions"] == oracle.count_interactions(rs, g["n_steps"])
+        fx = g["final_xy"]
+        assert np.isfinite(fx).all()
+    P = oracle_params(name)
+    for k in (0, 41):
+        _compare_events(by_id[evs[k]["event_id"]], oracle.run_event(P, evs[k]), 5525)
+
+
 def test_modes_and_mixes_agree():
     # PLAIN (two launches per step), BATCHED with and without graphs, SERVE;
     # an event alone and in a mix with others gives the same result.
