@@ -121,6 +121,8 @@ def lib():
                                           P(i32), P(i32), P(d), P(i32)]
         _lib.or_readout_event.restype = C.c_int
         _lib.or_spectrum_add.argtypes = [P(d), i32, d, d, i32, P(i64)]
+        _lib.or_uniform.argtypes = [u32]
+        _lib.or_uniform.restype = d
         _lib.or_rect_solid_angle.argtypes = [d, d, d, d, d, d, d]
         _lib.or_rect_solid_angle.restype = d
         _lib.or_weighting_potential.argtypes = [d, d, d, d, d, d, d, d, i32]
@@ -207,6 +209,11 @@ def philox4x32_10(ctr, key):
     o = (C.c_uint32 * 4)()
     lib().or_philox4x32_10(c, k, o)
     return [int(v) for v in o]
+
+
+def uniform(word: int) -> float:
+    """The uniform in (0, 1) that a 32-bit Philox word maps to."""
+    return lib().or_uniform(int(word) & 0xFFFFFFFF)
 
 
 def normals3(seed, event_id, purpose, carrier, step):

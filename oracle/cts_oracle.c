@@ -145,7 +145,7 @@ static void or_stream_words(uint64_t seed, uint64_t event_id, uint32_t purpose,
 
 /* Uniform in (0,1) from the top 23 bits: ((w >> 9) + 1/2) / 2^23.  Every such
  * value is exactly representable in FP32 as well as FP64. */
-static double or_uniform(uint32_t w) {
+double or_uniform(uint32_t w) {
   return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 

@@ -96,3 +96,35 @@ def test_streams_are_distinct_per_purpose_event_carrier_step(orc):
     assert orc.normals3(1, 2, 0, 3, 5) != base   # step
     assert orc.normals3(2, 2, 0, 3, 4) != base   # seed
     assert orc.normals3(1, 2, 0, 3, 4) == base   # deterministic
+
+
+def test_uniform_mapping_is_symmetric_open_and_fp32_exact(orc):
+    # u(w) = ((w >> 9) + 1/2) 2^-23: the complement word maps to 1 - u exactly,
+    # both ends stay inside (0, 1), and every value is an odd multiple of
+    # 2^-24, so FP32 and FP64 hold it exactly (the device draws the same u)
+    rng = np.random.default_rng(3)
+    words = list(rng.integers(0, 1 << 32, 2000, dtype=np.uint64)) + [0, 1, 511, 512,
+                                                                      0xFFFFFFFF, 0x80000000]
+    for w in words:
+        w = int(w)
+        u, v = orc.uniform(w), orc.uniform(w ^ 0xFFFFFFFF)
+        assert 0.0 < u < 1.0
+        assert u + v == 1.0
+        k = u * (1 << 24)
+        assert k == int(k) and int(k) % 2 == 1
+        assert float(np.float32(u)) == u
+    assert orc.uniform(0) == 2.0 ** -24 and orc.uniform(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    # 512 consecutive words share one value (the low 9 bits are dropped)
+    assert orc.uniform(512 * 77) == orc.uniform(512 * 77 + 511) != orc.uniform(512 * 78)
+
+
+def test_stream_layout_keeps_large_event_ids_and_purposes_apart(orc):
+    # event ids use both counter words; the purpose sits above bit 28 of the
+    # high word, so events below 2^60 never share a stream with another
+    # purpose of another event
+    for hi_bits in (24, 26, 27):
+        ev = 1 << (32 + hi_bits)
+        for purpose in (1, 2, 3, 4):
+            assert orc.normals3(7, ev, 0, 5, 6) != orc.normals3(7, 0, purpose, 5, 6)
+            assert orc.normals3(7, ev * purpose, 0, 5, 6) != orc.normals3(7, 0, purpose, 5, 6)
+    assert orc.normals3(7, (1 << 60) - 1, 0, 5, 6) != orc.normals3(7, (1 << 60) - 1, 1, 5, 6)

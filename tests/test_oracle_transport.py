@@ -262,3 +262,65 @@ def test_induced_charge_on_the_collecting_surface(orc):
     assert r.status == 0
     assert r.induced[-1] == pytest.approx(pts[:, 2].sum() / H, rel=1e-12)
     assert len(r.induced) == r.n_steps
+
+
+def test_photon_cloud_starts_at_its_absorption_depth(orc):
+    # The absorption depth is measured from the entrance (back) surface, so
+    # in this frame (z from the collecting surface) the cloud starts at
+    # z = H - depth; with sigma = 0 every pair sits exactly there.
+    P = _params(orc, thickness=100.0, max_steps=0)
+    ev = dict(seed=5, event_id=1, kind=W.PHOTON, energy_keV=3.0, n_pairs=40, depth_um=30.0,
+              x_um=2.0, y_um=-3.0, sigma_um=0.0)
+    r = orc.run_event(P, ev)
+    assert r.status == orc.EMAXSTEPS and r.n_steps == 0
+    assert np.array_equal(r.pos, np.tile([2.0, -3.0, 70.0], (40, 1)))
+    # a Gaussian cloud around that point (Eq. 2's sigma given directly)
+    r = orc.run_event(P, dict(ev, n_pairs=4000, sigma_um=1.5))
+    m, s = r.pos.mean(axis=0), r.pos.std(axis=0)
+    assert np.all(np.abs(m - [2.0, -3.0, 70.0]) < 4 * 1.5 / math.sqrt(4000))
+    assert np.all(np.abs(s - 1.5) < 0.05)
+
+
+@pytest.mark.parametrize("theta,phi", [(0.0, 0.0), (60.0, 0.0), (45.0, 90.0), (30.0, 225.0)])
+def test_track_runs_inward_from_the_back_surface(orc, theta, phi):
+    # sigma = 0: every pair lies on the segment from the entry point (x0, y0, H)
+    # along (sin t cos p, sin t sin p, -cos t), uniformly over its length
+    # (both species: an electron that started outside would leave through the
+    # back contact before the first step, where a hole would be mirrored)
+    H, L, n = 300.0, 80.0, 4000
+    mob = dict(W.HOLE_MOBILITY, **W.ELECTRON_MOBILITY)
+    P = _params(orc, thickness=H, max_steps=0, species=3, mob=mob)
+    ev = dict(seed=8, event_id=2, kind=W.TRACK, energy_keV=200.0, n_pairs=n, depth_um=0.0,
+              x_um=1.0, y_um=-2.0, sigma_um=0.0, track_len_um=L, theta_deg=theta, phi_deg=phi)
+    r = orc.run_event(P, ev)
+    assert (r.state == orc.ACTIVE).all()
+    assert np.array_equal(r.pos[:n], r.pos[n:])         # a pair's carriers start together
+    assert (r.sign[:n] == 1).all() and (r.sign[n:] == -1).all()
+    t, p = math.radians(theta), math.radians(phi)
+    u = np.array([math.sin(t) * math.cos(p), math.sin(t) * math.sin(p), -math.cos(t)])
+    d = r.pos[:n] - np.array([1.0, -2.0, H])
+    s = d @ u
+    assert np.abs(d - np.outer(s, u)).max() < 1e-9      # on the line
+    assert s.min() >= 0.0 and s.max() <= L              # on the segment, inside the sensor
+    assert abs(s.mean() - L / 2) < 4 * L / math.sqrt(12 * n)
+    assert stats.kstest(s / L, "uniform").pvalue > 1e-4
+
+
+def test_electrons_below_the_collecting_surface_are_mirrored(orc):
+    # Diffusion only, equal constant mobilities: an electron starting just
+    # above z = 0 ends its step at |z0 + dz| (reflected), so the end depths
+    # follow a folded normal: none exactly at 0 and E[z^2] / E[z]^2 = pi / 2
+    # whatever the step's width.  One far hole keeps the event running.
+    mob = dict(W.HOLE_MOBILITY, model=1, mu0_e=480.0, vsat_e=0.95e7, beta_e=1.2)
+    P = _params(orc, thickness=100.0, max_steps=1, species=3, repulsion=0, drift=0, mob=mob)
+    n = 40000
+    xyz = np.zeros((n + 1, 3))
+    xyz[:, 2] = 1e-12
+    xyz[n] = [0.0, 0.0, 50.0]
+    sign = np.concatenate([-np.ones(n), [1]]).astype(np.int8)
+    r = orc.run_event(P, W.explicit_event(xyz, sign, seed=4, event_id=6))
+    assert r.n_steps == 1
+    z = r.pos[:n, 2]
+    assert (z > 0).all()
+    ratio = np.mean(z ** 2) / np.mean(z) ** 2
+    assert ratio == pytest.approx(math.pi / 2, rel=0.02)
