@@ -92,3 +92,19 @@ def test_parameterisation_functions_and_fits():
     assert np.allclose(oracle.fit_alpha_of_t(t, oracle.alpha_of_t(pa, t)), pa, atol=1e-9)
     q = oracle.fit_beta_of_t(t, oracle.beta_of_t(pb, t), [0.3, 1.8, 0.6, 1.0, -0.6])
     assert np.allclose(q, pb, rtol=1e-4, atol=1e-6)
+
+
+def test_weighted_eq10_fit_is_weighted_least_squares():
+    # Rows scaled by w minimise sum w^2 r^2: exact data come back for any
+    # weights, and integer weights equal repeating each point w^2 times
+    pa = [1.5, 2.0, -0.3, 0.02]
+    t = np.linspace(0.2, 20.0, 40)
+    rng = np.random.default_rng(12)
+    w = rng.integers(1, 4, t.size).astype(float)
+    assert np.allclose(oracle.fit_alpha_of_t(t, oracle.alpha_of_t(pa, t), w), pa, atol=1e-9)
+    noisy = oracle.alpha_of_t(pa, t) + rng.normal(0, 0.05, t.size)
+    rep = np.repeat(np.arange(t.size), (w ** 2).astype(int))
+    a = oracle.fit_alpha_of_t(t, noisy, w)
+    b = oracle.fit_alpha_of_t(t[rep], noisy[rep])
+    assert np.allclose(a, b, rtol=1e-9, atol=1e-10)
+    assert not np.allclose(a, oracle.fit_alpha_of_t(t, noisy), rtol=1e-6, atol=1e-8)

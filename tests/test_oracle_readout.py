@@ -137,3 +137,25 @@ def test_noise_is_normal_with_the_stated_width():
     assert np.array_equal(r2["e"], r["e"][:3])
     r3 = oracle.readout(c[:1], [6], [0], 0.0, 10, noise_keV=sigma)
     assert not np.array_equal(r3["e"][0], r["e"][0])
+
+
+def test_fano_count_is_continuous_as_the_factor_vanishes():
+    # F -> 0 must reach the plain count round(E / w), not a value beside it
+    for e in (3.0, 8.0, 17.5, 20.0, 25.0):
+        for ev in range(3):
+            assert oracle.fano_pairs(11, ev, e, 1e-12) == oracle.n_pairs(e)
+
+
+def test_noise_alone_rarely_trips_the_3_sigma_veto():
+    # 40 noise pixels of the 7 x 7 annulus, each above 3 sigma with
+    # probability 0.00135: about 5 % of events are vetoed by noise alone
+    # (a 1 sigma threshold would veto nearly all of them)
+    n_ev, sigma = 400, 0.13
+    c = np.zeros((n_ev, 9, 9), np.int32)
+    c[:, 4, 4] = 5525
+    r = oracle.readout(c, np.full(n_ev, 3), np.arange(n_ev), 20.0, 300, noise_keV=sigma,
+                       veto_factor=3.0)
+    assert (r["cx"] == 4).all() and (r["cy"] == 4).all()
+    p = 1 - (1 - stats.norm.sf(3.0)) ** 40
+    k = int(r["vetoed"].sum())
+    assert abs(k - p * n_ev) < 5 * math.sqrt(n_ev * p * (1 - p)), (k, p * n_ev)
