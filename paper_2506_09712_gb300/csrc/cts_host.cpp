@@ -107,6 +107,7 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
     const double w = W / grid;
     int iblock = 0;
     int64_t pfl = 0;
+    int64_t reserved = 0;  // partial-sum floats of the tiles split so far
     struct Piece { int t, j0, j1, k, ns; };
     std::vector<Piece> pieces;
     for (size_t ti = 0; ti < tiles.size(); ++ti) {
@@ -120,7 +121,12 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
                           : f < 0.9375 ? w / 16.0 : f < 0.96875 ? w / 32.0 : w / 64.0;
       int ns = (int)std::max(1.0, std::ceil((double)t.ni * t.n / target));
       ns = std::min({ns, std::max(1, t.n / kPlanDynMinJ), kPlanDynMaxPieces});
-      if (ns > 1 && pfl + (int64_t)3 * tile_i > partial_cap) ns = 1;
+      // a split tile needs its own 3 * tile_i partial sums: run it whole once
+      // the buffer is spoken for
+      if (ns > 1) {
+        if (reserved + (int64_t)3 * tile_i > partial_cap) ns = 1;
+        else reserved += (int64_t)3 * tile_i;
+      }
       for (int k = 0; k < ns; ++k) {
         int j0 = (int)((int64_t)t.n * k / ns) & ~3, j1 = k + 1 == ns ? t.n : (int)((int64_t)t.n * (k + 1) / ns) & ~3;
         if (k > 0) j0 = pieces.back().j1;

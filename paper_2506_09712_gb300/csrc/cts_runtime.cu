@@ -542,6 +542,11 @@ int upload_units(sim_t* s, bool allow_split, bool slot_major = false) {
     s->err = "unit plan does not fit the unit buffer";
     return SIM_EINVAL;
   }
+  if (pfl > s->partial_cap) {
+    // the kernels would write partial sums past their buffer
+    s->err = "unit plan exceeds the partial-sum buffer";
+    return SIM_ECUDA;
+  }
   const int n = (int)s->plan.size();
   std::vector<SlotGeom> geom(s->S);
   for (int k = 0; k < s->S; ++k) {
@@ -1491,7 +1496,8 @@ int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, in
   int64_t pfl = 0;
   const int32_t nh = n_h, ne = n_e;
   if (plan_units(&nh, &ne, 1, t->tile_i, t->grid, t->ph.repulsion != 0, kMaxUnits,
-                 t->partial_cap, &plan, &begin, &pfl, t->ph.repulsion != 0 && t->dynamic) != 0)
+                 t->partial_cap, &plan, &begin, &pfl, t->ph.repulsion != 0 && t->dynamic) != 0 ||
+      pfl > t->partial_cap)
     return SIM_EINVAL;
   int rc = SIM_OK;
   cudaError_t e = cudaSuccess;

@@ -460,3 +460,37 @@ def test_autotune_cache_file_roundtrip(tmp_path):
     bad.write_text("cts-variant-table 1\nGPU X\n11 2\n0 3\n5 99\n")
     assert L.cts_variant_table_load(str(bad).encode(), b"GPU X", 11, m2.ctypes.data_as(p64),
                                     v2.ctypes.data_as(p32), 8, C.byref(n)) == -2
+
+
+@pytest.mark.parametrize("mode", [2, 3])
+def test_dynamic_plans_keep_partial_sums_inside_their_buffer(lib, mode):
+    # split tiles own disjoint 3 * tile_i regions of the FP64 partial-sum
+    # buffer; a plan must never place one beyond the buffer it is given
+    tile = 512
+    for cap in (0, 3 * tile, 3 * tile * 5, 3 * tile * 40):
+        rc, units, begin, pfl = cts.cts_plan_units([5525] * 16, [0] * 16, tile, 608,
+                                                   allow_split=mode, partial_cap=cap)
+        assert rc == 0 and pfl <= cap
+        assert _check_cover(units, [5525] * 16, [0] * 16)
+        split = units[units[:, 7] > 1]
+        regions = {}
+        for u in split:
+            assert 0 <= u[9] and u[9] + 3 * tile <= cap
+            regions.setdefault((u[0], u[1], u[2]), set()).add((u[8], u[9]))
+        # one (combine counter, region) per tile, different tiles never share one
+        assert all(len(v) == 1 for v in regions.values())
+        owners = [next(iter(v)) for v in regions.values()]
+        assert len({o[1] for o in owners}) == len(owners) == len({o[0] for o in owners})
+
+
+def test_whole_tile_plan_is_balanced_longest_first(lib):
+    # allow_split = 0 deals whole tiles, longest first, to the least loaded
+    # CTA: no CTA ends above the mean load plus one tile (list scheduling)
+    n_h, n_e, tile, grid = [5525, 829, 3000, 1381, 2210, 4834], [0] * 6, 512, 8
+    rc, units, begin, pfl = cts.cts_plan_units(n_h, n_e, tile, grid, allow_split=0)
+    assert rc == 0 and pfl == 0 and np.all(units[:, 7] == 1)
+    assert _check_cover(units, n_h, n_e)
+    cost = units[:, 3] * (units[:, 5] - units[:, 4])
+    load = np.array([cost[begin[g]:begin[g + 1]].sum() for g in range(grid)])
+    assert load.max() <= cost.sum() / grid + cost.max()
+    assert np.count_nonzero(load) == grid
