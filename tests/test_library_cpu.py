@@ -322,6 +322,21 @@ def test_ggd_fits_match_the_oracle():
     qo = oracle.fit_beta_of_t(t, yb, start)
     cost = lambda p: ((yb - oracle.beta_of_t(p, t)) ** 2).sum()
     assert cost(q) == pytest.approx(cost(qo), rel=1e-4)
+    # with per-point sigma both minimise the weighted cost, and the weighted
+    # optimum differs from the unweighted one
+    sg = np.where(t < 6.0, 0.002, 0.02)
+    ys = oracle.beta_of_t(pb, t) + sg * rng.standard_normal(t.size)
+    qs = cts.cts_fit_beta_t(t, ys, start, sg)
+    qso = oracle.fit_beta_of_t(t, ys, start, sg)
+    wcost = lambda p: (((ys - oracle.beta_of_t(p, t)) / sg) ** 2).sum()
+    assert wcost(qs) == pytest.approx(wcost(qso), rel=1e-4)
+    q_unw = cts.cts_fit_beta_t(t, ys, start)
+    assert wcost(qs) < wcost(q_unw) * (1 - 1e-3)
+    # from the unweighted optimum every step toward the weighted one raises
+    # the unweighted cost: only a fit that accepts steps by the weighted cost
+    # gets there
+    q2 = cts.cts_fit_beta_t(t, ys, q_unw, sg)
+    assert wcost(q2) == pytest.approx(wcost(qso), rel=1e-4)
     for tt in (0.5, 3.0, 12.0):
         a1, b1 = cts.cts_ggd_params_at(pa, pb, tt)
         assert a1 == pytest.approx(float(oracle.alpha_of_t(pa, tt)), rel=1e-14)
