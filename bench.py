@@ -58,6 +58,8 @@ def parse_args():
                     help="pick the kernel variant per resident-work bucket first (untimed)")
     ap.add_argument("--no-extras", action="store_true", help="skip plain/serving/oracle legs")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--large-n-steps", type=int, default=24,
+                    help="steps of the 200 keV track leg (0: run every event to the end)")
     return ap.parse_args()
 
 
@@ -154,19 +156,36 @@ def oracle_rate(workload: str, seconds: float, steps: int = 0):
     r = oracle.run_event(P, ev)
     dt = time.perf_counter() - t0
     return {"value": r.interactions / dt, "unit": UNIT, "cores": oracle.max_threads(),
-            "kind": "oracle", "seconds": dt, "interactions": r.interactions, "steps": steps,
+            "kind": "oracle", "seconds": dt, "interactions": r.interactions,
+            "steps": r.n_steps, "step_cap": steps,
             "sample": f"event 0 of {workload}: its first {r.n_steps} time steps "
                       f"({r.interactions} pair interactions), FP64, OpenMP over carriers"}
+
+
+def workload_config(workload: str, n_events: int, world: int) -> dict:
+    """The workload keys of the JSON line's config, the same for both arms."""
+    import workloads as W
+    p = W.preset(workload)
+    cfg = {"workload": workload, "events_per_gpu": n_events,
+           "energy_keV": p.get("energies", [[None]])[0][0],
+           "thickness_um": p["sensor"]["thickness_um"],
+           "bias_V": p["sensor"]["bias_V"], "dt_ps": p["sensor"]["dt_ps"],
+           "grid": f'{p["sensor"]["grid_n"]}x{p["sensor"]["grid_n"]}',
+           "parallelism": f"event-sharded x{world}"}
+    if p.get("energies") and len(p["energies"]) == 1:
+        cfg["carriers_per_event"] = int(round(p["energies"][0][0] * 1000 / 3.62))
+    return cfg
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
+    import workloads as W
     per_step = max(2.0, min(args.cpu_seconds, 150.0 / max(args.steps + args.warmup, 1)))
     rates, secs, steps, r = [], [], 0, None
     for k in range(args.warmup + args.steps):
         r = oracle_rate(args.workload, per_step, steps)
-        steps = r["steps"]
+        steps = r["step_cap"]
         if k >= args.warmup:
             rates.append(r["value"])
             secs.append(r["seconds"])
@@ -176,8 +195,10 @@ def run_reference(args, rank, world):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * total_s / max(len(secs), 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload,
-                       "reference": "FP64 CPU oracle on the host cores (no GPU)"},
+            "config": dict(workload_config(args.workload,
+                                           args.events or W.preset(args.workload)["n_events"],
+                                           world),
+                           reference="FP64 CPU oracle on the host cores (no GPU)"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"],
                              "kind": "oracle", "sample": r["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -260,6 +281,17 @@ def serving_leg(cts, W, torch, device):
         out["saturation_events_per_s"] = sat
 
         out["at_0p7_saturation"] = _offered(sim, W, name, 0.7 * sat, 160)
+    # the plain one-event-per-launch path on the first 24 of the same events
+    with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_PLAIN,
+                       device=device) as plain:
+        sample = evs[:24]
+        plain.run(sample[:1])
+        t0 = time.perf_counter()
+        plain.run(sample)
+        plain_eps = len(sample) / (time.perf_counter() - t0)
+    out["plain_events_per_s"] = plain_eps
+    out["plain_sample"] = f"the first {len(sample)} of the saturation run's events, PLAIN mode"
+    out["served_over_plain"] = sat / plain_eps
     with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_SERVE, device=device,
                        max_slots=256, queue_capacity=64) as sim:
         out["at_2kHz_bounded_queue"] = _offered(sim, W, name, p["rate_hz"], 400)
@@ -268,14 +300,17 @@ def serving_leg(cts, W, torch, device):
 
 def large_n_leg(cts, W, torch, device, stream, steps: int = 24):
     """The 16 straight 200 keV electron tracks (2 x 55 250 carriers each, both
-    species, 5 ps steps), all resident, for their first `steps` fused steps:
-    the pair kernel's rate at the largest event size."""
+    species, 5 ps steps), all resident: the pair kernel's rate at the largest
+    event size.  steps > 0 times the first `steps` fused steps (the densest
+    window: every carrier still active); steps = 0 runs every event to the
+    end (about 2 600 steps) and adds events/s."""
     name = "track_200keV_320um"
     p = W.preset(name)
-    p["sensor"]["max_steps"] = steps
+    if steps:
+        p["sensor"]["max_steps"] = steps
     evs = W.make_events(name)
     out = {"workload": name, "events": len(evs), "carriers_per_event": 2 * p["n_pairs"],
-           "steps": steps}
+           "window": f"first {steps} steps" if steps else "whole simulation"}
     with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_BATCHED, device=device,
                        max_slots=len(evs), time_launches=1, stream=stream.cuda_stream) as sim:
         for timed in (False, True):
@@ -293,10 +328,14 @@ def large_n_leg(cts, W, torch, device, stream, steps: int = 24):
         ms = e0.elapsed_time(e1)
         kms = s1["step_kernel_ms"] - s0["step_kernel_ms"]
         inter = sum(r["interactions"] for r in res)
+        n_steps = max(int(r["n_steps"]) for r in res)
         out.update({"interactions_per_s": inter / (ms * 1e-3),
                     "step_kernel_tflops": FLOPS_PER_PAIR * inter / (kms * 1e-3) / 1e12,
-                    "ms_per_step": ms / steps,
+                    "kernel_share": kms / ms, "ms": ms, "steps": n_steps,
+                    "ms_per_step": ms / n_steps,
                     "statuses": sorted({int(r["status"]) for r in res})})
+        if not steps:
+            out["events_per_s"] = len(evs) / (ms * 1e-3)
     return out
 
 
@@ -552,32 +591,29 @@ def run_ours(args, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "events_per_gpu": n_ev,
-                       "energy_keV": p.get("energies", [[None]])[0][0],
-                       "thickness_um": p["sensor"]["thickness_um"],
-                       "bias_V": p["sensor"]["bias_V"], "dt_ps": p["sensor"]["dt_ps"],
-                       "grid": f'{p["sensor"]["grid_n"]}x{p["sensor"]["grid_n"]}',
-                       "positions": "f64", "pair_field": "f32 + Kahan",
-                       "l2": "flushed (256 MiB write) before every timed step",
-                       "parallelism": f"event-sharded x{world}",
-                       "variant": st["variant"],
-                       "variant_table": table},
+            "config": dict(workload_config(args.workload, n_ev, world),
+                           positions="f64", pair_field="f32 + Kahan",
+                           l2="flushed (256 MiB write) before every timed step",
+                           variant=st["variant"], variant_table=table),
             "events_per_s": events_per_s,
             "roofline": roof, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
             "statuses_ok": all(s == 0 for s in statuses)}
-    if p.get("energies") and len(p["energies"]) == 1:
-        line["config"]["carriers_per_event"] = int(round(p["energies"][0][0] * 1000 / 3.62))
 
     if not args.no_extras and world == 1:
-        # the plain one-event-per-launch path on the same GPU (>= 5x target)
+        # the plain one-event-per-launch path on the same GPU (>= 5x target):
+        # 8 events of the same batch, one at a time
         with cts.Simulator(p["sensor"], p["mobility"], mode=cts.CTS_MODE_PLAIN,
                            device=local) as plain:
-            sample = events[:2]
+            sample = events[:8]
             plain.run(sample[:1])
             t0 = time.perf_counter()
-            plain.run(sample)
+            pres = plain.run(sample)
             plain_eps = len(sample) / (time.perf_counter() - t0)
-        line["plain"] = {"events_per_s": plain_eps, "sample": "2 events, PLAIN mode",
+        line["plain"] = {"events_per_s": plain_eps,
+                         "sample": f"the first {len(sample)} events of {args.workload}, "
+                                   f"PLAIN mode",
+                         "mean_steps_sample": float(np.mean([r["n_steps"] for r in pres])),
+                         "mean_steps_batch": float(np.mean([r["n_steps"] for r in res])),
                          "batched_over_plain": events_per_s / plain_eps}
         try:
             line["serving"] = serving_leg(cts, W, torch, local)
@@ -642,7 +678,7 @@ def run_ours(args, rank, world, local):
         except Exception as e:  # reported, never fatal for the bench line
             line["mip"] = {"error": repr(e)}
         try:
-            big = large_n_leg(cts, W, torch, local, stream)
+            big = large_n_leg(cts, W, torch, local, stream, args.large_n_steps)
             big["frac"] = big["step_kernel_tflops"] / peak_tflops
             line["large_n"] = big
         except Exception as e:  # reported, never fatal for the bench line

@@ -319,12 +319,12 @@ int sim_debug_trace_step(sim_t* sim, uint64_t* out, int32_t max_ctas, int32_t* n
 /* Allocation-free pair field, for callers that cannot allocate device
  * memory (they work inside another framework's memory pool or under a fixed
  * device budget, or must avoid the device-wide synchronisation of cudaMalloc
- * and cudaFree).  The paper has no counterpart: it is a packaging of the
- * Eq. 4 field kernel.  Inputs dev_x, dev_y, dev_z: n_h holes followed by n_e
- * electrons, FP32 positions in um, caller-owned device memory.  Output
- * dev_E: 3 * (n_h + n_e) floats, Ex of every carrier, then Ey, then Ez
- * (V/um), caller-owned device memory.  eps_r: relative permittivity;
- * softening_um: Plummer length (0 selects 1e-6 um).  Work is queued on
+ * and cudaFree).  The paper has no counterpart.  Inputs dev_x, dev_y,
+ * dev_z: n_h holes followed by n_e electrons, FP32 positions in um,
+ * caller-owned device memory.  Output dev_E: 3 * (n_h + n_e) floats, Ex
+ * of every carrier, then Ey, then Ez (V/um), caller-owned device memory.
+ * eps_r: relative permittivity; softening_um: Plummer length (finite;
+ * 0 selects 1e-6 um).  Work is queued on
  * `stream` (a cudaStream_t, NULL = legacy default) and the call returns
  * without waiting for it.
  * It allocates nothing: its working storage is one fixed array compiled into

@@ -168,7 +168,8 @@ int na_setup(int dev, void** addr, int* sms) {
 extern "C" int cts_field_noalloc(const float* dev_x, const float* dev_y, const float* dev_z,
                                  int32_t n_h, int32_t n_e, double eps_r, double softening_um,
                                  float* dev_E, void* stream) {
-  if (n_h < 0 || n_e < 0 || !(eps_r > 0) || !(softening_um >= 0) || !std::isfinite(eps_r))
+  if (n_h < 0 || n_e < 0 || !(eps_r > 0) || !(softening_um >= 0) || !std::isfinite(eps_r) ||
+      !std::isfinite(softening_um))
     return SIM_EINVAL;
   const int64_t n = (int64_t)n_h + n_e;
   if (n > kNaMaxCarriers) return SIM_ENOMEM_BUDGET;  // beyond the fixed scratch

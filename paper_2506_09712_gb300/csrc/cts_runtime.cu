@@ -423,20 +423,30 @@ int place_event(sim_t* s, int slot, EventRec&& r, int64_t base) {
   return SIM_OK;
 }
 
-// Admit queued events while slots and arena space allow (FIFO).
+// Admit queued events while slots and arena space allow (FIFO).  The queue
+// lock is held only to take an event off the queue: placing it (descriptor
+// upload, and for explicit events a stream synchronisation) runs outside it,
+// so sim_submit from other threads never waits behind the device.  Slots and
+// the arena belong to the driving thread (drive_mu).
 int admit(sim_t* s) {
   NvtxRange range("cts admit");
-  std::lock_guard<std::mutex> lk(s->qmu);
-  while (!s->queue.empty()) {
-    if (count_used(s) >= running_limit(s)) break;
-    const int slot = free_slot_index(s);
-    if (slot < 0) break;
-    EventRec& r = s->queue.front();
-    const int64_t n = std::max<int64_t>((int64_t)r.cap_h + r.cap_e, 1);
-    const int64_t base = s->alloc.alloc(n);
-    if (base < 0) break;
-    EventRec rec = std::move(r);
-    s->queue.pop_front();
+  for (;;) {
+    EventRec rec;
+    int slot = -1;
+    int64_t base = -1;
+    {
+      std::lock_guard<std::mutex> lk(s->qmu);
+      if (s->queue.empty()) break;
+      if (count_used(s) >= running_limit(s)) break;
+      slot = free_slot_index(s);
+      if (slot < 0) break;
+      EventRec& r = s->queue.front();
+      const int64_t n = std::max<int64_t>((int64_t)r.cap_h + r.cap_e, 1);
+      base = s->alloc.alloc(n);
+      if (base < 0) break;
+      rec = std::move(r);
+      s->queue.pop_front();
+    }
     const int rc = place_event(s, slot, std::move(rec), base);
     if (rc) return rc;
   }
