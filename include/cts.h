@@ -125,7 +125,11 @@ typedef struct sim_options_t {
   int64_t max_carriers;    /* carrier arena capacity (default: from budget) */
   int64_t hbm_budget_bytes;/* device bytes the handle may allocate (default 1 GiB) */
   int32_t queue_capacity;  /* bound of the admission queue (default 65536) */
-  int32_t variant;         /* pair-kernel variant + 1; 0 = default choice */
+  int32_t variant;         /* pair-kernel variant + 1; 0 = default choice: per
+                              chunk, the symmetric kernel (variant 1) when the
+                              running events hold at least 6.4e8 carrier pairs
+                              (sum of N^2), the per-pair kernel (variant 2)
+                              below that */
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
   int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */
   int32_t time_launches;   /* 1 = time every step-kernel launch with CUDA events */
@@ -217,6 +221,10 @@ typedef struct sim_stats_t {
   int64_t step_kernel_launches; /* launches timed into step_kernel_ms */
   int64_t h2d_bytes;        /* bytes copied host -> device by the library */
   int64_t d2h_bytes;        /* bytes copied device -> host by the library */
+  int32_t symmetric;        /* 1: the variant in use evaluates each unordered pair
+                               once and adds it to both carriers (Newton's third
+                               law); 0: every ordered pair */
+  int32_t reserved;
 } sim_stats_t;
 
 typedef struct sim_t sim_t;
@@ -310,10 +318,15 @@ int sim_debug_trajectory(sim_t* sim, const sim_event_t* ev, int64_t n_steps,
                          int64_t* steps_done);
 
 /* One step of the pair kernel (field only: the staged events do not move)
- * on the events admitted by sim_stage, with a per-CTA trace: out[8g..8g+7] =
- * (SM id, start ns, end ns, pairs, units, ns in unit prologues, ns in pair
- * loops, ns in epilogues) of CTA g, for up to max_ctas CTAs; *n_ctas
- * receives the grid size.  For load-balance and latency studies. */
+ * on the events admitted by sim_stage, with a trace.  Kernels that evaluate
+ * every ordered pair: out[8g..8g+7] = (SM id, start ns, end ns, pairs,
+ * units, ns in unit prologues, ns in pair loops, ns in epilogues) of CTA g,
+ * for up to max_ctas CTAs; *n_ctas receives the grid size.  The symmetric
+ * kernel (sim_stats_t.symmetric): one record per unit, out[8r..8r+7] = (SM
+ * id, ns when the warp took it, ns when it was done, queue position, kind: 0
+ * pair unit / 1 update unit, ns waiting for its inputs, ns working, warp),
+ * up to max_ctas records; *n_ctas receives the records written.  For
+ * load-balance and latency studies. */
 int sim_debug_trace_step(sim_t* sim, uint64_t* out, int32_t max_ctas, int32_t* n_ctas);
 
 /* Allocation-free pair field, for callers that cannot allocate device
@@ -436,11 +449,12 @@ int sim_build_flags(void);
 
 /* Per-launch log of the step kernel, kept while the handle was created with
  * options.time_launches != 0 (at most 1 << 20 entries, oldest dropped).
- * Copies up to `cap` entries, oldest first, as triples (kernel ms from CUDA
- * events around the launch, pair interactions the launch's units cover
+ * Copies up to `cap` entries, oldest first, as quadruples (kernel ms from
+ * CUDA events around the launch, ordered carrier pairs the launch covers
  * including carriers retired since the last compaction, events running in
- * the chunk) into out[3 * cap], writes the count to *n_out and clears the
- * log.  Returns SIM_OK or SIM_EINVAL. */
+ * the chunk, 1 if the symmetric kernel ran and 0 otherwise) into
+ * out[4 * cap], writes the count to *n_out and clears the log.  Returns
+ * SIM_OK or SIM_EINVAL. */
 int sim_debug_launch_log(sim_t* sim, double* out, int32_t cap, int32_t* n_out);
 
 /* Host-side fault injection for the failure-path tests: the next chunk (or

@@ -45,6 +45,41 @@ int cts_plan_units(const int32_t* n_h, const int32_t* n_e, int32_t n_slots, int3
                    cts_unit_t* out, int32_t* n_out, int32_t* cta_begin,
                    int64_t* partial_floats);
 
+/* The symmetric pair kernel's plan of one step (Eq. 4, Sec. 2.1, evaluated
+ * once per unordered pair and added to both carriers: Newton's third law).
+ * Each species range of a slot (n_h[s] holes, n_e[s] electrons; slots with
+ * n_h <= 0 get no work) is cut into tiles of 64 carriers (the last one
+ * shorter); an I block is 4 consecutive tiles of one species.  The pairs are
+ * covered exactly once by the (block b, tile g) combinations with g at or
+ * after b's first tile (same species; within b's own tiles, tile u pairs with
+ * the tiles v > u of the block and with itself) and with every electron tile
+ * g of a hole block b.  A pair unit (kind 0) is a rectangle of them, blocks
+ * [ib0, ib1) of species spec_i x tiles [jt0, jt1) of species spec_j, of one
+ * slot, run by one warp (the kernel skips the combinations below the
+ * diagonal).  It writes one partial field (3 x 64 floats) for every existing
+ * tile of its blocks, at index p_i + (b - ib0) * 4 + u, and for every tile of
+ * its J range, at p_j + (g - jt0).  Pair units are listed slot by slot,
+ * longest first within a slot; duty marks the first of each slot.  An update
+ * unit (kind 1) covers the slot's tiles [jt0, jt1) (slot-local, holes then
+ * electrons; at most 64 update units a slot); it waits until each tile's
+ * lcnt partials are written, then sums them and moves the tile's carriers;
+ * npair counts the slot's pair units.  A slot's update units follow the pair
+ * units of the next 32 slots (or the end of the list).  Tiles are listed slot by slot, holes then
+ * electrons; a tile's field is the sum of the partials lists[lptr .. lptr +
+ * lcnt), in unit order.  units has room for max_units entries, tiles for
+ * tiles_cap, lists for lists_cap; *n_partials receives the number of partial
+ * fields.  Returns 0, -1 for bad arguments, -2 if a capacity is too small. */
+typedef struct cts_sym_unit_t {
+  int32_t slot, spec_i, spec_j, ib0, ib1, jt0, jt1, p_i, p_j, duty, kind, npair;
+} cts_sym_unit_t;
+typedef struct cts_sym_tile_t {
+  int32_t slot, spec, tile, n, lptr, lcnt;
+} cts_sym_tile_t;
+int cts_plan_sym(const int32_t* n_h, const int32_t* n_e, int32_t n_slots, int32_t max_units,
+                 cts_sym_unit_t* units, int32_t* n_units, cts_sym_tile_t* tiles,
+                 int32_t tiles_cap, int32_t* n_tiles, int32_t* lists, int64_t lists_cap,
+                 int64_t* n_partials);
+
 /* First-fit carrier arena of the scheduler, for tests: replays n_ops
  * operations (size > 0: allocate size entries and write the offset, or -1 if
  * it does not fit, to result[k]; size < 0: free the block allocated by

@@ -104,7 +104,8 @@ class sim_stats_t(C.Structure):
                 ("chunks", C.c_int64), ("queue_depth", C.c_int64), ("rejected", C.c_int64),
                 ("sm_count", C.c_int32), ("variant", C.c_int32), ("device_ms", C.c_double),
                 ("step_kernel_ms", C.c_double), ("step_kernel_launches", C.c_int64),
-                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+                ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
+                ("symmetric", C.c_int32), ("reserved", C.c_int32)]
 
 
 class cts_unit_t(C.Structure):
@@ -121,7 +122,8 @@ EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_e
             "cts_fit_ggd", "cts_fit_alpha_t", "cts_fit_beta_t", "cts_ggd_params_at",
             "cts_variant_table_save", "cts_variant_table_load",
             "sim_set_variants",
-            "sim_get_variants", "sim_autotune", "sim_reset", "cts_field_noalloc", "cts_plan_units", "cts_arena_replay",
+            "sim_get_variants", "sim_autotune", "sim_reset", "cts_field_noalloc", "cts_plan_units", "cts_plan_sym",
+            "cts_arena_replay",
             "cts_estimate_steps"]
 
 _lib = None
@@ -189,6 +191,8 @@ def load(build_if_missing: bool = True):
                               C.c_void_p],
         "cts_plan_units": [P(i32), P(i32), i32, i32, i32, i32, i32, i64, P(cts_unit_t), P(i32),
                            P(i32), P(i64)],
+        "cts_plan_sym": [P(i32), P(i32), i32, i32, C.c_void_p, P(i32), C.c_void_p, i32, P(i32),
+                         P(i32), i64, P(i64)],
         "cts_arena_replay": [i64, P(i64), i32, P(i64)],
         "cts_estimate_steps": [d, d, d, d, d, d, d, d],
     }
@@ -465,9 +469,10 @@ def sim_debug_fma_peak(device=0, packed=True):
 
 
 def sim_debug_launch_log(h, cap=1 << 20):
-    """Per-launch (kernel ms, pair interactions covered, events running) rows
-    of the step kernel since the last call (handle made with time_launches)."""
-    out = np.zeros((cap, 3), dtype=np.float64)
+    """Per-launch (kernel ms, carrier pairs covered, events running, 1 if the
+    symmetric kernel ran) rows of the step kernel since the last call (handle
+    made with time_launches)."""
+    out = np.zeros((cap, 4), dtype=np.float64)
     n = C.c_int32(0)
     _check(load().sim_debug_launch_log(h, out.ctypes.data_as(C.POINTER(C.c_double)), int(cap),
                                        C.byref(n)), "sim_debug_launch_log")
@@ -539,6 +544,32 @@ def cts_plan_units(n_h, n_e, tile_i, grid, allow_split=1, max_units=65536,
         return rc, None, None, 0
     raw = np.frombuffer(out, dtype=np.int32, count=n.value * 10).reshape(-1, 10)
     return rc, raw.astype(np.int64), begin, pf.value
+
+
+SYM_UNIT_FIELDS = ("slot", "spec_i", "spec_j", "ib0", "ib1", "jt0", "jt1", "p_i", "p_j", "duty",
+                   "kind", "npair")
+SYM_TILE_FIELDS = ("slot", "spec", "tile", "n", "lptr", "lcnt")
+
+
+def cts_plan_sym(n_h, n_e, max_units=65536):
+    """The symmetric kernel's plan of one step: (rc, units[n, 12], tiles[m, 6],
+    lists[L], n_partials); columns as SYM_UNIT_FIELDS and SYM_TILE_FIELDS."""
+    n_h = np.ascontiguousarray(n_h, dtype=np.int32); n_e = np.ascontiguousarray(n_e, dtype=np.int32)
+    per_slot = [(max(a, 0) + 63) // 64 + (max(b, 0) + 63) // 64 for a, b in zip(n_h, n_e)]
+    tiles_cap = int(sum(per_slot)) + 1
+    units = np.zeros((max_units, len(SYM_UNIT_FIELDS)), dtype=np.int32)
+    tiles = np.zeros((tiles_cap, 6), dtype=np.int32)
+    # a tile's list holds at most one I and one J partial per unit of its slot
+    lists_cap = max(1, int(sum(t * (2 * t + 16) for t in per_slot)))
+    lists = np.zeros(lists_cap, dtype=np.int32)
+    nu, nt, npart = C.c_int32(0), C.c_int32(0), C.c_int64(0)
+    rc = load().cts_plan_sym(_ptr(n_h, C.c_int32), _ptr(n_e, C.c_int32), n_h.size, max_units,
+                             units.ctypes.data, C.byref(nu), tiles.ctypes.data, tiles_cap,
+                             C.byref(nt), _ptr(lists, C.c_int32), lists_cap, C.byref(npart))
+    if rc != 0:
+        return rc, None, None, None, 0
+    return (rc, units[:nu.value].astype(np.int64), tiles[:nt.value].astype(np.int64),
+            lists[:int(tiles[:nt.value, 5].sum())].copy(), npart.value)
 
 
 def cts_arena_replay(capacity, ops):

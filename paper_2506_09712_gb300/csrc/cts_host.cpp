@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -202,6 +203,142 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
   while (next_cta <= grid) (*cta_begin)[next_cta++] = (int32_t)out->size();
   if ((int64_t)out->size() > max_units) return -2;
   *partial_floats = pfl;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric planner.  Each unordered pair of carriers of an event is one
+// term of Eq. 4 for both carriers (Newton's third law), so a step needs
+// N(N-1)/2 pair evaluations.  With tiles of 64 carriers per species range and
+// I blocks of 4 tiles, the pairs are covered exactly once by the (block b,
+// tile g) combinations with
+//   same species:  g >= first tile of b (tiles of b itself: the pairs of
+//                  tile u < g of the block, and tile g = u with itself),
+//   b holes, g electrons: every g,
+// and a unit is a rectangle blocks [ib0, ib1) x tiles [jt0, jt1) of them (the
+// kernel skips combinations of a rectangle below the diagonal).  Every unit
+// writes one partial field per tile of its blocks and per tile of its J
+// range; a tile's field is the sum of its partials in unit order.
+// ---------------------------------------------------------------------------
+void sym_shape(int ntiles, int* rb, int* rj) {
+  // small events: short units, so that each step of an event is spread over
+  // many warps; large events: fewer, larger units (fewer partial fields)
+  if (ntiles <= 160) {
+    *rb = 1;
+    *rj = 8;
+  } else if (ntiles <= 640) {
+    *rb = 2;
+    *rj = 16;
+  } else {
+    *rb = 8;
+    *rj = 16;
+  }
+}
+
+int plan_sym(const int32_t* n_h, const int32_t* n_e, int n_slots, int max_units, SymPlan* out) {
+  out->units.clear();
+  out->tiles.clear();
+  out->lists.clear();
+  out->slot_tile0.assign((size_t)std::max(n_slots, 0), -1);
+  out->slot_ntiles.assign((size_t)std::max(n_slots, 0), 0);
+  out->n_partials = 0;
+  if (n_slots < 0 || max_units <= 0) return -1;
+  constexpr int T = kSymPlanTile, B = kSymPlanTpb;
+  std::vector<int32_t> th_of((size_t)n_slots, 0);
+  std::vector<std::vector<SymUnitPlan>> upd;   // update units of each planned slot
+  for (int s = 0; s < n_slots; ++s) {
+    const int nh = std::max(n_h[s], 0), ne = std::max(n_e[s], 0);
+    if (nh <= 0) continue;  // an event with no hole is finished
+    const int th = (nh + T - 1) / T, te = (ne + T - 1) / T;
+    th_of[s] = th;
+    out->slot_tile0[s] = (int32_t)out->tiles.size();
+    out->slot_ntiles[s] = th + te;
+    for (int spec = 0; spec < 2; ++spec) {
+      const int n = spec ? ne : nh, nt = spec ? te : th;
+      for (int t = 0; t < nt; ++t)
+        out->tiles.push_back(SymTilePlan{s, spec, t, std::min(T, n - T * t), 0, 0});
+    }
+    int rb, rj;
+    sym_shape(th + te, &rb, &rj);
+    std::vector<SymUnitPlan> su;
+    std::vector<int64_t> work;
+    auto rows = [&](int spec_i, int nti, int spec_j, int ntj, bool same) {
+      const int nb = (nti + B - 1) / B;
+      for (int b0 = 0; b0 < nb; b0 += rb) {
+        const int b1 = std::min(b0 + rb, nb);
+        for (int g = same ? b0 * B : 0; g < ntj; g += rj) {
+          const int g1 = std::min(g + rj, ntj);
+          int64_t w = 0;  // tile pairs evaluated
+          for (int b = b0; b < b1; ++b) {
+            const int lo = same ? std::max(g, b * B) : g;
+            w += (int64_t)std::max(g1 - lo, 0) * std::min(B, nti - b * B);
+          }
+          su.push_back(SymUnitPlan{s, spec_i, spec_j, b0, b1, g, g1, 0, 0, 0, 0, 0});
+          work.push_back(w);
+        }
+      }
+    };
+    rows(0, th, 0, th, true);
+    if (te > 0) {
+      rows(0, th, 1, te, false);
+      rows(1, te, 1, te, true);
+    }
+    // the slot's pair units longest first; its first unit does the
+    // bookkeeping of a launch's first step
+    std::vector<int> order(su.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    for (size_t k = 0; k < order.size(); ++k) {
+      SymUnitPlan u = su[order[k]];
+      u.duty = k == 0;
+      u.p_i = (int32_t)out->n_partials;
+      out->n_partials += (int64_t)(u.ib1 - u.ib0) * B;
+      u.p_j = (int32_t)out->n_partials;
+      out->n_partials += u.jt1 - u.jt0;
+      out->units.push_back(u);
+    }
+    // update units: a few tiles each (at least 2, at most 64 units a slot)
+    const int nt = th + te;
+    const int tu = std::max(kSymPlanUpdateTiles, (nt + 63) / 64);
+    upd.emplace_back();
+    for (int t = 0; t < nt; t += tu)
+      upd.back().push_back(SymUnitPlan{s, 0, 0, 0, 0, t, std::min(t + tu, nt), 0, 0, 0, 1,
+                                       (int32_t)su.size()});
+    // a slot's update units follow the pair units of kSymPlanUpdateLag more
+    // slots, so that its pair work is usually done when they are taken
+    if ((int)upd.size() > kSymPlanUpdateLag) {
+      for (const SymUnitPlan& u : upd.front()) out->units.push_back(u);
+      upd.erase(upd.begin());
+    }
+    if ((int64_t)out->units.size() > max_units) return -2;
+  }
+  for (const auto& us : upd)
+    for (const SymUnitPlan& u : us) out->units.push_back(u);
+  if ((int64_t)out->units.size() > max_units) return -2;
+  if (out->n_partials > INT32_MAX) return -2;
+  // per-tile partial lists, in unit order
+  auto gtile = [&](int slot, int spec, int t) {
+    return out->slot_tile0[slot] + (spec ? th_of[slot] : 0) + t;
+  };
+  auto each = [&](const SymUnitPlan& u, auto&& f) {
+    const int nti = u.spec_i ? out->slot_ntiles[u.slot] - th_of[u.slot] : th_of[u.slot];
+    for (int b = u.ib0; b < u.ib1; ++b)
+      for (int q = 0; q < B && b * B + q < nti; ++q)
+        f(gtile(u.slot, u.spec_i, b * B + q), u.p_i + (b - u.ib0) * B + q);
+    for (int g = u.jt0; g < u.jt1; ++g) f(gtile(u.slot, u.spec_j, g), u.p_j + (g - u.jt0));
+  };
+  for (const SymUnitPlan& u : out->units)
+    if (u.kind == 0) each(u, [&](int t, int) { out->tiles[t].lcnt++; });
+  int64_t acc = 0;
+  for (SymTilePlan& t : out->tiles) {
+    t.lptr = (int32_t)acc;
+    acc += t.lcnt;
+  }
+  out->lists.assign((size_t)acc, -1);
+  std::vector<int32_t> fill(out->tiles.size(), 0);
+  for (const SymUnitPlan& u : out->units)
+    if (u.kind == 0)
+      each(u, [&](int t, int p) { out->lists[(size_t)out->tiles[t].lptr + fill[t]++] = p; });
   return 0;
 }
 
@@ -549,6 +686,33 @@ int cts_plan_units(const int32_t* n_h, const int32_t* n_e, int32_t n_slots, int3
   }
   for (size_t g = 0; g < begin.size(); ++g) cta_begin[g] = begin[g];
   *n_out = (int32_t)units.size();
+  return 0;
+}
+
+int cts_plan_sym(const int32_t* n_h, const int32_t* n_e, int32_t n_slots, int32_t max_units,
+                 cts_sym_unit_t* units, int32_t* n_units, cts_sym_tile_t* tiles,
+                 int32_t tiles_cap, int32_t* n_tiles, int32_t* lists, int64_t lists_cap,
+                 int64_t* n_partials) {
+  if (!n_h || !n_e || !units || !n_units || !tiles || !n_tiles || !lists || !n_partials ||
+      n_slots < 0 || max_units <= 0 || tiles_cap < 0 || lists_cap < 0)
+    return -1;
+  cts::SymPlan plan;
+  const int rc = cts::plan_sym(n_h, n_e, n_slots, max_units, &plan);
+  if (rc != 0) return rc;
+  if ((int64_t)plan.tiles.size() > tiles_cap || (int64_t)plan.lists.size() > lists_cap) return -2;
+  for (size_t k = 0; k < plan.units.size(); ++k) {
+    const cts::SymUnitPlan& u = plan.units[k];
+    units[k] = cts_sym_unit_t{u.slot, u.spec_i, u.spec_j, u.ib0, u.ib1, u.jt0, u.jt1,
+                              u.p_i, u.p_j, u.duty, u.kind, u.npair};
+  }
+  for (size_t k = 0; k < plan.tiles.size(); ++k) {
+    const cts::SymTilePlan& t = plan.tiles[k];
+    tiles[k] = cts_sym_tile_t{t.slot, t.spec, t.tile, t.n, t.lptr, t.lcnt};
+  }
+  for (size_t k = 0; k < plan.lists.size(); ++k) lists[k] = plan.lists[k];
+  *n_units = (int32_t)plan.units.size();
+  *n_tiles = (int32_t)plan.tiles.size();
+  *n_partials = plan.n_partials;
   return 0;
 }
 

@@ -27,6 +27,32 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
                std::vector<int32_t>* cta_begin, int64_t* partial_floats, bool dynamic,
                bool slot_major = false);
 
+// Plan of the symmetric pair kernel (see cts_plan_sym in cts_host.h): units,
+// tiles and the per-tile partial lists of one step of the resident slots.
+constexpr int kSymPlanTile = 64;   // carriers per tile
+constexpr int kSymPlanTpb = 4;     // tiles per I block
+constexpr int kSymPlanUpdateTiles = 1;  // tiles per update unit (at least)
+constexpr int kSymPlanUpdateLag = 32;   // slots of pair units before a slot's update units
+struct SymUnitPlan {
+  // kind 0: pair unit; kind 1: update unit of the slot's tiles [jt0, jt1)
+  // (slot-local numbering, holes then electrons), after its npair pair units
+  int32_t slot, spec_i, spec_j, ib0, ib1, jt0, jt1, p_i, p_j, duty, kind, npair;
+};
+struct SymTilePlan {
+  int32_t slot, spec, tile, n, lptr, lcnt;
+};
+struct SymPlan {
+  std::vector<SymUnitPlan> units;
+  std::vector<SymTilePlan> tiles;
+  std::vector<int32_t> lists;         // partial indices, tile by tile
+  std::vector<int32_t> slot_tile0;    // global index of a slot's first tile (-1: none)
+  std::vector<int32_t> slot_ntiles;   // tiles of the slot
+  int64_t n_partials = 0;             // partial tiles the units write
+};
+// Unit shape (I blocks x J tiles) of a slot with `ntiles` tiles.
+void sym_shape(int ntiles, int* rb, int* rj);
+int plan_sym(const int32_t* n_h, const int32_t* n_e, int n_slots, int max_units, SymPlan* out);
+
 // Fano-distributed carrier-pair count of one photon (see cts_fano_pairs).
 int fano_pairs(uint64_t seed, uint64_t event_id, double energy_keV, double fano);
 

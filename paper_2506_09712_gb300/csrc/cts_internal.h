@@ -146,6 +146,89 @@ struct Arena {
   int64_t capacity;
 };
 
+// ---- the symmetric pair kernel (Newton's third law) ----------------------
+// Every unordered pair of an event is evaluated once and its term added to
+// both carriers.  Carriers of each species range are cut into tiles of
+// kSymTile; an I block is kSymTpb consecutive tiles of one species (one warp
+// holds its 32 * 2 * kSymTpb carriers in registers).  The pair matrix of a
+// step is covered by the (block b, tile g) combinations with g at or after
+// block b's first tile (same species) or g an electron tile (b a hole
+// block); a pair unit is a rectangle of them: blocks [ib0, ib1) x tiles
+// [jt0, jt1) of one (I species, J species) pair, run by one warp.  It writes
+// one FP32 partial field per tile it touches (kSymTile x 3 floats, at fixed
+// indices) and counts them per tile.  Update units follow the pair units of
+// their slot in the queue: once all of a tile's partials are in, a warp sums
+// them in a fixed order (compensated FP32) and updates the tile's carriers.
+constexpr int kSymTile = 64;        // carriers per tile (32 lanes x 2)
+constexpr int kSymRI = 8;           // i's per lane
+constexpr int kSymTpb = kSymRI / 2; // tiles per I block
+constexpr int kSymBlock = 32 * kSymRI;
+constexpr int kSymMaxRJ = 16;       // J tiles per unit at most (shared-memory sums)
+constexpr int kSymFold = 4;         // J tiles summed in registers before a fold
+constexpr int kSymPartFloats = 3 * kSymTile;  // one tile's partial field
+
+constexpr int kSymIElectrons = 1;   // the unit's I blocks are electrons
+constexpr int kSymJElectrons = 2;   // the unit's J tiles are electrons
+constexpr int kSymDuty = 4;         // the slot's per-step bookkeeping of the launch's first step
+constexpr int kSymOddStep = 8;      // the slot's chunk starts on an odd step
+constexpr int kSymUpdate = 16;      // an update unit (tiles [jt0, jt1) of the slot)
+
+struct alignas(16) SymUnit {
+  int64_t ibase;     // arena index of carrier 0 of the I species range
+  int64_t jbase;     // arena index of carrier 0 of the J species range
+  int32_t slot;
+  int32_t flags;     // kSym* bits
+  int32_t ib0, ib1;  // I blocks (species-local)
+  int32_t jt0, jt1;  // J tiles (species-local); update units: the slot's tiles
+  int32_t ni, nj;    // carriers in the I and J species ranges
+  int32_t pI;        // first I partial: block ib0 + q, tile u -> pI + q * kSymTpb + u
+  int32_t pJ;        // first J partial: tile jt0 + t -> pJ + t
+  int32_t tI, tJ;    // global tile index of species-local tile 0 of I and of J;
+                     // update units: of the slot's tile 0
+  int32_t ntiles;    // tiles of the slot (its step is done when all are updated)
+  int32_t npair;     // pair units of the slot
+  int32_t pad[2];
+};
+static_assert(sizeof(SymUnit) == 80, "symmetric unit descriptor layout");
+
+// A tile of one slot: its carriers and the list of partials that make its field.
+struct alignas(16) SymTile {
+  int64_t off;       // arena index of the tile's first carrier
+  int32_t slot;
+  int32_t spec;      // 0 holes, 1 electrons
+  int32_t n;         // carriers in the tile (<= kSymTile)
+  int32_t lptr;      // first entry of its partial list
+  int32_t lcnt;      // partials in the list
+  int32_t ntiles;    // tiles of its slot
+};
+static_assert(sizeof(SymTile) == 32, "symmetric tile descriptor layout");
+
+// Per-slot values of one step, written once (by the warp that finishes the
+// slot's previous step, or identically by the units of a launch's first
+// step) and read by every unit of the step.
+struct alignas(16) SymStep {
+  double azn[2];     // frame anchors of the next step
+  int32_t nah, nae;  // active carriers of each species
+  int32_t step;      // event-local step
+  int32_t skip;      // 1: the slot runs no pairs at this step
+  float s_off;       // electron frame z anchor minus the hole frame's (FP32)
+  int32_t pad[3];
+};
+static_assert(sizeof(SymStep) == 48, "symmetric step record layout");
+
+struct SymArgs {
+  const SymUnit* units;     // one step's units (replayed for every step of a launch)
+  const int32_t* n_units;   // [1] units per step
+  const SymTile* tiles;     // every tile of every planned slot
+  const int32_t* lists;     // partial indices, per tile (CSR by SymTile.lptr)
+  float* part;              // partials [n][3][kSymTile]
+  int32_t* tile_ctr;        // partials written per tile (returned to 0 by its update)
+  SymStep* rec;             // [K][S]
+  int32_t* ready;           // [K][S]: rec valid
+  int64_t n_part;           // partial fields in the buffer (bounds checks)
+  int32_t n_tiles;          // tiles planned (bounds checks)
+};
+
 struct StepArgs {
   Arena A;
   SlotDev* slots;
@@ -166,6 +249,7 @@ struct StepArgs {
   int32_t fused;             // 1: update positions; 0: write field_out
   double* induced;           // [K][S]: charge induced at each chunk step (e); NULL = off
   double* induced_px;        // [K][S][9]: the same per pixel of the 3 x 3 window; NULL = off
+  SymArgs sym;               // the symmetric kernel's plan and buffers
 };
 
 // ---- kernel launchers (cts_kernels.cu) ----------------------------------
@@ -175,6 +259,7 @@ struct Variant {
   const char* name;
   int ctas_per_sm;  // 0: as many as fit; else a fixed count
   int dynamic;      // 1: guided dynamic queue; 0: static equal shares
+  int sym;          // 1: the symmetric kernel (SymUnit plans, warp-level queue)
 };
 int variant_count();
 Variant variant_info(int v);

@@ -965,6 +965,548 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// The symmetric step kernel: every unordered pair of an event once per step,
+// its term added to both carriers (Newton's third law), one warp per unit.
+// ---------------------------------------------------------------------------
+// A warp holds an I block (32 * RI carriers, i-slot r of lane l = carrier
+// r * 32 + l, so tile u of the block is i-slots 2u and 2u + 1) as duplicated
+// FP32 pairs, and walks the unit's J tiles.  A J tile sits in shared memory
+// as 32 pairs (carrier m, carrier m + 32); in rotation step s lane l takes
+// pair (l + s) mod 32, so its i's meet all 64 carriers of the tile in 32
+// steps, and the J sums move with their pair from lane to lane by shuffle
+// (home again after the 32nd).  Both the i's and the j's accumulate
+// d w, d = r_i - r_j, w = (|d|^2 + eps^2)^(-3/2): the i's field is s_j times
+// their sum, the j's field -s_i times theirs.
+//
+// Shared memory per warp (floats): the staged tile (3 x 32 float2), the J
+// sums of the unit's tiles [kSymMaxRJ][3][64] and the I sums of the current
+// block [3][kSymBlock].
+constexpr int kSymStageFloats = 3 * 64;
+constexpr int kSymWarpFloats = kSymStageFloats + kSymMaxRJ * kSymPartFloats + 3 * kSymBlock;
+
+// The pairs of one (block, tile) combination.  QD = kSymTpb: every i-slot
+// pairs with the tile both ways.  Otherwise tile t = r / 2 of the block pairs
+// both ways if t < qd, with itself (i sums only: every ordered pair of the
+// tile once) if t == qd, not at all if t > qd or t >= vt (tiles past the
+// species' end); QD in [0, kSymTpb) fixes qd at compile time (a full block's
+// own tiles), QD = -1 takes qd and vt at run time.
+template <int RI, int QD>
+__device__ __forceinline__ void sym_tile_pairs(const float2* __restrict__ sx,
+                                               const float2* __restrict__ sy,
+                                               const float2* __restrict__ sz, int lane,
+                                               const float2 (&xi)[RI], const float2 (&yi)[RI],
+                                               const float2 (&zi)[RI], float2 (&aix)[RI],
+                                               float2 (&aiy)[RI], float2 (&aiz)[RI], float2& ajx,
+                                               float2& ajy, float2& ajz, float eps2s, int qd_rt,
+                                               int vt_rt) {
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+  const float2 eps2 = make_float2(eps2s, eps2s);
+  const int src = (lane + 1) & 31;
+  const int qd = QD >= 0 ? QD : qd_rt;
+  const int vt = QD >= 0 ? kSymTpb : vt_rt;
+#pragma unroll 1
+  for (int s = 0; s < 32; ++s) {
+    const int jj = (lane + s) & 31;
+    const float2 xj = sx[jj], yj = sy[jj], zj = sz[jj];
+#pragma unroll
+    for (int r = 0; r < RI; ++r) {
+      const int t = r >> 1;
+      if (t >= vt || t > qd) continue;
+      const float2 dx = __ffma2_rn(xj, m1, xi[r]);
+      const float2 dy = __ffma2_rn(yj, m1, yi[r]);
+      const float2 dz = __ffma2_rn(zj, m1, zi[r]);
+      float2 r2 = __ffma2_rn(dz, dz, eps2);
+      r2 = __ffma2_rn(dy, dy, r2);
+      r2 = __ffma2_rn(dx, dx, r2);
+      const float2 rs = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+      const float2 w = __fmul2_rn(__fmul2_rn(rs, rs), rs);
+      aix[r] = __ffma2_rn(dx, w, aix[r]);
+      aiy[r] = __ffma2_rn(dy, w, aiy[r]);
+      aiz[r] = __ffma2_rn(dz, w, aiz[r]);
+      if (t < qd) {
+        ajx = __ffma2_rn(dx, w, ajx);
+        ajy = __ffma2_rn(dy, w, ajy);
+        ajz = __ffma2_rn(dz, w, ajz);
+      }
+    }
+    ajx.x = __shfl_sync(0xffffffffu, ajx.x, src);
+    ajx.y = __shfl_sync(0xffffffffu, ajx.y, src);
+    ajy.x = __shfl_sync(0xffffffffu, ajy.x, src);
+    ajy.y = __shfl_sync(0xffffffffu, ajy.y, src);
+    ajz.x = __shfl_sync(0xffffffffu, ajz.x, src);
+    ajz.y = __shfl_sync(0xffffffffu, ajz.y, src);
+  }
+}
+
+// Adds the i sums held in registers to the block's sums in shared memory and
+// clears them (every kSymFold tiles: at most 128 terms per register half).
+template <int RI>
+__device__ __forceinline__ void sym_fold_i(float* iacc, int lane, float2 (&aix)[RI],
+                                           float2 (&aiy)[RI], float2 (&aiz)[RI]) {
+#pragma unroll
+  for (int r = 0; r < RI; ++r) {
+    const int c = r * 32 + lane;
+    iacc[c] += aix[r].x + aix[r].y;
+    iacc[kSymBlock + c] += aiy[r].x + aiy[r].y;
+    iacc[2 * kSymBlock + c] += aiz[r].x + aiz[r].y;
+    aix[r] = aiy[r] = aiz[r] = make_float2(0.0f, 0.0f);
+  }
+}
+
+// The values of step k for a slot, computed by the unit itself at the first
+// step of a launch (the same inputs give every unit the same bits).
+__device__ SymStep sym_first_record(const StepArgs& a, const SymUnit& U, SlotDev* S, int k,
+                                    int lane) {
+  int dh = 0, de = 0;
+  for (int kk = lane; kk < k; kk += 32) {
+    dh += __ldcg(a.ret + ((int64_t)kk * a.S + U.slot) * 2 + 0);
+    de += __ldcg(a.ret + ((int64_t)kk * a.S + U.slot) * 2 + 1);
+  }
+  dh = __reduce_add_sync(0xffffffffu, dh);
+  de = __reduce_add_sync(0xffffffffu, de);
+  SymStep R{};
+  R.nah = __ldcg(&S->act_h) - dh;
+  R.nae = __ldcg(&S->act_e) - de;
+  R.step = __ldcg(&S->step0) + k;
+  const int p = R.step & 1;
+  const bool plan_ok = ((((U.flags & kSymOddStep) ? 1 : 0) + k) & 1) == p;
+  if (!plan_ok && lane == 0) atomicOr(a.err, kErrPlan);
+  R.skip = !plan_ok || !__ldcg(&S->running) || R.nah <= 0 || (int64_t)R.step >= a.ph.max_steps;
+  if (!R.skip) {
+    double z0 = 0.0, z1 = 0.0;
+    if (lane == 0) {
+      const double az0 = __ldcg(&S->az[p][0]), az1 = __ldcg(&S->az[p][1]);
+      R.s_off = (float)(az1 - az0);
+      z0 = anchor_next(a.ph, 0, az0);
+      z1 = anchor_next(a.ph, 1, az1);
+    }
+    R.s_off = __shfl_sync(0xffffffffu, R.s_off, 0);
+    R.azn[0] = __shfl_sync(0xffffffffu, z0, 0);
+    R.azn[1] = __shfl_sync(0xffffffffu, z1, 0);
+  }
+  return R;
+}
+
+// Marks steps k .. k_end - 1 of a finished slot as skipped (idempotent).
+__device__ void sym_skip_from(const StepArgs& a, int slot, int k, int k_end, const SymStep& R) {
+  for (int kk = k; kk < k_end; ++kk) {
+    SymStep N = R;
+    N.skip = 1;
+    a.sym.rec[(int64_t)kk * a.S + slot] = N;
+    __threadfence();
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.sym.ready + (int64_t)kk * a.S + slot),
+                 "r"(1)
+                 : "memory");
+  }
+}
+
+// Written by the warp that finished the last tile of step k (lane 0): the
+// slot's values for step k + 1, its per-step bookkeeping, and the flag the
+// units of step k + 1 wait for.
+__device__ void sym_next_record(const StepArgs& a, SlotDev* S, int slot, const SymStep& R, int k,
+                                int k_end) {
+  __threadfence();
+  SymStep N{};
+  N.nah = R.nah - __ldcg(a.ret + ((int64_t)k * a.S + slot) * 2 + 0);
+  N.nae = R.nae - __ldcg(a.ret + ((int64_t)k * a.S + slot) * 2 + 1);
+  N.step = R.step + 1;
+  const int pn = N.step & 1;
+  N.skip = !__ldcg(&S->running) || N.nah <= 0 || (int64_t)N.step >= a.ph.max_steps;
+  if (!N.skip) {
+    const double az0 = __ldcg(&S->az[pn][0]), az1 = __ldcg(&S->az[pn][1]);
+    N.s_off = (float)(az1 - az0);
+    N.azn[0] = anchor_next(a.ph, 0, az0);
+    N.azn[1] = anchor_next(a.ph, 1, az1);
+    if (a.fused) slot_duties(a, S, N.step, pn, N.nah, N.nae, N.azn[0], N.azn[1]);
+    a.sym.rec[(int64_t)(k + 1) * a.S + slot] = N;
+    __threadfence();
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a.sym.ready +
+                                                              (int64_t)(k + 1) * a.S + slot),
+                 "r"(1)
+                 : "memory");
+  } else {
+    sym_skip_from(a, slot, k + 1, k_end, N);
+  }
+}
+
+// The field of one tile (the sum of its partials in list order, FP64) and its
+// carriers' update, by one warp.  The slot's values of step k come from its
+// step record; the warp that counts the slot's last tile of the step writes
+// the record of the next step.
+template <int IND>
+__device__ void sym_tile_update(const StepArgs& a, int gt, int k, int k_end, int lane) {
+  __threadfence();
+  const SymTile T = a.sym.tiles[gt];
+  const int slot = T.slot;
+  SlotDev* S = a.slots + slot;
+  SymStep R;
+  {
+    const SymStep* rp = a.sym.rec + (int64_t)k * a.S + slot;
+    const double2 az = __ldcg(reinterpret_cast<const double2*>(rp));
+    const int4 w0 = __ldcg(reinterpret_cast<const int4*>(rp) + 1);
+    R.azn[0] = az.x;
+    R.azn[1] = az.y;
+    R.nah = w0.x;
+    R.nae = w0.y;
+    R.step = w0.z;
+    R.skip = w0.w;
+  }
+  const float kc = a.ph.f_kc;
+  const int p = R.step & 1;
+  // The list, 32 entries at a time (one per lane); entry l goes to group
+  // l mod 4, each group a compensated FP32 sum in list order, then the
+  // groups in order: a fixed order (the same bits every run), four loads in
+  // flight, and no FP64 (a slow pipe on this part).
+  float sx[2][4], cx[2][4], sy[2][4], cy[2][4], sz[2][4], cz[2][4];
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+#pragma unroll
+    for (int g = 0; g < 4; ++g) sx[h][g] = cx[h][g] = sy[h][g] = cy[h][g] = sz[h][g] = cz[h][g] = 0.0f;
+  for (int l0 = 0; l0 < T.lcnt; l0 += 32) {
+    const int nl = min(32, T.lcnt - l0);
+    const int mine = lane < nl ? __ldg(a.sym.lists + T.lptr + l0 + lane) : -1;
+    for (int l = 0; l < nl; l += 4) {
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int idx = __shfl_sync(0xffffffffu, mine, (l + g) & 31);
+        if (l + g < nl) {
+          const float* src = a.sym.part + (int64_t)idx * kSymPartFloats;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            kahan_add(sx[h][g], cx[h][g], __ldcg(src + c));
+            kahan_add(sy[h][g], cy[h][g], __ldcg(src + kSymTile + c));
+            kahan_add(sz[h][g], cz[h][g], __ldcg(src + 2 * kSymTile + c));
+          }
+        }
+      }
+    }
+  }
+  float fx[2], fy[2], fz[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    float tx = 0.0f, ux = 0.0f, ty = 0.0f, uy = 0.0f, tz = 0.0f, uz = 0.0f;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      kahan_add(tx, ux, sx[h][g] - cx[h][g]);
+      kahan_add(ty, uy, sy[h][g] - cy[h][g]);
+      kahan_add(tz, uz, sz[h][g] - cz[h][g]);
+    }
+    fx[h] = tx - ux;
+    fy[h] = ty - uy;
+    fz[h] = tz - uz;
+  }
+  [[maybe_unused]] double q = 0.0;
+  [[maybe_unused]] double qpx[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int c = lane + 32 * h;
+    if (c < T.n) {
+      const float Ex = kc * fx[h], Ey = kc * fy[h], Ez = kc * fz[h];
+      const int64_t idx = T.off + c;
+      if (a.fused) {
+        if constexpr (IND > 0)
+          q += update_carrier<IND>(a, S, slot, T.spec, idx, R.step, p, k, Ex, Ey, Ez,
+                                   R.azn[T.spec], qpx);
+        else
+          update_carrier<0>(a, S, slot, T.spec, idx, R.step, p, k, Ex, Ey, Ez, R.azn[T.spec]);
+      } else {
+        const int64_t cap = a.A.capacity;
+        a.field_out[idx] = Ex;
+        a.field_out[cap + idx] = Ey;
+        a.field_out[2 * cap + idx] = Ez;
+      }
+    }
+  }
+  if constexpr (IND > 0) {
+    if (a.fused) {
+      add_induced(a, k, slot, q);
+      if constexpr (IND == 2) add_induced_px(a, k, slot, qpx);
+    }
+  }
+  if (lane == 0) a.sym.tile_ctr[gt] = 0;
+  // publish the tile's positions, states and counters before counting it
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) {
+    const int old = atomicAdd(a.tiles_done + (int64_t)k * a.S + slot, 1);
+    if (old + 1 == T.ntiles && k + 1 < k_end) sym_next_record(a, S, slot, R, k, k_end);
+  }
+  __syncwarp();
+}
+
+// Debug trace of the symmetric kernel (a.trace: [0] records written, [1]
+// capacity, records of 8 words from [8]): SM, time pulled, time done, queue
+// position, kind (0 pair, 1 update), ns waiting, ns working, warp.
+__device__ __forceinline__ unsigned long long sym_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ void sym_trace(const StepArgs& a, int qi, int kind, unsigned long long t0,
+                          unsigned long long t1, unsigned long long t2) {
+  const unsigned long long r = atomicAdd(a.trace, 1ull);
+  if (r >= a.trace[1]) return;
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  unsigned long long* o = a.trace + 8 + 8 * r;
+  o[0] = smid;
+  o[1] = t0;
+  o[2] = t2;
+  o[3] = (unsigned long long)qi;
+  o[4] = (unsigned long long)kind;
+  o[5] = t1 - t0;
+  o[6] = t2 - t1;
+  o[7] = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+}
+
+template <int RI, int NT, int IND>
+__global__ void __launch_bounds__(NT, 1) sym_kernel(StepArgs a, int k0, int nk) {
+  static_assert(RI == kSymRI, "the planner's block is 32 * kSymRI carriers");
+  static_assert(kSymTpb == 4, "the block's own tiles are specialised for four tiles");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* wsm = reinterpret_cast<float*>(smem_raw) + (size_t)warp * kSymWarpFloats;
+  float2* sx = reinterpret_cast<float2*>(wsm);
+  float2* sy = sx + 32;
+  float2* sz = sy + 32;
+  float* jacc = wsm + kSymStageFloats;
+  float* iacc = jacc + kSymMaxRJ * kSymPartFloats;
+  const float eps2 = a.ph.f_eps2;
+  const int n_u = __ldcg(a.sym.n_units);
+  const int k_end = k0 + nk;
+  // warps start pulling units in order of their index within the CTA, so
+  // that the first units of a launch spread over every SM
+  if (lane == 0 && warp > 0) {
+    const unsigned long long t0 = sym_now();
+    while (sym_now() - t0 < 400ull * (unsigned long long)warp) {
+    }
+  }
+  __syncwarp();
+  for (;;) {
+    int qi = 0;
+    if (lane == 0) qi = atomicAdd(&a.unit_counter[k0], 1);
+    qi = __shfl_sync(0xffffffffu, qi, 0);
+    if (qi >= n_u * nk) break;
+    const unsigned long long tr0 = (a.trace && lane == 0) ? sym_now() : 0ull;
+    const int kq = qi / n_u, k = k0 + kq;
+    const SymUnit U = a.sym.units[qi - kq * n_u];
+#ifdef CTS_BOUNDS_CHECK
+    {
+      const int64_t cap = a.A.capacity;
+      const bool upd = (U.flags & kSymUpdate) != 0;
+      const bool bad =
+          U.slot < 0 || U.slot >= a.S || k >= kMaxK || U.jt0 < 0 || U.jt1 < U.jt0 ||
+          U.tJ < 0 || U.tJ + U.jt1 > a.sym.n_tiles ||
+          (!upd && (U.ib0 < 0 || U.ib1 < U.ib0 || U.jt1 - U.jt0 > kSymMaxRJ || U.ni < 0 ||
+                    U.nj < 0 || U.ibase < 0 || U.ibase + U.ni > cap || U.jbase < 0 ||
+                    U.jbase + U.nj > cap || U.pI < 0 || U.pJ < 0 ||
+                    (int64_t)U.pJ + (U.jt1 - U.jt0) > a.sym.n_part ||
+                    (int64_t)U.pI + (int64_t)(U.ib1 - U.ib0) * kSymTpb > a.sym.n_part ||
+                    U.tI < 0 || U.tI + U.ib1 * kSymTpb > a.sym.n_tiles + kSymTpb));
+      if (bad) {
+        if (lane == 0) atomicOr(a.err, kErrBounds);
+        break;
+      }
+    }
+#endif
+    SlotDev* S = a.slots + U.slot;
+    SymStep R;
+    if (kq == 0) {
+      R = sym_first_record(a, U, S, k, lane);
+      if (R.skip) {
+        if (lane == 0) sym_skip_from(a, U.slot, k + 1, k_end, R);
+        continue;
+      }
+      // every unit of the slot writes the same record (its tile updates read it)
+      if (lane == 0) a.sym.rec[(int64_t)k * a.S + U.slot] = R;
+      if ((U.flags & kSymDuty) && a.fused && lane == 0)
+        slot_duties(a, S, R.step, R.step & 1, R.nah, R.nae, R.azn[0], R.azn[1]);
+    } else {
+      // the slot's previous step is complete once its record is published;
+      // the units it waits for sit earlier in the queue, so the wait ends
+      bool ok = false;
+      {
+        unsigned long long t0 = 0, tn;
+        if (lane == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (;;) {
+          int v = 0;
+          if (lane == 0)
+            asm volatile("ld.acquire.gpu.global.b32 %0, [%1];"
+                         : "=r"(v)
+                         : "l"(a.sym.ready + (int64_t)k * a.S + U.slot)
+                         : "memory");
+          if (__shfl_sync(0xffffffffu, v, 0)) {
+            ok = true;
+            break;
+          }
+          int late = 0;
+          if (lane == 0) {
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tn));
+            late = tn - t0 > kCountWaitNs;
+            __nanosleep(128);
+          }
+          if (__shfl_sync(0xffffffffu, late, 0)) break;
+        }
+      }
+      if (!ok) {
+        if (lane == 0) atomicOr(a.err, kErrTimeout);
+        break;
+      }
+      const SymStep* rp = a.sym.rec + (int64_t)k * a.S + U.slot;
+      const double2 az = __ldcg(reinterpret_cast<const double2*>(rp));
+      const int4 w0 = __ldcg(reinterpret_cast<const int4*>(rp) + 1);
+      const int4 w1 = __ldcg(reinterpret_cast<const int4*>(rp) + 2);
+      R.azn[0] = az.x;
+      R.azn[1] = az.y;
+      R.nah = w0.x;
+      R.nae = w0.y;
+      R.step = w0.z;
+      R.skip = w0.w;
+      R.s_off = __int_as_float(w1.x);
+      if (R.skip) continue;
+    }
+    if (U.flags & kSymUpdate) {
+      // an update unit: each of its tiles once all of the tile's partials are
+      // in (the pair units writing them sit earlier in the queue, so the
+      // waits end)
+      const unsigned long long tr1 = (a.trace && lane == 0) ? sym_now() : 0ull;
+      bool ok = true;
+      for (int t = U.jt0; t < U.jt1 && ok; ++t) {
+        const int gt = U.tJ + t;
+        if (lane == 0) ok = wait_count_bounded(a.sym.tile_ctr + gt, __ldg(&a.sym.tiles[gt].lcnt));
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        if (ok) sym_tile_update<IND>(a, gt, k, k_end, lane);
+      }
+      if (!ok) {
+        if (lane == 0) atomicOr(a.err, kErrTimeout);
+        break;
+      }
+      if (a.trace && lane == 0) sym_trace(a, qi, 1, tr0, tr1, sym_now());
+      continue;
+    }
+    const unsigned long long tr1 = (a.trace && lane == 0) ? sym_now() : 0ull;
+    const int p = R.step & 1;
+    const float4* __restrict__ sh = a.A.sh[p];
+    const int sI = U.flags & kSymIElectrons ? 1 : 0;
+    const int sJ = U.flags & kSymJElectrons ? 1 : 0;
+    const bool same = sI == sJ;
+    const float offI = sI ? R.s_off : 0.0f, offJ = sJ ? R.s_off : 0.0f;
+    const int nti = (U.ni + kSymTile - 1) / kSymTile;
+    const int nj_t = U.jt1 - U.jt0;
+    if (a.ph.repulsion) {
+      for (int e = lane; e < nj_t * kSymPartFloats; e += 32) jacc[e] = 0.0f;
+      for (int b = U.ib0; b < U.ib1; ++b) {
+        const int bt0 = b * kSymTpb;
+        const int vt = min(kSymTpb, nti - bt0);
+        float2 xi[RI], yi[RI], zi[RI], aix[RI], aiy[RI], aiz[RI];
+#pragma unroll
+        for (int r = 0; r < RI; ++r) {
+          const int ii = b * kSymBlock + r * 32 + lane;
+          const float4 q =
+              ii < U.ni ? __ldcg(sh + U.ibase + ii) : make_float4(kParked, kParked, kParked, 0.0f);
+          xi[r] = make_float2(q.x, q.x);
+          yi[r] = make_float2(q.y, q.y);
+          const float z = q.z + offI;
+          zi[r] = make_float2(z, z);
+          aix[r] = aiy[r] = aiz[r] = make_float2(0.0f, 0.0f);
+        }
+        for (int e = lane; e < 3 * kSymBlock; e += 32) iacc[e] = 0.0f;
+        const int g_first = same ? max(U.jt0, bt0) : U.jt0;
+        // the first tile's positions; later ones are fetched one tile ahead
+        float4 p0 = make_float4(kParked, kParked, kParked, 0.0f), p1 = p0;
+        if (g_first < U.jt1) {
+          const int j0 = g_first * kSymTile + lane;
+          if (j0 < U.nj) p0 = __ldcg(sh + U.jbase + j0);
+          if (j0 + 32 < U.nj) p1 = __ldcg(sh + U.jbase + j0 + 32);
+        }
+        int nf = 0;
+        for (int g = g_first; g < U.jt1; ++g) {
+          __syncwarp();
+          sx[lane] = make_float2(p0.x, p1.x);
+          sy[lane] = make_float2(p0.y, p1.y);
+          sz[lane] = make_float2(p0.z + offJ, p1.z + offJ);
+          __syncwarp();
+          if (g + 1 < U.jt1) {
+            const int j0 = (g + 1) * kSymTile + lane;
+            p0 = j0 < U.nj ? __ldcg(sh + U.jbase + j0) : make_float4(kParked, kParked, kParked, 0.0f);
+            p1 = j0 + 32 < U.nj ? __ldcg(sh + U.jbase + j0 + 32)
+                                : make_float4(kParked, kParked, kParked, 0.0f);
+          }
+          float2 ajx = make_float2(0.0f, 0.0f), ajy = ajx, ajz = ajx;
+          const int qd = same ? g - bt0 : kSymTpb;
+#define CTS_SYM_PAIRS(QD)                                                                   \
+  sym_tile_pairs<RI, QD>(sx, sy, sz, lane, xi, yi, zi, aix, aiy, aiz, ajx, ajy, ajz, eps2, \
+                         min(qd, kSymTpb), vt)
+          if (vt < kSymTpb) CTS_SYM_PAIRS(-1);
+          else if (qd >= kSymTpb) CTS_SYM_PAIRS(kSymTpb);
+          else if (qd == 0) CTS_SYM_PAIRS(0);
+          else if (qd == 1) CTS_SYM_PAIRS(1);
+          else if (qd == 2) CTS_SYM_PAIRS(2);
+          else CTS_SYM_PAIRS(3);
+#undef CTS_SYM_PAIRS
+          float* jt = jacc + (g - U.jt0) * kSymPartFloats;
+          jt[lane] += ajx.x;
+          jt[32 + lane] += ajx.y;
+          jt[kSymTile + lane] += ajy.x;
+          jt[kSymTile + 32 + lane] += ajy.y;
+          jt[2 * kSymTile + lane] += ajz.x;
+          jt[2 * kSymTile + 32 + lane] += ajz.y;
+          if (++nf == kSymFold) {
+            sym_fold_i<RI>(iacc, lane, aix, aiy, aiz);
+            nf = 0;
+          }
+        }
+        if (nf) sym_fold_i<RI>(iacc, lane, aix, aiy, aiz);
+        __syncwarp();
+        // the block's i fields: s_j times the sums
+        const float sgn = sJ ? -1.0f : 1.0f;
+        for (int u = 0; u < vt; ++u) {
+          float* dst = a.sym.part + (int64_t)(U.pI + (b - U.ib0) * kSymTpb + u) * kSymPartFloats;
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            dst[c * kSymTile + lane] = sgn * iacc[c * kSymBlock + u * kSymTile + lane];
+            dst[c * kSymTile + 32 + lane] = sgn * iacc[c * kSymBlock + u * kSymTile + 32 + lane];
+          }
+        }
+      }
+      __syncwarp();
+      // the tiles' j fields: -s_i times the sums
+      const float sgn = sI ? 1.0f : -1.0f;
+      for (int t = 0; t < nj_t; ++t) {
+        float* dst = a.sym.part + (int64_t)(U.pJ + t) * kSymPartFloats;
+        for (int e = lane; e < kSymPartFloats; e += 32) dst[e] = sgn * jacc[t * kSymPartFloats + e];
+      }
+    } else {
+      // no repulsion: zero fields (the partials still complete their tiles)
+      for (int b = U.ib0; b < U.ib1; ++b) {
+        const int vt = min(kSymTpb, nti - b * kSymTpb);
+        for (int u = 0; u < vt; ++u) {
+          float* dst = a.sym.part + (int64_t)(U.pI + (b - U.ib0) * kSymTpb + u) * kSymPartFloats;
+          for (int e = lane; e < kSymPartFloats; e += 32) dst[e] = 0.0f;
+        }
+      }
+      for (int t = 0; t < nj_t; ++t) {
+        float* dst = a.sym.part + (int64_t)(U.pJ + t) * kSymPartFloats;
+        for (int e = lane; e < kSymPartFloats; e += 32) dst[e] = 0.0f;
+      }
+    }
+    // the unit's partials are in: count them for their tiles' update units
+    __threadfence();
+    __syncwarp();
+    {
+      const int nI = min(U.ib1 * kSymTpb, nti) - U.ib0 * kSymTpb;
+      const int ntot = nI + nj_t;
+      for (int e = lane; e < ntot; e += 32) {
+        const int gt = e < nI ? U.tI + U.ib0 * kSymTpb + e : U.tJ + U.jt0 + (e - nI);
+        atomicAdd(a.sym.tile_ctr + gt, 1);
+      }
+    }
+    if (a.trace && lane == 0) sym_trace(a, qi, 0, tr0, tr1, sym_now());
+  }
+}
+
 // Update alone: reads the field written by a FIELD_ONLY step launch.
 // PX: the instantiation that records the 3 x 3 window's pixels too.
 template <bool PX>
@@ -1689,12 +2231,17 @@ struct VariantEntry {
 
 // (threads, i's per thread, packed f32x2, j unroll, min CTAs per SM [register
 // cap], CTAs per SM launched [0 = all that fit], dynamic queue).  Entry 0 is
-// the default: sources paired in packed FP32 lanes, 512-carrier tiles, guided
-// dynamic queue (fastest on the 64 x 20 keV batch).
+// the default: the symmetric kernel (each unordered pair once, one warp per
+// unit, 12 warps per SM).  The others evaluate every ordered pair: sources
+// paired in packed FP32 lanes, 512-carrier tiles, guided dynamic queue first.
 #define CTS_V(NT, R, MODE, JU, MB, CPS, DYN, NAME) \
   {NT, R, NAME, step_kernel<NT, R, MODE, JU, MB, 0>, CPS, DYN, MODE, \
    step_kernel<NT, R, MODE, JU, MB, 1>, step_kernel<NT, R, MODE, JU, MB, 2>}
+#define CTS_SYM(NT, NAME) \
+  {NT, kSymRI, NAME, sym_kernel<kSymRI, NT, 0>, 1, 1, 3, sym_kernel<kSymRI, NT, 1>, \
+   sym_kernel<kSymRI, NT, 2>}
 const VariantEntry kVariants[] = {
+    CTS_SYM(384, "sym_nt384_r8_warp"),
     CTS_V(256, 2, 2, 4, 3, 0, 1, "nt256_r2_jpair_dyn"),
     CTS_V(256, 4, 2, 4, 2, 0, 1, "nt256_r4_jpair_dyn"),
     CTS_V(128, 2, 2, 4, 6, 0, 1, "nt128_r2_jpair_dyn"),
@@ -1706,12 +2253,17 @@ const VariantEntry kVariants[] = {
     CTS_V(512, 2, 1, 4, 1, 1, 0, "nt512_r2_ipair_1sm_static"),
     CTS_V(256, 2, 0, 4, 3, 0, 1, "nt256_r2_scalar_dyn"),
     CTS_V(256, 2, 0, 2, 4, 0, 0, "nt256_r2_scalar_static"),
+    CTS_SYM(256, "sym_nt256_r8_warp"),
 };
 #undef CTS_V
+#undef CTS_SYM
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 constexpr size_t kStageBytes = 2 * kChunkJ * sizeof(float4);
 constexpr size_t kSoaBytes = 3 * kChunkJ * sizeof(float);
-size_t smem_of(const VariantEntry& e) { return kStageBytes + (e.mode == 2 ? kSoaBytes : 0); }
+size_t smem_of(const VariantEntry& e) {
+  if (e.mode == 3) return (size_t)(e.nt / 32) * kSymWarpFloats * sizeof(float);
+  return kStageBytes + (e.mode == 2 ? kSoaBytes : 0);
+}
 
 }  // namespace
 
@@ -1719,7 +2271,7 @@ int variant_count() { return kNumVariants; }
 
 Variant variant_info(int v) {
   const VariantEntry& e = kVariants[v];
-  return Variant{e.nt, e.r, e.name, e.ctas_per_sm, e.dynamic};
+  return Variant{e.nt, e.r, e.name, e.ctas_per_sm, e.dynamic, e.mode == 3 ? 1 : 0};
 }
 
 size_t variant_smem(int v) { return smem_of(kVariants[v]); }

@@ -38,7 +38,16 @@ constexpr int kDefaultSlots = 256;
 constexpr int kDefaultK = 32;
 constexpr size_t kLaunchLogCap = size_t(1) << 20;
 constexpr int64_t kDefaultBudget = 1ll << 30;
+// Default kernel choice per chunk (measured on the 20 keV batch: the
+// symmetric kernel is faster from about 21 resident events of 5525 carriers,
+// i.e. 6.4e8 carrier pairs, and slower below)
+constexpr double kSymMinWork = 6.4e8;
+constexpr int kSymVariant = 0;   // sym_nt384_r8_warp
+constexpr int kPairVariant = 1;  // nt256_r2_jpair_dyn
 constexpr int kMaxUnits = 1 << 16;
+constexpr int kMaxSymUnits = 1 << 18;  // units of one step of the symmetric kernel
+// upload_sym_plan: the plan needs more units or tiles than the buffers hold
+constexpr int kSymPlanTooLarge = 1;
 constexpr int kDefaultQueue = 1 << 16;
 // arena (positions, two shadows, id, collection point, step, state), explicit
 // staging, split-tile accumulators (3 doubles) and the PLAIN field buffer
@@ -96,6 +105,7 @@ struct sim_t {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   int S = 0, K = 0, variant = 0, grid = 0, tile_i = 0, dynamic = 0;
+  bool sym = false;  // the current variant is the symmetric kernel
   int64_t capacity = 0, partial_cap = 0;
   bool broken = false;
   std::string err;
@@ -135,10 +145,30 @@ struct sim_t {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> lev;  // per-launch events (time_launches): K + 1
 
+  // the symmetric kernel's plan of the current chunk and its buffers (the
+  // partial fields and lists grow with the plan; growing them drops the
+  // captured graphs, which hold their addresses)
+  SymPlan splan;
+  SymUnit* d_sym_units = nullptr;
+  SymUnit* h_sym_units = nullptr;
+  int32_t* d_sym_nu = nullptr;
+  int32_t* h_sym_nu = nullptr;
+  SymTile* d_sym_tiles = nullptr;
+  SymTile* h_sym_tiles = nullptr;
+  int64_t sym_tiles_cap = 0;
+  int32_t* d_sym_lists = nullptr;
+  int32_t* h_sym_lists = nullptr;
+  int64_t sym_lists_cap = 0;
+  float* d_sym_part = nullptr;
+  int64_t sym_part_cap = 0;  // partial fields (3 x 64 floats each)
+  int32_t* d_sym_ctr = nullptr;     // partials written per tile
+  SymStep* d_sym_rec = nullptr;
+  int32_t* d_sym_ready = nullptr;
+
   // host state
   std::vector<HostSlot> slots;
   ArenaAllocator alloc;
-  std::deque<std::array<double, 3>> launch_log;  // (ms, pairs, running) per step launch
+  std::deque<std::array<double, 4>> launch_log;  // (ms, pairs, running, symmetric) per launch
   std::vector<UnitPlan> plan;
   std::vector<int32_t> plan_begin;
   std::mutex qmu;
@@ -494,6 +524,16 @@ StepArgs step_args(sim_t* s, bool fused) {
   a.ph = s->ph;
   a.S = s->S;
   a.fused = fused ? 1 : 0;
+  a.sym.units = s->d_sym_units;
+  a.sym.n_units = s->d_sym_nu;
+  a.sym.tiles = s->d_sym_tiles;
+  a.sym.lists = s->d_sym_lists;
+  a.sym.part = s->d_sym_part;
+  a.sym.tile_ctr = s->d_sym_ctr;
+  a.sym.rec = s->d_sym_rec;
+  a.sym.ready = s->d_sym_ready;
+  a.sym.n_part = s->sym_part_cap;
+  a.sym.n_tiles = (int32_t)s->sym_tiles_cap;
   return a;
 }
 
@@ -535,8 +575,137 @@ void device_units(const std::vector<UnitPlan>& plan, const std::vector<SlotGeom>
   }
 }
 
+// The captured chunk graphs hold buffer addresses: drop them when a buffer
+// moves (they are captured again at the next chunk).
+void drop_graphs(sim_t* s) {
+  for (size_t g = 0; g < s->graphs.size(); ++g) {
+    if (s->graphs[g]) cudaGraphExecDestroy(s->graphs[g]);
+    s->graphs[g] = nullptr;
+    s->graph_K[g] = -1;
+  }
+}
+
+// Grows the symmetric kernel's list and partial buffers to hold `lists`
+// entries and `parts` partial fields (by half again, to spare later growth).
+int sym_reserve(sim_t* s, int64_t lists, int64_t parts) {
+  if (lists > s->sym_lists_cap) {
+    const int64_t cap = std::max<int64_t>(lists + lists / 2, 1 << 16);
+    drop_graphs(s);
+    if (s->d_sym_lists) cudaFree(s->d_sym_lists);
+    if (s->h_sym_lists) cudaFreeHost(s->h_sym_lists);
+    s->d_sym_lists = nullptr;
+    s->h_sym_lists = nullptr;
+    s->sym_lists_cap = 0;
+    CK(cudaMalloc((void**)&s->d_sym_lists, (size_t)cap * sizeof(int32_t)));
+    CK(cudaMallocHost((void**)&s->h_sym_lists, (size_t)cap * sizeof(int32_t)));
+    s->sym_lists_cap = cap;
+  }
+  if (parts > s->sym_part_cap) {
+    const int64_t cap = std::max<int64_t>(parts + parts / 2, 1 << 12);
+    drop_graphs(s);
+    if (s->d_sym_part) cudaFree(s->d_sym_part);
+    s->d_sym_part = nullptr;
+    s->sym_part_cap = 0;
+    CK(cudaMalloc((void**)&s->d_sym_part, (size_t)cap * kSymPartFloats * sizeof(float)));
+    s->sym_part_cap = cap;
+  }
+  return SIM_OK;
+}
+
+// Where a slot sits for the symmetric plan: its arena range, species range
+// lengths and first step of the chunk.
+struct SymGeom {
+  int64_t base = 0;
+  int32_t cap_h = 0, n_h = 0, n_e = 0;
+  int64_t step0 = 0;
+};
+
+// Plan the symmetric kernel's step for the given slots and upload units,
+// tiles and partial lists.
+int upload_sym_plan(sim_t* s, const std::vector<SymGeom>& g) {
+  const int n_slots = (int)g.size();
+  std::vector<int32_t> nh(n_slots), ne(n_slots);
+  for (int k = 0; k < n_slots; ++k) {
+    nh[k] = g[k].n_h;
+    ne[k] = g[k].n_e;
+  }
+  SymPlan& P = s->splan;
+  const int prc = plan_sym(nh.data(), ne.data(), n_slots, kMaxSymUnits, &P);
+  if (prc == -2 || (prc == 0 && (int64_t)P.tiles.size() > s->sym_tiles_cap)) return kSymPlanTooLarge;
+  if (prc != 0) {
+    s->err = "symmetric unit plan failed";
+    return SIM_EINVAL;
+  }
+  int rc = sym_reserve(s, (int64_t)P.lists.size(), P.n_partials);
+  if (rc) return rc;
+  const int nu = (int)P.units.size();
+  for (int q = 0; q < nu; ++q) {
+    const SymUnitPlan& u = P.units[q];
+    const SymGeom& sg = g[u.slot];
+    const int th = (sg.n_h + kSymTile - 1) / kSymTile;
+    SymUnit d{};
+    d.slot = u.slot;
+    d.ntiles = P.slot_ntiles[u.slot];
+    d.npair = u.npair;
+    d.jt0 = u.jt0;
+    d.jt1 = u.jt1;
+    if (u.kind == 1) {
+      d.flags = kSymUpdate | ((sg.step0 & 1) ? kSymOddStep : 0);
+      d.tI = d.tJ = P.slot_tile0[u.slot];
+    } else {
+      d.ibase = sg.base + (u.spec_i ? sg.cap_h : 0);
+      d.jbase = sg.base + (u.spec_j ? sg.cap_h : 0);
+      d.flags = (u.spec_i ? kSymIElectrons : 0) | (u.spec_j ? kSymJElectrons : 0) |
+                (u.duty ? kSymDuty : 0) | ((sg.step0 & 1) ? kSymOddStep : 0);
+      d.ib0 = u.ib0;
+      d.ib1 = u.ib1;
+      d.ni = u.spec_i ? sg.n_e : sg.n_h;
+      d.nj = u.spec_j ? sg.n_e : sg.n_h;
+      d.pI = u.p_i;
+      d.pJ = u.p_j;
+      d.tI = P.slot_tile0[u.slot] + (u.spec_i ? th : 0);
+      d.tJ = P.slot_tile0[u.slot] + (u.spec_j ? th : 0);
+    }
+    s->h_sym_units[q] = d;
+  }
+  for (size_t t = 0; t < P.tiles.size(); ++t) {
+    const SymTilePlan& tp = P.tiles[t];
+    const SymGeom& sg = g[tp.slot];
+    SymTile d{};
+    d.off = sg.base + (tp.spec ? sg.cap_h : 0) + (int64_t)kSymTile * tp.tile;
+    d.slot = tp.slot;
+    d.spec = tp.spec;
+    d.n = tp.n;
+    d.lptr = tp.lptr;
+    d.lcnt = tp.lcnt;
+    d.ntiles = P.slot_ntiles[tp.slot];
+    s->h_sym_tiles[t] = d;
+  }
+  std::memcpy(s->h_sym_lists, P.lists.data(), P.lists.size() * sizeof(int32_t));
+  *s->h_sym_nu = nu;
+  CK(h2d(s, s->d_sym_units, s->h_sym_units, std::max(nu, 1) * sizeof(SymUnit)));
+  CK(h2d(s, s->d_sym_tiles, s->h_sym_tiles, std::max<size_t>(P.tiles.size(), 1) * sizeof(SymTile)));
+  CK(h2d(s, s->d_sym_lists, s->h_sym_lists, std::max<size_t>(P.lists.size(), 1) * sizeof(int32_t)));
+  CK(h2d(s, s->d_sym_nu, s->h_sym_nu, sizeof(int32_t)));
+  return SIM_OK;
+}
+
 // Build and upload the unit list of the running slots.
 int upload_units(sim_t* s, bool allow_split, bool slot_major = false) {
+  if (s->sym) {
+    std::vector<SymGeom> geom(s->S);
+    for (int k = 0; k < s->S; ++k) {
+      const HostSlot& h = s->slots[k];
+      geom[k].base = h.base;
+      geom[k].cap_h = h.rec.cap_h;
+      geom[k].step0 = h.n_steps;
+      if (h.used && h.running) {
+        geom[k].n_h = h.n_h;
+        geom[k].n_e = h.n_e;
+      }
+    }
+    return upload_sym_plan(s, geom);
+  }
   std::vector<int32_t> nh(s->S, 0), ne(s->S, 0);
   for (int k = 0; k < s->S; ++k)
     if (s->slots[k].used && s->slots[k].running) {
@@ -581,6 +750,8 @@ int issue_chunk(sim_t* s, int K, bool multi) {
   CK(cudaMemsetAsync(s->d_unit_counter, 0, K * sizeof(int32_t), s->stream));
   CK(cudaMemsetAsync(s->d_ret, 0, (size_t)K * s->S * 2 * sizeof(int32_t), s->stream));
   CK(cudaMemsetAsync(s->d_tiles_done, 0, (size_t)K * s->S * sizeof(int32_t), s->stream));
+  if (s->sym)
+    CK(cudaMemsetAsync(s->d_sym_ready, 0, (size_t)K * s->S * sizeof(int32_t), s->stream));
   if (s->d_induced)
     CK(cudaMemsetAsync(s->d_induced, 0, (size_t)K * s->S * sizeof(double), s->stream));
   if (s->d_induced_px)
@@ -656,12 +827,33 @@ int run_chunk(sim_t* s) {
       if (W >= (double)s->table_min[q]) v = s->table_var[q];
     int rcv = set_variant(s, v);
     if (rcv) return rcv;
+  } else if (!plain && s->opt.variant == 0) {
+    // the default choice per chunk: the symmetric kernel while the resident
+    // pair work fills the GPU, the per-pair kernel (finer work units, shorter
+    // steps) below it; the events' state is the same for both
+    double W = 0.0;
+    for (auto& h : s->slots)
+      if (h.used && h.running) W += (double)(h.n_h + h.n_e) * (double)(h.n_h + h.n_e);
+    int rcv = set_variant(s, W >= kSymMinWork ? kSymVariant : kPairVariant);
+    if (rcv) return rcv;
   }
   // one launch for the whole chunk: the queue replays the step's pieces K
   // times, slot by slot
   const bool sph = s->field.spherical != 0;
-  const bool multi = !plain && !sph && s->dynamic && s->ph.repulsion && !s->opt.step_launches;
-  int rc = sph ? SIM_OK : upload_units(s, !plain, multi);
+  int rc = SIM_OK;
+  if (!sph && s->sym) {
+    // a symmetric plan larger than its buffers: this chunk runs the per-pair kernel
+    rc = upload_units(s, !plain, true);
+    if (rc == kSymPlanTooLarge) {
+      rc = set_variant(s, kPairVariant);
+      if (rc) return rc;
+    } else if (rc) {
+      return rc;
+    }
+  }
+  const bool multi = !plain && !sph && s->dynamic && (s->sym || s->ph.repulsion) &&
+                     !s->opt.step_launches;
+  if (!sph && !s->sym) rc = upload_units(s, !plain, multi);
   if (rc) return rc;
   const int gi = sph ? 2 * variant_count() : 2 * s->variant + (multi ? 1 : 0);
   const int nl = (multi || sph) ? 1 : K;  // step-kernel launches in the chunk
@@ -701,7 +893,12 @@ int run_chunk(sim_t* s) {
   s->st_ms += ms;
   if (s->opt.time_launches && !plain) {
     double pairs = 0.0;
-    for (const UnitPlan& u : s->plan) pairs += (double)u.ni * (double)(u.j1 - u.j0);
+    if (s->sym) {
+      for (const HostSlot& h : s->slots)
+        if (h.used && h.running && h.n_h > 0) pairs += (double)(h.n_h + h.n_e) * (h.n_h + h.n_e);
+    } else {
+      for (const UnitPlan& u : s->plan) pairs += (double)u.ni * (double)(u.j1 - u.j0);
+    }
     double running = 0.0;
     for (const HostSlot& h : s->slots) running += h.used && h.running;
     for (int k = 0; k < nl; ++k) {
@@ -709,7 +906,7 @@ int run_chunk(sim_t* s) {
       CK(cudaEventElapsedTime(&lm, s->lev[k], s->lev[k + 1]));
       s->st_kernel_ms += lm;
       if (s->launch_log.size() >= kLaunchLogCap) s->launch_log.pop_front();
-      s->launch_log.push_back({(double)lm, pairs * (K / nl), running});
+      s->launch_log.push_back({(double)lm, pairs * (K / nl), running, s->sym ? 1.0 : 0.0});
     }
     s->st_kernel_launches += nl;
   }
@@ -1012,6 +1209,18 @@ int alloc_all(sim_t* s) {
   AL(s->d_explicit, C);
   AL(s->d_list, s->S);
   if (s->opt.mode == CTS_MODE_PLAIN) AL(s->d_field, 3 * C);
+  // symmetric kernel: a slot of n carriers has at most n / 64 + 2 tiles
+  s->sym_tiles_cap = C / kSymTile + 2 * (int64_t)s->S + 1;
+  AL(s->d_sym_units, kMaxSymUnits);
+  AL(s->d_sym_nu, 1);
+  AL(s->d_sym_tiles, s->sym_tiles_cap);
+  AL(s->d_sym_ctr, s->sym_tiles_cap);
+  AL(s->d_sym_rec, (int64_t)kMaxK * s->S);
+  AL(s->d_sym_ready, (int64_t)kMaxK * s->S);
+
+  HL(s->h_sym_units, kMaxSymUnits);
+  HL(s->h_sym_nu, 1);
+  HL(s->h_sym_tiles, s->sym_tiles_cap);
   HL(s->h_summary, s->S);
   HL(s->h_units, kMaxUnits);
   HL(s->h_cta_begin, kMaxGrid + 1);
@@ -1028,6 +1237,9 @@ int alloc_all(sim_t* s) {
   CK(cudaMemset(s->d_combine, 0, kMaxUnits * sizeof(int32_t)));
   CK(cudaMemset(s->d_partial, 0, std::max<int64_t>(s->partial_cap, 1) * sizeof(double)));
   CK(cudaMemset(s->d_err, 0, sizeof(int32_t)));
+  CK(cudaMemset(s->d_sym_nu, 0, sizeof(int32_t)));
+  CK(cudaMemset(s->d_sym_ctr, 0, (size_t)s->sym_tiles_cap * sizeof(int32_t)));
+
   CK(cudaEventCreate(&s->ev0));
   CK(cudaEventCreate(&s->ev1));
   s->lev.assign(kMaxK + 1, nullptr);
@@ -1042,11 +1254,14 @@ void free_all(sim_t* s) {
                  s->A.rstep, s->A.cstate, s->d_slots, s->d_summary, s->d_readout, s->d_pixels,
                  s->d_units, s->d_cta_begin, s->d_unit_counter, s->d_ret, s->d_partial,
                  s->d_combine, s->d_tiles_done, s->d_induced, s->d_err, s->d_field, s->d_explicit,
-                 s->d_list, s->d_drift, s->d_induced_px};
+                 s->d_list, s->d_drift, s->d_induced_px, s->d_sym_units, s->d_sym_nu,
+                 s->d_sym_tiles, s->d_sym_lists, s->d_sym_part, s->d_sym_ctr, s->d_sym_rec,
+                 s->d_sym_ready};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {s->h_summary, s->h_units, s->h_cta_begin, s->h_list, s->h_slotdev, s->h_readout,
-                  s->h_pixels, s->h_err, s->h_induced, s->h_induced_px};
+                  s->h_pixels, s->h_err, s->h_induced, s->h_induced_px, s->h_sym_units,
+                  s->h_sym_nu, s->h_sym_tiles, s->h_sym_lists};
   for (void* p : host)
     if (p) cudaFreeHost(p);
   if (s->ev0) cudaEventDestroy(s->ev0);
@@ -1077,6 +1292,7 @@ int set_variant(sim_t* s, int v) {
   s->grid = std::min(s->sm_count * occ, kMaxGrid);
   s->tile_i = vi.nt * vi.r;
   s->dynamic = vi.dynamic;
+  s->sym = vi.sym != 0;
   return SIM_OK;
 }
 
@@ -1471,6 +1687,7 @@ int sim_get_stats(sim_t* s, sim_stats_t* o) {
   o->step_kernel_launches = s->st_kernel_launches;
   o->h2d_bytes = s->st_h2d;
   o->d2h_bytes = s->st_d2h;
+  o->symmetric = s->sym ? 1 : 0;
   return SIM_OK;
 }
 
@@ -1505,10 +1722,20 @@ int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, in
   std::vector<int32_t> begin;
   int64_t pfl = 0;
   const int32_t nh = n_h, ne = n_e;
-  if (plan_units(&nh, &ne, 1, t->tile_i, t->grid, t->ph.repulsion != 0, kMaxUnits,
-                 t->partial_cap, &plan, &begin, &pfl, t->ph.repulsion != 0 && t->dynamic) != 0 ||
-      pfl > t->partial_cap)
+  if (t->sym) {
+    SymGeom g;
+    g.cap_h = n_h;
+    g.n_h = n_h;
+    g.n_e = n_e;
+    const int rcs = upload_sym_plan(t, std::vector<SymGeom>{g});
+    if (rcs == kSymPlanTooLarge) return SIM_ENOMEM_BUDGET;
+    if (rcs) return rcs;
+  } else if (plan_units(&nh, &ne, 1, t->tile_i, t->grid, t->ph.repulsion != 0, kMaxUnits,
+                        t->partial_cap, &plan, &begin, &pfl,
+                        t->ph.repulsion != 0 && t->dynamic) != 0 ||
+             pfl > t->partial_cap) {
     return SIM_EINVAL;
+  }
   int rc = SIM_OK;
   cudaError_t e = cudaSuccess;
   do {
@@ -1533,17 +1760,20 @@ int sim_debug_field(sim_t* s, const float* x, const float* y, const float* z, in
     if ((e = cudaMemcpyAsync(d_slot, &sd, sizeof(SlotDev), cudaMemcpyHostToDevice, s->stream)) !=
         cudaSuccess)
       break;
-    SlotGeom sg;
-    sg.cap_h = n_h;
-    sg.n_h = n_h;
-    device_units(plan, std::vector<SlotGeom>{sg}, s->h_units);
-    std::memcpy(s->h_cta_begin, begin.data(), begin.size() * sizeof(int32_t));
-    if ((e = cudaMemcpyAsync(s->d_units, s->h_units, std::max<size_t>(plan.size(), 1) * sizeof(Unit),
-                             cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
-      break;
-    if ((e = cudaMemcpyAsync(s->d_cta_begin, s->h_cta_begin, begin.size() * sizeof(int32_t),
-                             cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
-      break;
+    if (!t->sym) {
+      SlotGeom sg;
+      sg.cap_h = n_h;
+      sg.n_h = n_h;
+      device_units(plan, std::vector<SlotGeom>{sg}, s->h_units);
+      std::memcpy(s->h_cta_begin, begin.data(), begin.size() * sizeof(int32_t));
+      if ((e = cudaMemcpyAsync(s->d_units, s->h_units,
+                               std::max<size_t>(plan.size(), 1) * sizeof(Unit),
+                               cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+        break;
+      if ((e = cudaMemcpyAsync(s->d_cta_begin, s->h_cta_begin, begin.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s->stream)) != cudaSuccess)
+        break;
+    }
     if ((e = cudaMemsetAsync(s->d_unit_counter, 0, sizeof(int32_t), s->stream)) != cudaSuccess)
       break;
     if ((e = cudaMemsetAsync(s->d_ret, 0, 2 * sizeof(int32_t), s->stream)) != cudaSuccess) break;
@@ -1585,15 +1815,24 @@ int sim_debug_trace_step(sim_t* s, uint64_t* out, int32_t max_ctas, int32_t* n_c
   for (auto& h : s->slots) any |= h.used && h.running;
   if (!any) return SIM_ESTATE;
   rc = upload_units(s, true);
+  if (rc == kSymPlanTooLarge) rc = SIM_ENOMEM_BUDGET;
   if (rc) return rc;
   float* d_field = nullptr;
   unsigned long long* d_trace = nullptr;
   cudaError_t e = cudaSuccess;
-  std::vector<unsigned long long> h((size_t)8 * s->grid);
+  // broadcast kernels: one record per CTA; the symmetric kernel: a counter,
+  // the capacity and one record per unit, from word 8
+  const size_t words = s->sym ? 8 * ((size_t)std::max(max_ctas, 0) + 1) : (size_t)8 * s->grid;
+  std::vector<unsigned long long> h(words);
   do {
     if ((e = cudaMalloc(&d_field, 3 * (size_t)s->capacity * sizeof(float)))) break;
     if ((e = cudaMalloc(&d_trace, h.size() * sizeof(unsigned long long)))) break;
     if ((e = cudaMemsetAsync(d_trace, 0, h.size() * sizeof(unsigned long long), s->stream))) break;
+    if (s->sym) {
+      const unsigned long long cap = (unsigned long long)std::max(max_ctas, 0);
+      if ((e = cudaMemcpyAsync(d_trace + 1, &cap, sizeof(cap), cudaMemcpyHostToDevice, s->stream)))
+        break;
+    }
     if ((e = cudaMemsetAsync(s->d_ret, 0, (size_t)s->S * 2 * sizeof(int32_t), s->stream))) break;
     if ((e = cudaMemsetAsync(s->d_unit_counter, 0, sizeof(int32_t), s->stream))) break;
     StepArgs a = step_args(s, false);
@@ -1611,6 +1850,13 @@ int sim_debug_trace_step(sim_t* s, uint64_t* out, int32_t max_ctas, int32_t* n_c
     s->err = cudaGetErrorString(e);
     return SIM_ECUDA;
   }
+  if (s->sym) {
+    const int n = (int)std::min<unsigned long long>(h[0], (unsigned long long)max_ctas);
+    for (int r = 0; r < n; ++r)
+      for (int q = 0; q < 8; ++q) out[8 * r + q] = h[8 + 8 * (size_t)r + q];
+    *n_ctas = n;
+    return SIM_OK;
+  }
   const int n = std::min(max_ctas, s->grid);
   for (int g = 0; g < n; ++g)
     for (int q = 0; q < 8; ++q) out[8 * g + q] = h[8 * (size_t)g + q];
@@ -1623,7 +1869,7 @@ int sim_debug_launch_log(sim_t* s, double* out, int32_t cap, int32_t* n_out) {
   std::lock_guard<std::mutex> dl(s->drive_mu);
   const int n = (int)std::min<size_t>((size_t)cap, s->launch_log.size());
   for (int q = 0; q < n; ++q)
-    for (int c = 0; c < 3; ++c) out[3 * q + c] = s->launch_log[q][c];
+    for (int c = 0; c < 4; ++c) out[4 * q + c] = s->launch_log[q][c];
   s->launch_log.clear();
   *n_out = n;
   return SIM_OK;
@@ -1687,6 +1933,7 @@ int sim_debug_time_step(sim_t* s, int32_t variant, int32_t reps, double* ms_per_
     if (rc) return rc;
   }
   rc = upload_units(s, true);
+  if (rc == kSymPlanTooLarge) rc = SIM_ENOMEM_BUDGET;
   float* d_field = nullptr;
   cudaError_t e = cudaSuccess;
   float ms = 0.f;
