@@ -272,10 +272,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if the
+def profiled_traffic(kernel: str = "sym_kernel"):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if the
     kernel source is unchanged since that capture (else None)."""
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
@@ -608,7 +608,7 @@ def run_ours(args, rank, world, local):
     achieved = fpi * dom_inter / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
             "frac": achieved / peak_tflops if achieved else None,
-            "traffic": profiled_traffic(),
+            "traffic": profiled_traffic() if dominant_sym else None,
             "kernel": ("sym_kernel (each unordered pair once, fused update)" if dominant_sym
                        else "step_kernel (every ordered pair, fused update)"),
             "peak_basis": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz "

@@ -317,6 +317,21 @@ int sim_debug_trajectory(sim_t* sim, const sim_event_t* ev, int64_t n_steps,
                          double* pos_out, int8_t* state_out, int64_t capacity,
                          int64_t* steps_done);
 
+/* One time step of Algorithm 1 (Sec. 2.1; the field of Eq. 4, the moves of
+ * Eqs. 3, 5, 6, then collection and exit) through the library's step kernel,
+ * from given FP64 positions: n carriers, xyz[3n] (um, x y z per carrier) and
+ * sign[n] (+1 hole, -1 electron; NULL = all holes), all active, taken as
+ * carriers 0 .. n-1 of an event (seed, event_id) at its step 0, so carrier c
+ * draws its diffusion normals from counter (c, 0).  Writes the positions
+ * after the step to xyz_out[3n] (a collected hole: its collection point x, y
+ * and NaN z; an electron that left: NaN) and the states (0 active, 1
+ * collected, 2 exited) to state_out[n].  The handle must be BATCHED with no
+ * event resident or queued (SIM_ESTATE).  For one-step parity tests: both
+ * sides start from the same state, so trajectory divergence cannot hide the
+ * difference of a single step. */
+int sim_debug_step(sim_t* sim, uint64_t seed, uint64_t event_id, int32_t n, const double* xyz,
+                   const int8_t* sign, double* xyz_out, int8_t* state_out);
+
 /* One step of the pair kernel (field only: the staged events do not move)
  * on the events admitted by sim_stage, with a trace.  Kernels that evaluate
  * every ordered pair: out[8g..8g+7] = (SM id, start ns, end ns, pairs,

@@ -18,8 +18,9 @@ extern "C" {
 /* One unit of pair work: i's [i0, i0 + ni) of species spec (0 holes, 1
  * electrons) of slot `slot`, against sources [j0, j1) of the slot's
  * concatenated [holes | electrons] list.  Units of one i-block share iblock
- * and are split into nsplit j ranges (split = 0 .. nsplit - 1); pbase is the
- * offset (FP64 entries) of the tile's 3 x tile_i accumulators (nsplit > 1). */
+ * and are split into nsplit j ranges (split = 0 .. nsplit - 1); piece split
+ * of a tile writes its partial sums to the FP64 entries [pbase + 3 * tile_i *
+ * split, + 3 * tile_i) (nsplit > 1), and the pieces are added in split order. */
 typedef struct cts_unit_t {
   int32_t slot, spec, i0, ni, j0, j1, split, nsplit, iblock, pbase;
 } cts_unit_t;

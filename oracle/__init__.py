@@ -128,6 +128,9 @@ def lib():
         _lib.or_weighting_potential.argtypes = [d, d, d, d, d, d, d, d, i32]
         _lib.or_weighting_potential.restype = d
         _lib.or_window_potentials.argtypes = [P(_Params), d, d, d, P(d)]
+        _lib.or_step.argtypes = [P(_Params), u64, u64, i64, i64, P(d), P(d), P(d),
+                                 P(C.c_int8), P(C.c_int8), C.c_int]
+        _lib.or_step.restype = i64
     return _lib
 
 
@@ -494,6 +497,23 @@ def run_events(params: _Params, events: list[dict], induced_px: bool = False) ->
 
 def run_event(params: _Params, ev: dict, induced_px: bool = False) -> EventResult:
     return run_events(params, [ev], induced_px)[0]
+
+
+def step(params: _Params, seed: int, event_id: int, step_index: int, pos, sign, state):
+    """One time step of Algorithm 1 from the given FP64 positions (n x 3),
+    signs and states (carriers laid out as init_event does): the repulsion
+    field from these positions, the moves with the diffusion normals of step
+    `step_index`, then the boundaries.  Returns (new positions, new states)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    n = pos.shape[0]
+    x = np.ascontiguousarray(pos[:, 0]); y = np.ascontiguousarray(pos[:, 1])
+    z = np.ascontiguousarray(pos[:, 2])
+    sg = np.ascontiguousarray(sign, dtype=np.int8)
+    st = np.array(state, dtype=np.int8)
+    lib().or_step(C.byref(params), int(seed), int(event_id), int(step_index), n,
+                  _ptr(x, C.c_double), _ptr(y, C.c_double), _ptr(z, C.c_double),
+                  _ptr(sg, C.c_int8), _ptr(st, C.c_int8), 1)
+    return np.stack([x, y, z], axis=1), st
 
 
 WEIGHT_PAIRS = 32   # image pairs the oracle sums before the two-term tail

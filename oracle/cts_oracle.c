@@ -505,6 +505,39 @@ void or_window_potentials(const or_params_t* P, double x, double y, double z,
 }
 
 /* ------------------------------------------------------------------------ */
+/* The moves of one step (Eqs. 3, 5): for active carrier c = rows[r] with    */
+/* repulsion field (ex, ey, ez)[r] at the step start, total field E = E_rep  */
+/* + drift field (Eq. 6), mobility mu(|E|), drift sign(q) mu E dt and the     */
+/* Gaussian diffusion step sqrt(2 D dt) g, D = mu kT/e, g from the event's   */
+/* stream at counter (c, step).  New positions go to (nx, ny, nz)[r].        */
+/* ------------------------------------------------------------------------ */
+static void or_moves(const or_params_t* P, uint64_t seed, uint64_t event_id, int64_t step,
+                     int64_t n_act, const int64_t* rows, const double* x, const double* y,
+                     const double* z, const int8_t* sign, const double* ex, const double* ey,
+                     const double* ez, int parallel, double* nx, double* ny, double* nz) {
+  double kT = or_thermal_voltage(P->temperature_K);
+  double dt = P->dt_ps * 1e-3; /* ps -> ns */
+#pragma omp parallel for schedule(static) if (parallel)
+  for (int64_t r = 0; r < n_act; ++r) {
+    int64_t c = rows[r];
+    double Ex = ex[r], Ey = ey[r], Ez = ez[r];
+    if (P->drift) Ez += -or_drift_field(P, z[c]);
+    double Emag = sqrt(Ex * Ex + Ey * Ey + Ez * Ez);
+    double mu = or_mobility(P, sign[c], Emag);
+    double s = (double)sign[c];
+    double dx = s * mu * Ex * dt, dy = s * mu * Ey * dt, dz = s * mu * Ez * dt;
+    if (P->diffusion) {
+      double D = mu * kT;
+      double g[3];
+      or_normals3(seed, event_id, OR_PURPOSE_DIFFUSION, (uint32_t)c, (uint32_t)step, g);
+      double a = sqrt(2.0 * D * dt);
+      dx += a * g[0]; dy += a * g[1]; dz += a * g[2];
+    }
+    nx[r] = x[c] + dx; ny[r] = y[c] + dy; nz[r] = z[c] + dz;
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One event, Algorithm 1: repeat {repulsion field of every carrier from the */
 /* positions at the start of the step; drift field Eq. 6; mobility from     */
 /* |E_drift + E_repulsion|; D = mu kT/e; x, y by Eq. 3 and z by Eq. 5 with  */
@@ -524,8 +557,6 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
   int8_t* state = (int8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
 
   double kc = or_coulomb_k(P->eps_r);
-  double kT = or_thermal_voltage(P->temperature_K);
-  double dt = P->dt_ps * 1e-3; /* ps -> ns */
 
   double* nx = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
   double* ny = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
@@ -579,25 +610,8 @@ int or_run_event(const or_params_t* P, const or_event_t* ev, or_result_t* R,
       for (int64_t r = 0; r < n_act; ++r) ex[r] = ey[r] = ez[r] = 0.0;
     }
     /* Moves (all from step-start positions, then committed together). */
-#pragma omp parallel for schedule(static) if (parallel)
-    for (int64_t r = 0; r < n_act; ++r) {
-      int64_t c = rows[r];
-      double Ex = ex[r], Ey = ey[r], Ez = ez[r];
-      if (P->drift) Ez += -or_drift_field(P, z[c]);
-      double Emag = sqrt(Ex * Ex + Ey * Ey + Ez * Ez);
-      double mu = or_mobility(P, sign[c], Emag);
-      double s = (double)sign[c];
-      double dx = s * mu * Ex * dt, dy = s * mu * Ey * dt, dz = s * mu * Ez * dt;
-      if (P->diffusion) {
-        double D = mu * kT;
-        double g[3];
-        or_normals3(ev->seed, ev->event_id, OR_PURPOSE_DIFFUSION, (uint32_t)c,
-                    (uint32_t)step, g);
-        double a = sqrt(2.0 * D * dt);
-        dx += a * g[0]; dy += a * g[1]; dz += a * g[2];
-      }
-      nx[r] = x[c] + dx; ny[r] = y[c] + dy; nz[r] = z[c] + dz;
-    }
+    or_moves(P, ev->seed, ev->event_id, step, n_act, rows, x, y, z, sign, ex, ey, ez, parallel,
+             nx, ny, nz);
     for (int64_t r = 0; r < n_act; ++r) {
       int64_t c = rows[r];
       ez[r] = z[c];  /* the depth before the move, for the induced charge */
@@ -673,6 +687,43 @@ void or_run_events(const or_params_t* P, const or_event_t* evs, int64_t n_ev,
                    or_result_t* R) {
 #pragma omp parallel for schedule(dynamic, 1)
   for (int64_t e = 0; e < n_ev; ++e) or_run_event(P, &evs[e], &R[e], 0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* One time step of Algorithm 1 from a given state (one-step parity tests):  */
+/* the repulsion field of every active carrier from the positions given,     */
+/* the moves at step index `step`, committed together, then the boundaries.  */
+/* x, y, z, state: n carriers laid out as or_init_event does (holes, then    */
+/* the pairs' electrons), updated in place.  Returns the active carriers     */
+/* before the step.                                                          */
+/* ------------------------------------------------------------------------ */
+int64_t or_step(const or_params_t* P, uint64_t seed, uint64_t event_id, int64_t step,
+                int64_t n, double* x, double* y, double* z, const int8_t* sign,
+                int8_t* state, int parallel) {
+  size_t m = (size_t)(n > 0 ? n : 1);
+  int64_t* rows = (int64_t*)calloc(m, sizeof(int64_t));
+  double* ex = (double*)calloc(m, sizeof(double));
+  double* ey = (double*)calloc(m, sizeof(double));
+  double* ez = (double*)calloc(m, sizeof(double));
+  double* nx = (double*)calloc(m, sizeof(double));
+  double* ny = (double*)calloc(m, sizeof(double));
+  double* nz = (double*)calloc(m, sizeof(double));
+  int64_t n_act = 0;
+  for (int64_t c = 0; c < n; ++c)
+    if (state[c] == OR_ACTIVE) rows[n_act++] = c;
+  if (P->repulsion)
+    or_field_rows(n, x, y, z, sign, state, rows, n_act, or_coulomb_k(P->eps_r),
+                  P->softening_um, parallel, ex, ey, ez);
+  or_moves(P, seed, event_id, step, n_act, rows, x, y, z, sign, ex, ey, ez, parallel, nx, ny, nz);
+  for (int64_t r = 0; r < n_act; ++r) {
+    int64_t c = rows[r];
+    x[c] = nx[r]; y[c] = ny[r]; z[c] = nz[r];
+  }
+  or_result_t R;
+  memset(&R, 0, sizeof R);
+  or_boundaries(P, n, x, y, z, sign, state, step, &R);
+  free(rows); free(ex); free(ey); free(ez); free(nx); free(ny); free(nz);
+  return n_act;
 }
 
 int or_max_threads(void) {

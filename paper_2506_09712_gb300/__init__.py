@@ -117,7 +117,7 @@ class cts_unit_t(C.Structure):
 EXPORTED = ["sim_init", "sim_submit", "sim_poll", "sim_run", "sim_stage", "sim_execute",
             "sim_collect", "sim_get_stats", "sim_destroy", "sim_strerror", "sim_debug_field",
             "sim_debug_bin", "sim_debug_philox", "sim_debug_normals", "sim_debug_trajectory",
-            "sim_debug_inject", "sim_debug_trace_step", "sim_debug_time_step", "sim_debug_launch_log",
+            "sim_debug_inject", "sim_debug_step", "sim_debug_trace_step", "sim_debug_time_step", "sim_debug_launch_log",
             "sim_debug_fma_peak", "sim_build_flags", "sim_readout", "cts_fano_pairs", "sim_generate",
             "cts_fit_ggd", "cts_fit_alpha_t", "cts_fit_beta_t", "cts_ggd_params_at",
             "cts_variant_table_save", "cts_variant_table_load",
@@ -167,6 +167,7 @@ def load(build_if_missing: bool = True):
         "sim_debug_normals": [P(u64), i64, P(d)],
         "sim_debug_trajectory": [C.c_void_p, P(sim_event_t), i64, P(d), P(C.c_int8), i64,
                                  P(i64)],
+        "sim_debug_step": [C.c_void_p, u64, u64, i32, P(d), P(C.c_int8), P(d), P(C.c_int8)],
         "sim_debug_inject": [C.c_void_p, C.c_int],
         "sim_debug_trace_step": [C.c_void_p, P(u64), i32, P(i32)],
         "sim_debug_time_step": [C.c_void_p, i32, i32, P(d)],
@@ -323,6 +324,21 @@ def sim_debug_trajectory(h, event: sim_event_t, n_steps, n_carriers):
                                      _ptr(st, C.c_int8), pos.shape[0], C.byref(done))
     _check(rc, "sim_debug_trajectory")
     return pos[:n_carriers], st[:n_carriers], done.value
+
+
+def sim_debug_step(h, seed, event_id, xyz, sign=None):
+    """One step through the step kernel from FP64 positions xyz (n x 3, all
+    active carriers 0..n-1 of event (seed, event_id) at its step 0); returns
+    (positions, states) after the step."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    n = xyz.shape[0]
+    sg = None if sign is None else np.ascontiguousarray(sign, dtype=np.int8)
+    out = np.zeros((n, 3), dtype=np.float64)
+    st = np.zeros(n, dtype=np.int8)
+    _check(load().sim_debug_step(h, int(seed), int(event_id), n, _ptr(xyz, C.c_double),
+                                 _ptr(sg, C.c_int8), _ptr(out, C.c_double), _ptr(st, C.c_int8)),
+           "sim_debug_step")
+    return out, st
 
 
 def sim_debug_inject(h, fault):

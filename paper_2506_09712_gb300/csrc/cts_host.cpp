@@ -122,11 +122,12 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
                           : f < 0.9375 ? w / 16.0 : f < 0.96875 ? w / 32.0 : w / 64.0;
       int ns = (int)std::max(1.0, std::ceil((double)t.ni * t.n / target));
       ns = std::min({ns, std::max(1, t.n / kPlanDynMinJ), kPlanDynMaxPieces});
-      // a split tile needs its own 3 * tile_i partial sums: run it whole once
-      // the buffer is spoken for
+      // each piece of a split tile needs its own 3 * tile_i partial sums (the
+      // tile's pieces are added in piece order): run the tile whole once the
+      // buffer is spoken for
       if (ns > 1) {
-        if (reserved + (int64_t)3 * tile_i > partial_cap) ns = 1;
-        else reserved += (int64_t)3 * tile_i;
+        if (reserved + (int64_t)3 * tile_i * ns > partial_cap) ns = 1;
+        else reserved += (int64_t)3 * tile_i * ns;
       }
       for (int k = 0; k < ns; ++k) {
         int j0 = (int)((int64_t)t.n * k / ns) & ~3, j1 = k + 1 == ns ? t.n : (int)((int64_t)t.n * (k + 1) / ns) & ~3;
@@ -143,7 +144,7 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
       if (pc.ns > 1 && pc.k == 0) {
         pb[pc.t] = (int)pfl;
         ib[pc.t] = iblock++;
-        pfl += (int64_t)3 * tile_i;
+        pfl += (int64_t)3 * tile_i * pc.ns;
       }
     std::stable_sort(pieces.begin(), pieces.end(), [&](const Piece& a, const Piece& b) {
       if (slot_major && tiles[a.t].slot != tiles[b.t].slot)
@@ -184,13 +185,13 @@ int plan_units(const int32_t* n_h, const int32_t* n_e, int n_slots, int tile_i, 
     const int ns = (int)segs.size();
     int pbase = 0, ib = -1;
     if (ns > 1) {
-      if (pfl + (int64_t)3 * tile_i > partial_cap) {
+      if (pfl + (int64_t)3 * tile_i * ns > partial_cap) {
         // no room for partial sums: run the tile whole on its first CTA
         segs.assign(1, {segs.front().first, {0, t.n}});
       } else {
         pbase = (int)pfl;
         ib = iblock++;
-        pfl += (int64_t)3 * tile_i;
+        pfl += (int64_t)3 * tile_i * ns;
       }
     }
     const int nsf = (int)segs.size();

@@ -104,11 +104,12 @@ struct alignas(16) Unit {
   int32_t ni;        // i's in the unit
   int32_t len_h;     // hole sources
   int32_t len_e;     // electron sources
-  int32_t nsplit;    // pieces of the tile (> 1: FP64 accumulators + combine)
+  int32_t nsplit;    // pieces of the tile (> 1: FP64 partial sums + combine)
   int32_t iblock;    // combine counter (nsplit > 1)
-  int32_t pbase;     // FP64 offset of the tile's accumulators
+  int32_t pbase;     // FP64 offset of the tile's partial sums: piece k at
+                     // pbase + 3 * tile_i * k
   int32_t ntiles;    // tiles of the slot (its step is done when all are updated)
-  int32_t pad;
+  int32_t split;     // this piece's index k
 };
 static_assert(sizeof(Unit) == 64, "unit descriptor is four 16-byte words");
 constexpr int kUnitElectrons = 1;  // the i's are electrons
@@ -237,7 +238,7 @@ struct StepArgs {
   int32_t* unit_counter;     // [K]: dynamic queue position per step (dynamic plans)
   int32_t dynamic;           // 1: pull units from unit_counter instead of cta_begin
   int32_t* ret;              // [K][S][2]
-  double* partial;           // FP64 accumulators of split tiles (3 x tile_i each, kept zero)
+  double* partial;           // FP64 partial sums of split tiles (3 x tile_i per piece)
   int32_t* combine_count;    // per i-block
   int32_t* tiles_done;       // [K][S]: tiles of each slot updated at each chunk step
   float* field_out;          // FIELD_ONLY output, SoA [3][capacity]

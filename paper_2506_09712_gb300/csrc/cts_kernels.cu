@@ -856,21 +856,23 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
       vz[r] = sz[r] - cz[r];
     }
 
-    // Completion of the tile: each piece adds its compensated sum (S - c of
-    // two FP32 values is exact in FP64) into the tile's FP64 accumulators; the
-    // CTA finishing the tile's last piece reads them once, clears them for the
-    // next step, updates the tile's carriers and counts the tile as done.
+    // Completion of the tile: each piece writes its compensated sum (S - c of
+    // two FP32 values is exact in FP64) to its own FP64 slot; the CTA
+    // finishing the tile's last piece adds the pieces in piece order (the
+    // same bits every run), updates the tile's carriers and counts the tile
+    // as done.
     bool last = true;
     if (U.nsplit > 1) {
       double* acc = a.partial + U.pbase;
       if (!skip) {
+        double* mine = acc + (int64_t)U.split * 3 * TI;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int li = r * NT + tid;
           if (li < U.ni) {
-            atomicAdd(acc + li, (double)sx[r] - (double)cx[r]);
-            atomicAdd(acc + TI + li, (double)sy[r] - (double)cy[r]);
-            atomicAdd(acc + 2 * TI + li, (double)sz[r] - (double)cz[r]);
+            mine[li] = (double)sx[r] - (double)cx[r];
+            mine[TI + li] = (double)sy[r] - (double)cy[r];
+            mine[2 * TI + li] = (double)sz[r] - (double)cz[r];
           }
         }
       }
@@ -889,12 +891,16 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
         for (int r = 0; r < R; ++r) {
           const int li = r * NT + tid;
           if (li < U.ni) {
-            vx[r] = (float)__ldcg(acc + li);
-            vy[r] = (float)__ldcg(acc + TI + li);
-            vz[r] = (float)__ldcg(acc + 2 * TI + li);
-            acc[li] = 0.0;
-            acc[TI + li] = 0.0;
-            acc[2 * TI + li] = 0.0;
+            double ex = 0.0, ey = 0.0, ez = 0.0;
+            for (int k = 0; k < U.nsplit; ++k) {
+              const double* pk = acc + (int64_t)k * 3 * TI;
+              ex += __ldcg(pk + li);
+              ey += __ldcg(pk + TI + li);
+              ez += __ldcg(pk + 2 * TI + li);
+            }
+            vx[r] = (float)ex;
+            vy[r] = (float)ey;
+            vz[r] = (float)ez;
           }
         }
       }

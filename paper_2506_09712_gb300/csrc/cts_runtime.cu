@@ -570,6 +570,7 @@ void device_units(const std::vector<UnitPlan>& plan, const std::vector<SlotGeom>
     d.nsplit = u.nsplit;
     d.iblock = u.iblock;
     d.pbase = u.pbase;
+    d.split = u.split;
     d.ntiles = ntiles[u.slot];
     out[q] = d;
   }
@@ -2369,5 +2370,22 @@ int sim_debug_trajectory(sim_t* s, const sim_event_t* ev, int64_t n_steps, doubl
   s->slots[0] = HostSlot{};
   return rc;
 }
+
+int sim_debug_step(sim_t* s, uint64_t seed, uint64_t event_id, int32_t n, const double* xyz,
+                   const int8_t* sign, double* xyz_out, int8_t* state_out) {
+  if (!s || n < 1 || !xyz || !xyz_out || !state_out) return SIM_EINVAL;
+  sim_event_t ev{};
+  ev.kind = CTS_EXPLICIT;
+  ev.seed = seed;
+  ev.event_id = event_id;
+  ev.n_pairs = n;
+  ev.explicit_xyz = xyz;
+  ev.explicit_sign = sign;
+  int64_t done = 0;
+  const int rc = sim_debug_trajectory(s, &ev, 1, xyz_out, state_out, n, &done);
+  if (rc) return rc;
+  return done == 1 ? SIM_OK : SIM_ESTATE;
+}
+
 
 }  // extern "C"

@@ -1,6 +1,6 @@
 """CPU checks of bench.py's bookkeeping that needs no GPU: the source regions
-the step kernel's DRAM-traffic figure is tied to, and how a stale figure is
-dropped."""
+the symmetric step kernel's DRAM-traffic figure is tied to, and how a stale
+figure is dropped."""
 import json
 import os
 
@@ -19,8 +19,9 @@ def test_hash_regions_exist():
     assert ker.count("// Update alone:") == 1
     assert ker.count("const VariantEntry kVariants[]") == 1
     assert ker.index("const VariantEntry kVariants[]") < ker.index("#undef CTS_V")
-    # the step kernel itself lies inside the hashed part
+    # both step kernels lie inside the hashed part
     assert ker.index("step_kernel(StepArgs a") < ker.index("// Update alone:")
+    assert ker.index("sym_kernel(StepArgs a") < ker.index("// Update alone:")
 
 
 def test_hash_is_deterministic_and_hex():
@@ -30,7 +31,7 @@ def test_hash_is_deterministic_and_hex():
 
 
 def test_traffic_is_dropped_when_the_source_hash_differs(monkeypatch):
-    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    path = os.path.join(ROOT, "profiles", "sym_kernel_traffic.json")
     d = json.load(open(path))
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: d["kernel_source_hash"])
     assert bench.profiled_traffic() == d["dram_bytes_per_launch"]
@@ -39,7 +40,7 @@ def test_traffic_is_dropped_when_the_source_hash_differs(monkeypatch):
 
 
 def test_committed_traffic_summary_is_consistent():
-    d = json.load(open(os.path.join(ROOT, "profiles", "step_kernel_traffic.json")))
+    d = json.load(open(os.path.join(ROOT, "profiles", "sym_kernel_traffic.json")))
     total = d["dram_read_bytes_captured"] + d["dram_write_bytes_captured"]
     assert d["dram_bytes_per_launch_captured"] == total
     # scaled from the captured events to the benchmark's 64-event launch

@@ -221,13 +221,18 @@ def test_trajectory_parity_3keV(steps):
     col = ref.state == oracle.COLLECTED
     d = np.concatenate([np.abs(pos[act] - ref.pos[act]).max(axis=1),
                         np.abs(pos[col, :2] - ref.final_xy[col]).max(axis=1)])
-    # FP32 displacements around FP64 positions differ by ~1e-7 um per step; close
-    # pairs (Euler-unstable below ~0.05 um) amplify that for a few carriers, as
-    # measured in the divergence study of the design notes.  A wrong term would
-    # move every carrier by far more.
-    assert np.median(d) <= 2e-6, np.median(d)
-    assert np.quantile(d, 0.99) <= 5e-4, np.quantile(d, 0.99)
-    assert d.max() <= 2e-2, d.max()
+    # One step from the same FP64 cloud differs by the FP32 rounding of that
+    # step (tests/test_gpu_one_step.py: below 2e-5 of the displacement, a few
+    # 1e-6 um); over more steps close pairs (Euler-unstable below ~0.05 um)
+    # amplify that for a few carriers (the divergence series there: median
+    # 1e-7 um after 10 steps, 2e-5 after 100, maxima 2e-4 and 4e-2 um).  A
+    # wrong term would move every carrier by far more.
+    print(f"\n3 keV trajectory, {steps} steps: |dr| median {np.median(d):.2e} "
+          f"p99 {np.quantile(d, 0.99):.2e} max {d.max():.2e} um")
+    med, p99, mx = {1: (2e-7, 2e-6, 5e-5), 10: (1e-6, 5e-5, 2e-3), 60: (2e-6, 5e-4, 2e-2)}[steps]
+    assert np.median(d) <= med, np.median(d)
+    assert np.quantile(d, 0.99) <= p99, np.quantile(d, 0.99)
+    assert d.max() <= mx, d.max()
 
 
 def _compare_events(gpu, ref, n_carriers):

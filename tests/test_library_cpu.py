@@ -192,9 +192,17 @@ def test_planner_small_work_uses_fewer_ctas(lib):
 
 
 def test_planner_respects_budgets(lib):
+    # every piece of a split tile takes 3 * tile_i partial sums: a budget of
+    # 40 such regions splits a few of the 44 tiles and runs the rest whole
+    cap = 3 * 512 * 40
+    rc, units, begin, pfl = cts.cts_plan_units([5525] * 4, [0] * 4, 512, 456, partial_cap=cap)
+    split_tiles = {tuple(u[:3]) for u in units if u[7] > 1}
+    assert rc == 0 and pfl <= cap and 0 < len(split_tiles) < 44
+    assert _check_cover(units, [5525] * 4, [0] * 4)
+    # a budget smaller than two regions splits nothing
     rc, units, begin, pfl = cts.cts_plan_units([5525] * 4, [0] * 4, 512, 456,
-                                               partial_cap=3 * 512 * 4)
-    assert rc == 0 and pfl <= 3 * 512 * 4 and np.count_nonzero(units[:, 7] > 1) > 0
+                                               partial_cap=3 * 512)
+    assert rc == 0 and pfl == 0 and np.all(units[:, 7] == 1)
     assert _check_cover(units, [5525] * 4, [0] * 4)
     rc, _, _, _ = cts.cts_plan_units([5525] * 64, [0] * 64, 512, 456, max_units=100)
     assert rc == -2
@@ -479,23 +487,30 @@ def test_autotune_cache_file_roundtrip(tmp_path):
 
 @pytest.mark.parametrize("mode", [2, 3])
 def test_dynamic_plans_keep_partial_sums_inside_their_buffer(lib, mode):
-    # split tiles own disjoint 3 * tile_i regions of the FP64 partial-sum
-    # buffer; a plan must never place one beyond the buffer it is given
+    # every piece of a split tile owns its 3 * tile_i region of the FP64
+    # partial-sum buffer (pbase + 3 * tile_i * piece); a plan must never place
+    # one beyond the buffer it is given, and regions never overlap
     tile = 512
-    for cap in (0, 3 * tile, 3 * tile * 5, 3 * tile * 40):
+    for cap in (0, 3 * tile, 3 * tile * 5, 3 * tile * 40, 3 * tile * 400):
         rc, units, begin, pfl = cts.cts_plan_units([5525] * 16, [0] * 16, tile, 608,
                                                    allow_split=mode, partial_cap=cap)
         assert rc == 0 and pfl <= cap
         assert _check_cover(units, [5525] * 16, [0] * 16)
         split = units[units[:, 7] > 1]
         regions = {}
+        used = np.zeros(max(cap, 1), dtype=int)
         for u in split:
-            assert 0 <= u[9] and u[9] + 3 * tile <= cap
-            regions.setdefault((u[0], u[1], u[2]), set()).add((u[8], u[9]))
-        # one (combine counter, region) per tile, different tiles never share one
+            lo = u[9] + 3 * tile * u[6]
+            assert 0 <= u[9] and 0 <= u[6] < u[7] and lo + 3 * tile <= cap
+            used[lo:lo + 3 * tile] += 1
+            regions.setdefault((u[0], u[1], u[2]), set()).add((u[8], u[9], u[7]))
+        assert used.max() <= 1
+        # one (combine counter, base, pieces) per tile, different tiles never share one
         assert all(len(v) == 1 for v in regions.values())
         owners = [next(iter(v)) for v in regions.values()]
         assert len({o[1] for o in owners}) == len(owners) == len({o[0] for o in owners})
+        if cap >= 3 * tile * 400:
+            assert len(split) > 0
 
 
 def test_whole_tile_plan_is_balanced_longest_first(lib):

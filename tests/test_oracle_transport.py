@@ -324,3 +324,20 @@ def test_electrons_below_the_collecting_surface_are_mirrored(orc):
     assert (z > 0).all()
     ratio = np.mean(z ** 2) / np.mean(z) ** 2
     assert ratio == pytest.approx(math.pi / 2, rel=0.02)
+
+
+def test_single_steps_reproduce_the_whole_event(orc):
+    # orc.step (one loop body of Algorithm 1 from a given state, the entry
+    # the one-step parity tests use) taken 20 times from the initial cloud
+    # gives the states and positions of run_event after 20 steps, bit for bit
+    p = W.preset("plain_3keV_100um")
+    ev = W.make_events("plain_3keV_100um", n=1)[0]
+    prm = orc.make_params(dict(p["sensor"], max_steps=20), W.field_switches(), p["mobility"])
+    ref = orc.run_event(prm, ev)
+    pos, sign = orc.init_event(prm, ev)
+    st = np.zeros(len(sign), dtype=np.int8)
+    for k in range(20):
+        pos, st = orc.step(prm, ev["seed"], ev["event_id"], k, pos, sign, st)
+    act = st == orc.ACTIVE
+    assert np.array_equal(st, ref.state)
+    assert np.array_equal(pos[act], ref.pos[act])
