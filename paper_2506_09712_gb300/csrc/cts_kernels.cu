@@ -1873,9 +1873,14 @@ __global__ void bin_points_kernel(Phys ph, const double* x, const double* y, int
 // event runs the chunk's steps by itself (an event's step needs only its own
 // carriers).  Per step: the FP64 centre of the active holes (a fixed-order
 // block reduction), the squared distances as order-preserving 64-bit keys,
-// a bitonic sort in shared memory, the enclosed count Q(<r) = the first
-// position of a key's run in the sorted order, the field k_C Q (r - c) / r^3
-// and the fused update.
+// the enclosed count Q(<r) = the number of keys strictly below a hole's key,
+// the field k_C Q (r - c) / r^3 and the fused update.  Q comes from a
+// counting pass: the keys' span is cut into at most kSphBins bins of equal
+// width in key space (about logarithmic in r^2), Q = the holes in lower bins
+// (an exclusive scan of the bin counts) + the smaller keys of the own bin.
+// A step whose fullest bin holds more than kSphBinMax holes (radii piled up
+// at one value) ranks by a bitonic sort instead: the first position of a
+// key's run in sorted order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
   // warp trees, then thread 0 adds the warp totals in warp order
@@ -1894,12 +1899,45 @@ __device__ __forceinline__ double block_sum_fixed(double v, double* red) {
   return t;
 }
 
+constexpr int kSphBins = 4096;
+constexpr int kSphBinMax = 256;
+
+// Block minimum and maximum of 64-bit keys (every thread gets both).
+__device__ __forceinline__ void block_minmax_u64(unsigned long long& lo, unsigned long long& hi,
+                                                 unsigned long long* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_down_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_down_sync(0xffffffffu, hi, o));
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    red[warp] = lo;
+    red[32 + warp] = hi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w) {
+      red[0] = min(red[0], red[w]);
+      red[32] = max(red[32], red[32 + w]);
+    }
+  }
+  __syncthreads();
+  lo = red[0];
+  hi = red[32];
+  __syncthreads();
+}
+
 template <bool PX>
 __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, int nk) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSphMax]
   int32_t* idx = reinterpret_cast<int32_t*>(key + kSphMax);                    // [kSphMax]
+  int32_t* bstart = idx + kSphMax;                                              // [kSphBins]
+  int32_t* bcount = bstart + kSphBins;                                          // [kSphBins]
   __shared__ double red[33];
+  __shared__ unsigned long long ured[64];
+  __shared__ int32_t wsum[32];
+  __shared__ int s_fallback;
   __shared__ double s_azn;
   const int slot = blockIdx.x;
   if (slot >= a.S) return;
@@ -1951,6 +1989,7 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
     }
     // keys: squared distance from the centre (non-negative doubles order like
     // their bit patterns); retired holes and padding sort last
+    unsigned long long kmin = ~0ull, kmax = 0ull;
     for (int t = tid; t < p2; t += nt) {
       unsigned long long kv = ~0ull;
       if (t < nh) {
@@ -1960,54 +1999,127 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
           const double dx = __ldcg(a.A.px + ai) - sx, dy = __ldcg(a.A.py + ai) - sy,
                        dz = __ldcg(a.A.pz + ai) - sz;
           kv = (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz);
+          kmin = min(kmin, kv);
+          kmax = max(kmax, kv);
         }
       }
       key[t] = kv;
       idx[t] = t;
     }
+    for (int b = tid; b < kSphBins; b += nt) bcount[b] = 0;
+    block_minmax_u64(kmin, kmax, ured);
+    // bins of equal width in key space: the smallest shift with fewer than
+    // kSphBins bins over [kmin, kmax]
+    int shift = 0;
+    while (((kmax - kmin) >> shift) >= (unsigned long long)kSphBins) ++shift;
+    if (tid == 0) s_fallback = 0;
     __syncthreads();
-    for (int size = 2; size <= p2; size <<= 1)
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int t = tid; t < (p2 >> 1); t += nt) {
-          const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
-          const bool up = (lo & size) == 0;
-          const unsigned long long kl = key[lo], kh = key[hi];
-          if ((kl > kh) == up) {
-            key[lo] = kh;
-            key[hi] = kl;
-            const int32_t il = idx[lo];
-            idx[lo] = idx[hi];
-            idx[hi] = il;
-          }
-        }
-        __syncthreads();
+    for (int t = tid; t < nh; t += nt)
+      if (key[t] != ~0ull) atomicAdd(&bcount[(int)((key[t] - kmin) >> shift)], 1);
+    __syncthreads();
+    // exclusive scan of the bin counts (kSphBins / nt per thread), and the
+    // fullest bin
+    {
+      constexpr int kPer = kSphBins / 1024;
+      int local[kPer], acc = 0, most = 0;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        local[q] = tid * kPer + q < kSphBins ? bcount[tid * kPer + q] : 0;
+        most = max(most, local[q]);
+        acc += local[q];
       }
-    // field and update, by sorted position; positions >= nah hold retired
-    // holes (parked shadow only) and padding entries (skipped)
+      const int lane = tid & 31, warp = tid >> 5;
+      int incl = acc;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+      }
+      most = __reduce_max_sync(0xffffffffu, most);
+      if (lane == 31) wsum[warp] = incl;
+      if (lane == 0 && most > kSphBinMax) s_fallback = 1;
+      __syncthreads();
+      if (tid == 0) {
+        int run = 0;
+        for (int w = 0; w < (nt >> 5); ++w) {
+          const int v = wsum[w];
+          wsum[w] = run;
+          run += v;
+        }
+      }
+      __syncthreads();
+      int base = wsum[warp] + incl - acc;
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        if (tid * kPer + q < kSphBins) bstart[tid * kPer + q] = base;
+        base += local[q];
+      }
+    }
+    __syncthreads();
+    const bool fallback = s_fallback != 0;
+    if (!fallback) {
+      // each bin's holes in bin order (the order within a bin does not
+      // matter: a hole counts the smaller keys of its bin)
+      for (int b = tid; b < kSphBins; b += nt) bcount[b] = 0;
+      __syncthreads();
+      for (int t = tid; t < nh; t += nt)
+        if (key[t] != ~0ull) {
+          const int b = (int)((key[t] - kmin) >> shift);
+          idx[bstart[b] + atomicAdd(&bcount[b], 1)] = t;
+        }
+      __syncthreads();
+    } else {
+      for (int size = 2; size <= p2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          for (int t = tid; t < (p2 >> 1); t += nt) {
+            const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+            const bool up = (lo & size) == 0;
+            const unsigned long long kl = key[lo], kh = key[hi];
+            if ((kl > kh) == up) {
+              key[lo] = kh;
+              key[hi] = kl;
+              const int32_t il = idx[lo];
+              idx[lo] = idx[hi];
+              idx[hi] = il;
+            }
+          }
+          __syncthreads();
+        }
+    }
+    // field and update: with the counting pass hole t by its own index, with
+    // the sort by sorted position (positions >= nah hold retired holes, with
+    // a parked shadow only, and padding entries, skipped)
     const float kcf = ph.f_kc;
     const double azn = s_azn;
     double qi = 0.0;
     double qpx[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int j = tid; j < p2; j += nt) {
-      const int t = idx[j];
+    for (int j = tid; j < (fallback ? p2 : nh); j += nt) {
+      const int t = fallback ? idx[j] : j;
       if (t >= nh) continue;
       const int64_t ai = S->base + t;
       float ex = 0.0f, ey = 0.0f, ez = 0.0f;
-      if (j < nah && ph.repulsion) {
-        int q = j;
-        while (q > 0 && key[q - 1] == key[j]) --q;
-        if (q > 0) {
-          // offsets and the enclosed count in FP64, the field itself in FP32
-          // like the pairwise path (FP64 sqrt and division are slow here)
-          const float dx = (float)(__ldcg(a.A.px + ai) - sx),
-                      dy = (float)(__ldcg(a.A.py + ai) - sy),
-                      dz = (float)(__ldcg(a.A.pz + ai) - sz);
-          const float rs = rsqrtf((float)__longlong_as_double((long long)key[j]));
-          const float f = kcf * (float)q * rs * rs * rs;
-          ex = f * dx;
-          ey = f * dy;
-          ez = f * dz;
+      const unsigned long long kt = fallback ? key[j] : key[t];
+      int q = 0;
+      if (kt != ~0ull && ph.repulsion) {
+        if (fallback) {
+          q = j;
+          while (q > 0 && key[q - 1] == kt) --q;
+        } else {
+          const int b = (int)((kt - kmin) >> shift);
+          q = bstart[b];
+          for (int u = bstart[b]; u < bstart[b] + bcount[b]; ++u) q += key[idx[u]] < kt;
         }
+      }
+      if (q > 0) {
+        // offsets and the enclosed count in FP64, the field itself in FP32
+        // like the pairwise path (FP64 sqrt and division are slow here)
+        const float dx = (float)(__ldcg(a.A.px + ai) - sx),
+                    dy = (float)(__ldcg(a.A.py + ai) - sy),
+                    dz = (float)(__ldcg(a.A.pz + ai) - sz);
+        const float rs = rsqrtf((float)__longlong_as_double((long long)kt));
+        const float f = kcf * (float)q * rs * rs * rs;
+        ex = f * dx;
+        ey = f * dy;
+        ez = f * dz;
       }
       qi += update_carrier<PX ? 2 : 1>(a, S, slot, 0, ai, step, p, k, ex, ey, ez, azn, qpx);
     }
@@ -2343,7 +2455,8 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
   return cudaGetLastError();
 }
 
-constexpr size_t kSphSmem = (size_t)kSphMax * (sizeof(unsigned long long) + sizeof(int32_t));
+constexpr size_t kSphSmem =
+    (size_t)kSphMax * (sizeof(unsigned long long) + sizeof(int32_t)) + 2 * kSphBins * sizeof(int32_t);
 
 cudaError_t spherical_prepare() {
   const cudaError_t e = cudaFuncSetAttribute(

@@ -86,3 +86,30 @@ def test_spherical_rejects_events_beyond_the_sort_size():
         ok = dict(W.make_events(name, n=1)[0], n_pairs=16384, depth_um=300.0)
         r = sim.run([ok])[0]
         assert r["status"] == 0 and r["n_carriers"] == 16384
+
+
+def test_spherical_equal_radii_take_the_sorting_path():
+    # 300 holes at one radius and 300 at a larger one (the six axis points
+    # (+-a, 0, 0), (0, +-a, 0), (0, 0, +-a) repeated, so the centre is 0 and
+    # the squared radii are equal to the bit): the counting pass finds more
+    # than 256 holes in one bin and ranks by sorting.  Equal radii do not
+    # count each other: the inner shell feels no field, the outer one the
+    # inner 300.  One step without drift and diffusion, constant mobility.
+    name = "batch_20keV_320um"
+    p = W.preset(name)
+    mob = dict(p["mobility"], model=W.MOB_CONST)
+    field = W.field_switches(spherical=1, drift=0, diffusion=0)
+    axes = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]],
+                    dtype=float)
+    centre = np.array([0.0, 0.0, 160.0])
+    xyz = np.concatenate([np.tile(axes * 0.5, (50, 1)), np.tile(axes * 2.0, (50, 1))]) + centre
+    ev = W.explicit_event(xyz, seed=5, event_id=7)
+    ref = oracle.run_event(oracle.make_params(dict(p["sensor"], max_steps=1), field, mob), ev)
+    with cts.Simulator(p["sensor"], mob, field) as sim:
+        pos, st, done = sim.trajectory(dict(ev, n_carriers=600), 1)
+    assert done == ref.n_steps == 1
+    assert np.array_equal(st, ref.state)
+    moved = np.linalg.norm(ref.pos - xyz, axis=1)
+    assert np.all(moved[:300] == 0.0) and np.all(moved[300:] > 0.0)
+    d = np.abs(pos - ref.pos).max(axis=1)
+    assert d.max() < 1e-6 * moved.max()
