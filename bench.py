@@ -619,6 +619,8 @@ def run_ours(args, rank, world, local):
             # each) would need for the same interactions/s in this kernel
             "direct_equivalent_tflops": FLOPS_PER_PAIR * dom_inter / (dom_ms * 1e-3) / 1e12
             if dom_ms > 0 else None,
+            "frac_direct_equivalent": FLOPS_PER_PAIR * dom_inter / (dom_ms * 1e-3) / 1e12
+            / peak_tflops if dom_ms > 0 else None,
             "kernel_ms": dom_ms, "kernel_launches": int(len(rows)),
             "interactions_in_kernel": dom_inter,
             "kernel_mix_ms": {"symmetric": sym_ms, "per_pair": pair_ms},

@@ -126,10 +126,10 @@ typedef struct sim_options_t {
   int64_t hbm_budget_bytes;/* device bytes the handle may allocate (default 1 GiB) */
   int32_t queue_capacity;  /* bound of the admission queue (default 65536) */
   int32_t variant;         /* pair-kernel variant + 1; 0 = default choice: per
-                              chunk, the symmetric kernel (variant 1) when the
-                              running events hold at least 6.4e8 carrier pairs
-                              (sum of N^2), the per-pair kernel (variant 2)
-                              below that */
+                              chunk, the symmetric kernel (variant 13) when
+                              the running events hold at least 6.4e8 carrier
+                              pairs (sum of N^2), the per-pair kernel
+                              (variant 2) below that; PLAIN: variant 1 */
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
   int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */
   int32_t time_launches;   /* 1 = time every step-kernel launch with CUDA events */

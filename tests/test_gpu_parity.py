@@ -229,7 +229,9 @@ def test_trajectory_parity_3keV(steps):
     # wrong term would move every carrier by far more.
     print(f"\n3 keV trajectory, {steps} steps: |dr| median {np.median(d):.2e} "
           f"p99 {np.quantile(d, 0.99):.2e} max {d.max():.2e} um")
-    med, p99, mx = {1: (2e-7, 2e-6, 5e-5), 10: (1e-6, 5e-5, 2e-3), 60: (2e-6, 5e-4, 2e-2)}[steps]
+    # measured on GB300 (median, 99 %, max in um): 1 step 6e-8, 3e-7, 1.6e-6;
+    # 10 steps 4e-7, 1.4e-5, 5.6e-5; 60 steps 1.3e-6, 8.5e-5, 1.1e-4
+    med, p99, mx = {1: (2e-7, 2e-6, 2e-5), 10: (1e-6, 5e-5, 5e-4), 60: (3e-6, 5e-4, 2e-3)}[steps]
     assert np.median(d) <= med, np.median(d)
     assert np.quantile(d, 0.99) <= p99, np.quantile(d, 0.99)
     assert d.max() <= mx, d.max()
