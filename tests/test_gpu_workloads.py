@@ -2,7 +2,9 @@
 cluster-size and single-pixel-spectrum distributions against the oracle), the
 two-species electron-track events, and continuous batching in SERVE mode
 (a result is the same alone and in a live mix)."""
+import json
 import math
+import os
 import threading
 import time
 
@@ -47,37 +49,66 @@ def pixel_spectrum(pix):
     return win[win >= 1.0]
 
 
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "uneven_5_25keV_450um_oracle200.json")
+
+
 @pytest.mark.slow
 def test_uneven_batch_1e4_events_ks_against_oracle():
+    # 10^4 events of E ~ U(5, 25) keV in 450 um Si on the GPU against the FP64
+    # oracle's first 200 events (tests/golden/, written by the committed
+    # make_uneven_oracle.py): the shared 200 event by event, then the
+    # cluster-size and single-pixel-spectrum distributions (Sec. 4.2) by
+    # two-sample KS tests.
     name = "uneven_5_25keV_450um"
     p = W.preset(name)
     evs = W.make_events(name, n=10_000)
+    with open(GOLDEN) as fh:
+        refs = json.load(fh)["results"]
+    n_ref = len(refs)
+    assert n_ref == 200 and [r["event_id"] for r in refs] == list(range(200))
+    # the oracle's events are the workload's 200-event list (its depths are
+    # drawn for the list as a whole, so it is not a prefix of the 10^4 list);
+    # the energies and depths the oracle ran are taken from the file (another
+    # machine's numpy may round the drawn depths differently in the last bit)
+    evs_ref = W.make_events(name, n=200)
+    for e, r in zip(evs_ref, refs):
+        assert e["depth_um"] == pytest.approx(r["depth_um"], rel=1e-12)
+        e["depth_um"], e["energy_keV"] = r["depth_um"], r["energy_keV"]
     with cts.Simulator(p["sensor"], p["mobility"], max_slots=512) as sim:
         res = sim.run(evs)
-    assert all(r["status"] == 0 for r in res)
-    n_ref = 16
-    refs = oracle.run_events(_params(name), evs[:n_ref])
-    # The shared events agree one by one.  These events take up to ~3000 steps;
-    # forward Euler is locally unstable for pairs closer than (2 mu k dt)^(1/3)
-    # ~ 0.05 um, so FP32 and FP64 trajectories part slowly and a few carriers
-    # near pixel edges may land differently: most events stay within 1e-3 of N
-    # per pixel, all within 1e-2, and the distributions below are binding.
-    within = 0
-    for g, r in zip(res[:n_ref], refs):
+        res_ref = sim.run(evs_ref)
+    assert all(r["status"] == 0 for r in res + res_ref)
+    # The shared events one by one.  They take up to ~3000 steps; forward
+    # Euler is locally unstable for pairs closer than (2 mu k dt)^(1/3) ~
+    # 0.05 um, so FP32 and FP64 trajectories part slowly and a few carriers
+    # near pixel edges may land differently: every event stays within
+    # 1e-2 N per pixel, at least 85 % within the 1e-3 N target (measured on
+    # GB300: 184 of 200, the worst 1.7e-3 N), and the distributions are the
+    # binding test (measured: KS p = 1.0 for the cluster sizes, 0.86 for the
+    # spectrum).
+    within, worst = 0, 0.0
+    for g, r in zip(res_ref, refs):
         n = g["n_carriers"]
-        assert g["n_collected"] == r.n_collected == n
-        assert abs(g["n_steps"] - r.n_steps) <= 2
-        dmax = np.abs(g["pixels"] - r.pixels).max()
+        assert n == r["n_carriers"]
+        assert g["n_collected"] == r["n_collected"] == n
+        assert abs(g["n_steps"] - r["n_steps"]) <= 2
+        dmax = np.abs(g["pixels"] - np.asarray(r["pixels"])).max()
+        worst = max(worst, dmax / n)
         assert dmax <= 1e-2 * n
         within += dmax <= 1e-3 * n
-    assert within >= 0.75 * n_ref
-    # distributions of the 10^4-event run against the oracle's sample
+    frac = within / n_ref
+    # distributions of the 10^4-event run against the oracle's 200 events
     cs_gpu = [cluster_size(r["pixels"]) for r in res]
-    cs_ref = [cluster_size(r.pixels) for r in refs]
+    cs_ref = [cluster_size(np.asarray(r["pixels"])) for r in refs]
     sp_gpu = np.concatenate([pixel_spectrum(r["pixels"]) for r in res])
-    sp_ref = np.concatenate([pixel_spectrum(r.pixels) for r in refs])
-    assert stats.ks_2samp(cs_gpu, cs_ref).pvalue > 0.01
-    assert stats.ks_2samp(sp_gpu, sp_ref).pvalue > 0.01
+    sp_ref = np.concatenate([pixel_spectrum(np.asarray(r["pixels"])) for r in refs])
+    p_cs = stats.ks_2samp(cs_gpu, cs_ref).pvalue
+    p_sp = stats.ks_2samp(sp_gpu, sp_ref).pvalue
+    print(f"\nuneven 1e4 vs oracle 200: {within}/{n_ref} events within 1e-3 N per pixel "
+          f"(worst {worst:.2e} N); KS p cluster size {p_cs:.3g}, spectrum {p_sp:.3g}")
+    assert frac >= 0.85
+    assert p_cs > 0.01
+    assert p_sp > 0.01
     # charge conservation over the whole run
     tot = sum(r["pixels"].sum() + r["n_outside"] for r in res)
     assert tot == sum(r["n_carriers"] for r in res)
