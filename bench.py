@@ -383,9 +383,10 @@ def spherical_leg(cts, W, torch, device, stream, events, p):
             torch.cuda.synchronize()
             res = sim.collect(len(events))
             ms.append(e0.elapsed_time(e1))
+        cluster = sim.stats()["sph_cluster"]
     t = min(ms[1:])
     return {"field": "spherical (Eq. 7)", "events": len(events), "ms_per_batch": t,
-            "events_per_s": len(events) / (t * 1e-3),
+            "events_per_s": len(events) / (t * 1e-3), "ctas_per_event": cluster,
             "statuses_ok": all(r["status"] == 0 for r in res)}
 
 

@@ -143,6 +143,10 @@ typedef struct sim_options_t {
   const char* autotune_cache; /* file of a variant table (cts_host.h): loaded by
                               sim_init when it matches this device and build,
                               written by sim_autotune; NULL = none */
+  int32_t sph_cluster;     /* spherical model: CTAs per event (1, 2 or 4); 0 =
+                              the widest with which all max_slots events are
+                              resident at once.  Results do not depend on it. */
+  int32_t reserved;
 } sim_options_t;
 
 /* One event (Algorithm 1 inputs: E, absorption depth h, plus the entry point).
@@ -224,7 +228,7 @@ typedef struct sim_stats_t {
   int32_t symmetric;        /* 1: the variant in use evaluates each unordered pair
                                once and adds it to both carriers (Newton's third
                                law); 0: every ordered pair */
-  int32_t reserved;
+  int32_t sph_cluster;      /* spherical model: CTAs per event; 0 otherwise */
 } sim_stats_t;
 
 typedef struct sim_t sim_t;

@@ -57,7 +57,8 @@ class sim_options_t(C.Structure):
                 ("variant", C.c_int32), ("disable_graphs", C.c_int32),
                 ("keep_final_xy", C.c_int32), ("time_launches", C.c_int32),
                 ("keep_induced", C.c_int32), ("step_launches", C.c_int32),
-                ("stream", C.c_void_p), ("autotune_cache", C.c_char_p)]
+                ("stream", C.c_void_p), ("autotune_cache", C.c_char_p),
+                ("sph_cluster", C.c_int32), ("reserved", C.c_int32)]
 
 
 class sim_readout_params_t(C.Structure):
@@ -105,7 +106,7 @@ class sim_stats_t(C.Structure):
                 ("sm_count", C.c_int32), ("variant", C.c_int32), ("device_ms", C.c_double),
                 ("step_kernel_ms", C.c_double), ("step_kernel_launches", C.c_int64),
                 ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
-                ("symmetric", C.c_int32), ("reserved", C.c_int32)]
+                ("symmetric", C.c_int32), ("sph_cluster", C.c_int32)]
 
 
 class cts_unit_t(C.Structure):

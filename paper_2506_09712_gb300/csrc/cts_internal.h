@@ -281,13 +281,18 @@ cudaError_t launch_bin(const Phys& ph, Arena A, const SlotDev* slots, const int3
                        int n, int32_t* pixels, SlotReadout* readout, cudaStream_t s);
 cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, int64_t n,
                               int32_t* pixels, long long* outside, cudaStream_t s);
-// Simplified spherical model: one CTA per slot for steps k0 .. k0 + nk - 1;
-// events of at most kSphMax holes (sorted in shared memory).
+// Simplified spherical model: one cluster of `cluster` CTAs (1, 2 or 4) per
+// slot for steps k0 .. k0 + nk - 1; events of at most kSphMax holes (keys in
+// shared memory).
 constexpr int kSphMax = 16384;
 // spherical_prepare raises the kernel's shared-memory limit on the current
-// device (once per handle, at sim_init, outside any stream capture).
+// device and finds how many clusters of each width are resident at once
+// (once per handle, at sim_init, outside any stream capture).
 cudaError_t spherical_prepare();
-cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s);
+// The cluster width for `slots` resident events: `request` when it is 1, 2
+// or 4, else the widest with which all slots' clusters are resident at once.
+int spherical_cluster(int slots, int request);
+cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, int cluster, cudaStream_t s);
 
 // Fast generation from the generalised Gaussian model: one CTA per event.
 struct GenEvent {

@@ -13,6 +13,7 @@
 //   init_kernel   the initial cloud of each new event (Algorithm 1, Eq. 2).
 //   close_kernel  end-of-chunk bookkeeping and order-preserving compaction.
 //   bin_kernel    warp-aggregated pixel readout of collected holes.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <curand_kernel.h>
 
@@ -407,40 +408,32 @@ __device__ __noinline__ void window_potentials(double x, double y, double z, dou
   }
 }
 
-// Position update of one carrier (Eqs. 3, 5, 6; Sec. 2.1) with the field E
-// (V/um) of its step, collection/exit and the next shadow entry.  When the
-// induced charge is recorded, returns H times the charge (units of e) the
-// move induces on the collecting surface (Shockley-Ramo, weighting potential
-// 1 - z/H, the end point held on [0, H]); else 0.  IND: 0 records nothing,
-// 1 the whole surface, 2 also adds q (phi(end) - phi(start)) of the 3 x 3
-// window's pixels to qpx.
-template <int IND>
-__device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, int slot, int spec,
-                                               int64_t idx, int step, int p, int k, float Ex,
-                                               float Ey, float Ez, double azn,
-                                               double* qpx = nullptr) {
+// Position update of one active carrier (Eqs. 3, 5, 6; Sec. 2.1) at arena
+// index idx, carrier id and state st, position (x, y, z) at the start of the
+// step, with the field E (V/um) of its step: collection/exit and (SHADOW) the
+// next shadow entry.  When the induced charge is recorded, returns H times
+// the charge (units of e) the move induces on the collecting surface
+// (Shockley-Ramo, weighting potential 1 - z/H, the end point held on [0, H]);
+// else 0.  IND: 0 records nothing, 1 the whole surface, 2 also adds
+// q (phi(end) - phi(start)) of the 3 x 3 window's pixels to qpx.  *retired
+// (when given) is set when the carrier left.
+template <int IND, bool SHADOW = true>
+__device__ __forceinline__ double update_carrier_at(const StepArgs& a, SlotDev* S, int slot,
+                                                  int spec, int64_t idx, int id, int8_t st,
+                                                  double x, double y, double z, int step, int p,
+                                                  int k, float Ex, float Ey, float Ez, double azn,
+                                                  double* qpx = nullptr,
+                                                  bool* retired = nullptr) {
   const Phys& ph = a.ph;
-  float4* __restrict__ shout = a.A.sh[p ^ 1];
-#ifdef CTS_BOUNDS_CHECK
-  if (idx < 0 || idx >= a.A.capacity || slot < 0 || slot >= a.S || k < 0 || k >= kMaxK) {
-    atomicOr(a.err, kErrBounds);
-    return 0.0;
-  }
-#endif
-  const int id = a.A.cid[idx];
+  [[maybe_unused]] float4* __restrict__ shout = a.A.sh[p ^ 1];
   const int64_t rid = S->base + id;
 #ifdef CTS_BOUNDS_CHECK
-  if (id < 0 || id >= S->n_total || rid < 0 || rid >= a.A.capacity) {
+  if (idx < 0 || idx >= a.A.capacity || slot < 0 || slot >= a.S || k < 0 || k >= kMaxK ||
+      id < 0 || id >= S->n_total || rid < 0 || rid >= a.A.capacity) {
     atomicOr(a.err, kErrBounds);
     return 0.0;
   }
 #endif
-  const int8_t st = __ldcg(a.A.cstate + rid);
-  if ((st & kStateMask) != kStateActive) {
-    shout[idx] = make_float4(kParked, kParked, kParked, 0.0f);
-    return 0.0;
-  }
-  double x = __ldcg(a.A.px + idx), y = __ldcg(a.A.py + idx), z = __ldcg(a.A.pz + idx);
   [[maybe_unused]] const double x_start = x, y_start = y, z_start = z;
   if (ph.drift) Ez -= drift_E(ph, (float)z);
   const float Em = sqrtf(Ex * Ex + Ey * Ey + Ez * Ez);
@@ -469,6 +462,7 @@ __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, 
   a.A.px[idx] = x;
   a.A.py[idx] = y;
   a.A.pz[idx] = z;
+  if (retired) *retired = retire != 0;
   if (retire) {
     a.A.cstate[rid] = (int8_t)((st & kElectronBit) | retire);
     a.A.rstep[rid] = step;
@@ -477,13 +471,14 @@ __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, 
       a.A.fy[rid] = y;
     }
     atomicAdd(&a.ret[((int64_t)k * a.S + slot) * 2 + spec], 1);
-    shout[idx] = make_float4(kParked, kParked, kParked, 0.0f);
-  } else {
+    if constexpr (SHADOW) shout[idx] = make_float4(kParked, kParked, kParked, 0.0f);
+  } else if constexpr (SHADOW) {
     shout[idx] = make_float4((float)(x - S->ax), (float)(y - S->ay), (float)(z - azn), 0.0f);
   }
   if constexpr (IND == 0) {
     return 0.0;
   } else {
+    if (IND == 1 && !a.induced) return 0.0;
     const double zb = fmin(fmax(z, 0.0), ph.H);
     if constexpr (IND == 2) {
       float w0[9], w1[9];
@@ -498,6 +493,37 @@ __device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, 
     if (!a.induced) return 0.0;
     return spec ? zb - z_start : z_start - zb;
   }
+}
+
+// update_carrier_at for the carrier at arena index idx, its id, state and
+// position read here; a carrier that is not active gets a parked shadow.
+template <int IND, bool SHADOW = true>
+__device__ __forceinline__ double update_carrier(const StepArgs& a, SlotDev* S, int slot, int spec,
+                                               int64_t idx, int step, int p, int k, float Ex,
+                                               float Ey, float Ez, double azn,
+                                               double* qpx = nullptr) {
+#ifdef CTS_BOUNDS_CHECK
+  if (idx < 0 || idx >= a.A.capacity) {
+    atomicOr(a.err, kErrBounds);
+    return 0.0;
+  }
+#endif
+  const int id = a.A.cid[idx];
+  const int64_t rid = S->base + id;
+#ifdef CTS_BOUNDS_CHECK
+  if (id < 0 || id >= S->n_total || rid < 0 || rid >= a.A.capacity) {
+    atomicOr(a.err, kErrBounds);
+    return 0.0;
+  }
+#endif
+  const int8_t st = __ldcg(a.A.cstate + rid);
+  if ((st & kStateMask) != kStateActive) {
+    if constexpr (SHADOW) a.A.sh[p ^ 1][idx] = make_float4(kParked, kParked, kParked, 0.0f);
+    return 0.0;
+  }
+  const double x = __ldcg(a.A.px + idx), y = __ldcg(a.A.py + idx), z = __ldcg(a.A.pz + idx);
+  return update_carrier_at<IND, SHADOW>(a, S, slot, spec, idx, id, st, x, y, z, step, p, k, Ex,
+                                        Ey, Ez, azn, qpx);
 }
 
 // Adds a warp's induced charges (H times, from update_carrier) to the slot's
@@ -1866,169 +1892,276 @@ __global__ void bin_points_kernel(Phys ph, const double* x, const double* y, int
 }
 
 // ---------------------------------------------------------------------------
-// Test hooks.
+// Simplified spherical model (Sec. 2.2, Eq. 7), holes only.  One cluster of
+// C CTAs (C = 1, 2 or 4, chosen by the host so that the resident events fill
+// the SMs) runs all K steps of a chunk for one event: an event's step needs
+// only its own carriers.  CTA r of the cluster owns a contiguous range of the
+// event's holes, whole groups of kSphGroup.  Per step:
+//  1. the centre of the active holes in FP64: every group is summed in a
+//     fixed order (lane l adds holes l, l + 32, ... of the group, then a lane
+//     tree), the group sums likewise (group g by lane g mod 32, then a lane
+//     tree; the other CTAs' group sums read through distributed shared
+//     memory), so the centre does not depend on C;
+//  2. the keys of the own holes: the squared distance's FP64 bit pattern
+//     (non-negative doubles order like their bits), written to the arena's
+//     second FP32 shadow (8 bytes of each 16-byte entry); the FP32 offset
+//     from the centre and the carrier id go to the first shadow.  The
+//     spherical model uses neither shadow for anything else;
+//  3. after a cluster barrier every CTA bins all keys of the event in shared
+//     memory (bins of equal width in key space over the keys' range at the
+//     previous step of the chunk, about logarithmic in r^2; keys outside go
+//     to the end bins) and lists each bin's keys;
+//  4. the enclosed count Q(<r) = the number of keys strictly below a hole's
+//     key: the keys of lower bins (the bin's list start) plus the smaller
+//     keys of its own bin; the field k_C Q (r - c) / r^3 and the fused
+//     update of the own holes.
+// A step whose fullest bin holds more than kSphBinMax keys (radii piled up
+// at one value) ranks by a bitonic sort of all keys in every CTA instead: the
+// first position of a key's run in sorted order.  Q is an exact count either
+// way, so the results depend neither on the bins nor on C.  FP64 arithmetic
+// is slow on this GPU, so a hole costs few FP64 operations per step: three
+// adds for the centre, six for its key, three conversions for its offset,
+// and the update's own.  The holes' states live in shared memory during a
+// launch (read from the arena at its first step), so each pass issues all of
+// a hole's global loads at once.
 // ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
-// Simplified spherical model (Sec. 2.2, Eq. 7), holes only: one CTA per
-// event runs the chunk's steps by itself (an event's step needs only its own
-// carriers).  Per step: the FP64 centre of the active holes (a fixed-order
-// block reduction), the squared distances as order-preserving 64-bit keys,
-// the enclosed count Q(<r) = the number of keys strictly below a hole's key,
-// the field k_C Q (r - c) / r^3 and the fused update.  Q comes from a
-// counting pass: the keys' span is cut into at most kSphBins bins of equal
-// width in key space (about logarithmic in r^2), Q = the holes in lower bins
-// (an exclusive scan of the bin counts) + the smaller keys of the own bin.
-// A step whose fullest bin holds more than kSphBinMax holes (radii piled up
-// at one value) ranks by a bitonic sort instead: the first position of a
-// key's run in sorted order.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ double block_sum_fixed(double v, double* red) {
-  // warp trees, then thread 0 adds the warp totals in warp order
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) red[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0) {
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    red[32] = t;
-  }
-  __syncthreads();
-  t = red[32];
-  __syncthreads();
-  return t;
-}
-
 constexpr int kSphBins = 4096;
 constexpr int kSphBinMax = 256;
+constexpr int kSphGroup = 256;
+constexpr int kSphGroups = kSphMax / kSphGroup;
 
-// Block minimum and maximum of 64-bit keys (every thread gets both).
-__device__ __forceinline__ void block_minmax_u64(unsigned long long& lo, unsigned long long& hi,
-                                                 unsigned long long* red) {
-  for (int o = 16; o > 0; o >>= 1) {
-    lo = min(lo, __shfl_down_sync(0xffffffffu, lo, o));
-    hi = max(hi, __shfl_down_sync(0xffffffffu, hi, o));
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (lane == 0) {
-    red[warp] = lo;
-    red[32 + warp] = hi;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < nw; ++w) {
-      red[0] = min(red[0], red[w]);
-      red[32] = max(red[32], red[32 + w]);
-    }
-  }
-  __syncthreads();
-  lo = red[0];
-  hi = red[32];
-  __syncthreads();
+__device__ __forceinline__ unsigned long long shfl_down_u64(unsigned long long v, int o) {
+  return (unsigned long long)__shfl_down_sync(0xffffffffu, (long long)v, o);
+}
+
+// Bin of a key in the range [lo, lo + (kSphBins << shift)).
+__device__ __forceinline__ int sph_bin(unsigned long long kv, unsigned long long lo, int shift) {
+  if (kv <= lo) return 0;
+  const unsigned long long b = (kv - lo) >> shift;
+  return b >= (unsigned long long)kSphBins ? kSphBins - 1 : (int)b;
+}
+
+// The smallest shift with fewer than kSphBins bins over [lo, hi].
+__device__ __forceinline__ int sph_shift(unsigned long long lo, unsigned long long hi) {
+  if (hi <= lo) return 0;
+  const int bits = 64 - __clzll((long long)(hi - lo));  // bit length of the span
+  return bits > 12 ? bits - 12 : 0;
 }
 
 template <bool PX>
 __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, int nk) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), rank = (int)cl.block_rank();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  unsigned long long* key = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSphMax]
-  int32_t* idx = reinterpret_cast<int32_t*>(key + kSphMax);                    // [kSphMax]
-  int32_t* bstart = idx + kSphMax;                                              // [kSphBins]
-  int32_t* bcount = bstart + kSphBins;                                          // [kSphBins]
-  __shared__ double red[33];
-  __shared__ unsigned long long ured[64];
+  unsigned long long* kb = reinterpret_cast<unsigned long long*>(smem_raw);  // [kSphMax]
+  uint16_t* idx = reinterpret_cast<uint16_t*>(kb + kSphMax);                  // [kSphMax]
+  int32_t* bstart = reinterpret_cast<int32_t*>(idx + kSphMax);                // [kSphBins]
+  int32_t* bcount = bstart + kSphBins;                                         // [kSphBins]
+  double* gsum = reinterpret_cast<double*>(bcount + kSphBins);                 // [kSphGroups][4]
+  int8_t* act = reinterpret_cast<int8_t*>(gsum + 4 * kSphGroups);             // [kSphMax]
   __shared__ int32_t wsum[32];
-  __shared__ int s_fallback;
+  __shared__ int s_most;
+  __shared__ int s_nah;
+  __shared__ double s_c[3];
   __shared__ double s_azn;
-  const int slot = blockIdx.x;
+  __shared__ unsigned long long s_rng[2];  // the keys' range: this step's, being found
+  __shared__ unsigned long long s_lo;      // the bins' range
+  __shared__ int s_shift;
+  const int slot = blockIdx.x / C;
   if (slot >= a.S) return;
   SlotDev* S = a.slots + slot;
   if (!S->running) return;
   const int nh = S->n_h;
   if (nh <= 0 || nh > kSphMax) {
-    if (nh > kSphMax && threadIdx.x == 0) atomicOr(a.err, kErrPlan);
+    if (nh > kSphMax && threadIdx.x == 0 && rank == 0) atomicOr(a.err, kErrPlan);
     return;
   }
 #ifdef CTS_BOUNDS_CHECK
   if (!slot_in_arena(a.A, S) || nh > S->cap_h || k0 < 0 || k0 + nk > kMaxK) {
-    if (threadIdx.x == 0) atomicOr(a.err, kErrBounds);
+    if (threadIdx.x == 0 && rank == 0) atomicOr(a.err, kErrBounds);
     return;
   }
 #endif
+  // every CTA of the cluster passes this point (the tests above read the
+  // same slot), so the cluster barriers below are uniform
   int p2 = 2;
   while (p2 < nh) p2 <<= 1;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+  const int ng = (nh + kSphGroup - 1) / kSphGroup;  // groups of kSphGroup holes
+  const int gpc = (ng + C - 1) / C;                   // groups per CTA
+  const int g0 = min(ng, rank * gpc), g1 = min(ng, g0 + gpc);
+  const int lo = g0 * kSphGroup, hi = min(nh, g1 * kSphGroup), m = hi - lo;  // own holes
+  const unsigned long long kNone = ~0ull;
+  const int64_t base = S->base;
+  // per hole: FP32 offset and id (first shadow), key (second shadow)
+  float4* __restrict__ off = a.A.sh[0];
+  unsigned long long* __restrict__ kscr = reinterpret_cast<unsigned long long*>(a.A.sh[1]);
   const Phys& ph = a.ph;
+  for (int t = lo + tid; t < hi; t += nt) act[t - lo] = __ldcg(a.A.cstate + base + a.A.cid[base + t]);
+  if (tid == 0) {
+    s_rng[0] = kNone;
+    s_rng[1] = 0ull;
+  }
+  __syncthreads();
   for (int kq = 0; kq < nk; ++kq) {
     const int k = k0 + kq;
     const int step = S->step0 + k;
     const int p = step & 1;
-    // centre of the active holes
-    double sx = 0.0, sy = 0.0, sz = 0.0, cnt = 0.0;
-    for (int t = tid; t < nh; t += nt) {
-      const int64_t ai = S->base + t;
-      const int8_t st = __ldcg(a.A.cstate + S->base + a.A.cid[ai]);
-      if ((st & kStateMask) != kStateActive) continue;
-      sx += __ldcg(a.A.px + ai);
-      sy += __ldcg(a.A.py + ai);
-      sz += __ldcg(a.A.pz + ai);
-      cnt += 1.0;
+    // 1. group sums of the own groups
+    for (int g = g0 + warp; g < g1; g += nt >> 5) {
+      double x = 0.0, y = 0.0, z = 0.0;
+      int c = 0;
+#pragma unroll
+      for (int r = 0; r < kSphGroup / 32; ++r) {
+        const int t = g * kSphGroup + r * 32 + lane;
+        if (t < nh && (act[t - lo] & kStateMask) == kStateActive) {
+          x += __ldcg(a.A.px + base + t);
+          y += __ldcg(a.A.py + base + t);
+          z += __ldcg(a.A.pz + base + t);
+          ++c;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+        z += __shfl_down_sync(0xffffffffu, z, o);
+      }
+      c = __reduce_add_sync(0xffffffffu, c);
+      if (lane == 0) {
+        gsum[4 * g + 0] = x;
+        gsum[4 * g + 1] = y;
+        gsum[4 * g + 2] = z;
+        gsum[4 * g + 3] = (double)c;
+      }
     }
-    cnt = block_sum_fixed(cnt, red);
-    const int nah = (int)cnt;
+    cl.sync();
+    // 2. the centre from all groups of the cluster (the three divisions on
+    // lanes 0, 1, 2 at once); the bins' range: the previous step's keys
+    if (warp == 0) {
+      double x = 0.0, y = 0.0, z = 0.0, c = 0.0;
+      for (int g = lane; g < ng; g += 32) {
+        const int r = g / gpc;
+        const double* src = r == rank ? gsum : cl.map_shared_rank(gsum, r);
+        x += src[4 * g + 0];
+        y += src[4 * g + 1];
+        z += src[4 * g + 2];
+        c += src[4 * g + 3];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_down_sync(0xffffffffu, x, o);
+        y += __shfl_down_sync(0xffffffffu, y, o);
+        z += __shfl_down_sync(0xffffffffu, z, o);
+        c += __shfl_down_sync(0xffffffffu, c, o);
+      }
+      x = __shfl_sync(0xffffffffu, x, 0);
+      y = __shfl_sync(0xffffffffu, y, 0);
+      z = __shfl_sync(0xffffffffu, z, 0);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (lane < 3) s_c[lane] = (lane == 0 ? x : lane == 1 ? y : z) / c;
+      if (lane == 0) {
+        s_nah = (int)c;
+        s_lo = s_rng[0];
+        s_shift = sph_shift(s_rng[0], s_rng[1]);
+        s_rng[0] = kNone;
+        s_rng[1] = 0ull;
+        s_most = 0;
+      }
+    }
+    for (int b = tid; b < kSphBins; b += nt) bcount[b] = 0;
+    __syncthreads();
+    const int nah = s_nah;
     if (nah <= 0 || (int64_t)step >= ph.max_steps) break;
-    sx = block_sum_fixed(sx, red) / cnt;
-    sy = block_sum_fixed(sy, red) / cnt;
-    sz = block_sum_fixed(sz, red) / cnt;
+    const double sx = s_c[0], sy = s_c[1], sz = s_c[2];
     if (tid == 0) {
       const double azn = anchor_next(ph, 0, __ldcg(&S->az[p][0]));
       s_azn = azn;
-      atomicAdd(&S->interactions, (unsigned long long)nah);
-      S->n_steps = step + 1;
-      S->az[p ^ 1][0] = azn;
-      S->az[p ^ 1][1] = azn;
+      if (rank == 0) {
+        atomicAdd(&S->interactions, (unsigned long long)nah);
+        S->n_steps = step + 1;
+        S->az[p ^ 1][0] = azn;
+        S->az[p ^ 1][1] = azn;
+      }
     }
-    // keys: squared distance from the centre (non-negative doubles order like
-    // their bit patterns); retired holes and padding sort last
-    unsigned long long kmin = ~0ull, kmax = 0ull;
-    for (int t = tid; t < p2; t += nt) {
-      unsigned long long kv = ~0ull;
-      if (t < nh) {
-        const int64_t ai = S->base + t;
-        const int8_t st = __ldcg(a.A.cstate + S->base + a.A.cid[ai]);
-        if ((st & kStateMask) == kStateActive) {
-          const double dx = __ldcg(a.A.px + ai) - sx, dy = __ldcg(a.A.py + ai) - sy,
-                       dz = __ldcg(a.A.pz + ai) - sz;
-          kv = (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz);
-          kmin = min(kmin, kv);
-          kmax = max(kmax, kv);
+    // keys of the own holes (retired holes: kNone) and their FP32 offsets
+    for (int t = lo + tid; t < hi; t += nt) {
+      unsigned long long kv = kNone;
+      if ((act[t - lo] & kStateMask) == kStateActive) {
+        const int64_t ai = base + t;
+        const int id = a.A.cid[ai];
+        const double dx = __ldcg(a.A.px + ai) - sx, dy = __ldcg(a.A.py + ai) - sy,
+                     dz = __ldcg(a.A.pz + ai) - sz;
+        kv = (unsigned long long)__double_as_longlong(dx * dx + dy * dy + dz * dz);
+        off[ai] = make_float4((float)dx, (float)dy, (float)dz, __int_as_float(id));
+      }
+      kscr[2 * (base + t)] = kv;
+    }
+    cl.sync();
+    // 3. all keys of the event: the bin counts and the keys' range (which
+    // sets the next step's bins; at a chunk's first step, in a pass of its
+    // own, this step's)
+    {
+      unsigned long long blo = s_lo;
+      int shift = s_shift;
+      if (kq == 0) {
+        unsigned long long klo = kNone, khi = 0ull;
+        for (int t = tid; t < nh; t += nt) {
+          const unsigned long long kv = __ldcg(kscr + 2 * (base + t));
+          if (kv != kNone) {
+            klo = min(klo, kv);
+            khi = max(khi, kv);
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          klo = min(klo, shfl_down_u64(klo, o));
+          khi = max(khi, shfl_down_u64(khi, o));
+        }
+        if (lane == 0 && klo != kNone) {
+          atomicMin(&s_rng[0], klo);
+          atomicMax(&s_rng[1], khi);
+        }
+        __syncthreads();
+        blo = s_rng[0];
+        shift = sph_shift(s_rng[0], s_rng[1]);
+        if (tid == 0) {
+          s_lo = blo;
+          s_shift = shift;
         }
       }
-      key[t] = kv;
-      idx[t] = t;
+      unsigned long long klo = kNone, khi = 0ull;
+      for (int t = tid; t < nh; t += nt) {
+        const unsigned long long kv = __ldcg(kscr + 2 * (base + t));
+        if (kv != kNone) {
+          atomicAdd(&bcount[sph_bin(kv, blo, shift)], 1);
+          klo = min(klo, kv);
+          khi = max(khi, kv);
+        }
+      }
+      if (kq > 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+          klo = min(klo, shfl_down_u64(klo, o));
+          khi = max(khi, shfl_down_u64(khi, o));
+        }
+        if (lane == 0 && klo != kNone) {
+          atomicMin(&s_rng[0], klo);
+          atomicMax(&s_rng[1], khi);
+        }
+      }
     }
-    for (int b = tid; b < kSphBins; b += nt) bcount[b] = 0;
-    block_minmax_u64(kmin, kmax, ured);
-    // bins of equal width in key space: the smallest shift with fewer than
-    // kSphBins bins over [kmin, kmax]
-    int shift = 0;
-    while (((kmax - kmin) >> shift) >= (unsigned long long)kSphBins) ++shift;
-    if (tid == 0) s_fallback = 0;
     __syncthreads();
-    for (int t = tid; t < nh; t += nt)
-      if (key[t] != ~0ull) atomicAdd(&bcount[(int)((key[t] - kmin) >> shift)], 1);
-    __syncthreads();
-    // exclusive scan of the bin counts (kSphBins / nt per thread), and the
+    const unsigned long long blo = s_lo;
+    const int shift = s_shift;
+    // exclusive scan of the bin counts (kSphBins / nt per thread) and the
     // fullest bin
     {
       constexpr int kPer = kSphBins / 1024;
       int local[kPer], acc = 0, most = 0;
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
-        local[q] = tid * kPer + q < kSphBins ? bcount[tid * kPer + q] : 0;
+        local[q] = bcount[tid * kPer + q];
         most = max(most, local[q]);
         acc += local[q];
       }
-      const int lane = tid & 31, warp = tid >> 5;
       int incl = acc;
       for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -2036,7 +2169,7 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
       }
       most = __reduce_max_sync(0xffffffffu, most);
       if (lane == 31) wsum[warp] = incl;
-      if (lane == 0 && most > kSphBinMax) s_fallback = 1;
+      if (lane == 0) atomicMax(&s_most, most);
       __syncthreads();
       if (tid == 0) {
         int run = 0;
@@ -2047,86 +2180,119 @@ __global__ void __launch_bounds__(1024, 1) spherical_kernel(StepArgs a, int k0, 
         }
       }
       __syncthreads();
-      int base = wsum[warp] + incl - acc;
+      int bs = wsum[warp] + incl - acc;
 #pragma unroll
       for (int q = 0; q < kPer; ++q) {
-        if (tid * kPer + q < kSphBins) bstart[tid * kPer + q] = base;
-        base += local[q];
+        bstart[tid * kPer + q] = bs;
+        bs += local[q];
+        bcount[tid * kPer + q] = 0;
       }
     }
     __syncthreads();
-    const bool fallback = s_fallback != 0;
-    if (!fallback) {
-      // each bin's holes in bin order (the order within a bin does not
-      // matter: a hole counts the smaller keys of its bin)
-      for (int b = tid; b < kSphBins; b += nt) bcount[b] = 0;
-      __syncthreads();
-      for (int t = tid; t < nh; t += nt)
-        if (key[t] != ~0ull) {
-          const int b = (int)((key[t] - kmin) >> shift);
-          idx[bstart[b] + atomicAdd(&bcount[b], 1)] = t;
-        }
-      __syncthreads();
-    } else {
-      for (int size = 2; size <= p2; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-          for (int t = tid; t < (p2 >> 1); t += nt) {
-            const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
-            const bool up = (lo & size) == 0;
-            const unsigned long long kl = key[lo], kh = key[hi];
-            if ((kl > kh) == up) {
-              key[lo] = kh;
-              key[hi] = kl;
-              const int32_t il = idx[lo];
-              idx[lo] = idx[hi];
-              idx[hi] = il;
-            }
-          }
-          __syncthreads();
-        }
-    }
-    // field and update: with the counting pass hole t by its own index, with
-    // the sort by sorted position (positions >= nah hold retired holes, with
-    // a parked shadow only, and padding entries, skipped)
+    const bool fallback = s_most > kSphBinMax;
     const float kcf = ph.f_kc;
     const double azn = s_azn;
     double qi = 0.0;
     double qpx[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int j = tid; j < (fallback ? p2 : nh); j += nt) {
-      const int t = fallback ? idx[j] : j;
-      if (t >= nh) continue;
-      const int64_t ai = S->base + t;
-      float ex = 0.0f, ey = 0.0f, ez = 0.0f;
-      const unsigned long long kt = fallback ? key[j] : key[t];
-      int q = 0;
-      if (kt != ~0ull && ph.repulsion) {
-        if (fallback) {
-          q = j;
-          while (q > 0 && key[q - 1] == kt) --q;
-        } else {
-          const int b = (int)((kt - kmin) >> shift);
-          q = bstart[b];
-          for (int u = bstart[b]; u < bstart[b] + bcount[b]; ++u) q += key[idx[u]] < kt;
+    if (!fallback) {
+      // each bin's keys (the order within a bin does not matter: a hole
+      // counts the smaller keys of its bin)
+      for (int t = tid; t < nh; t += nt) {
+        const unsigned long long kv = __ldcg(kscr + 2 * (base + t));
+        if (kv != kNone) {
+          const int b = sph_bin(kv, blo, shift);
+          kb[bstart[b] + atomicAdd(&bcount[b], 1)] = kv;
         }
       }
-      if (q > 0) {
-        // offsets and the enclosed count in FP64, the field itself in FP32
-        // like the pairwise path (FP64 sqrt and division are slow here)
-        const float dx = (float)(__ldcg(a.A.px + ai) - sx),
-                    dy = (float)(__ldcg(a.A.py + ai) - sy),
-                    dz = (float)(__ldcg(a.A.pz + ai) - sz);
-        const float rs = rsqrtf((float)__longlong_as_double((long long)kt));
-        const float f = kcf * (float)q * rs * rs * rs;
-        ex = f * dx;
-        ey = f * dy;
-        ez = f * dz;
+      __syncthreads();
+      // 4. field and update of the own active holes (key, offset, id and
+      // position loads issued together)
+      for (int t = tid; t < m; t += nt) {
+        if ((act[t] & kStateMask) != kStateActive) continue;
+        const int64_t ai = base + lo + t;
+        const unsigned long long kt = __ldcg(kscr + 2 * ai);
+        const float4 o = off[ai];
+        const double x = __ldcg(a.A.px + ai), y = __ldcg(a.A.py + ai), z = __ldcg(a.A.pz + ai);
+        float ex = 0.0f, ey = 0.0f, ez = 0.0f;
+        int q = 0;
+        if (ph.repulsion) {
+          const int b = sph_bin(kt, blo, shift);
+          const int s0 = bstart[b], s1 = s0 + bcount[b];
+          q = s0;
+          for (int u = s0; u < s1; ++u) q += kb[u] < kt;
+        }
+        if (q > 0) {
+          // offsets and the enclosed count from FP64 positions, the field
+          // itself in FP32 like the pairwise path
+          const float rs = rsqrtf((float)__longlong_as_double((long long)kt));
+          const float f = kcf * (float)q * rs * rs * rs;
+          ex = f * o.x;
+          ey = f * o.y;
+          ez = f * o.z;
+        }
+        bool gone = false;
+        qi += update_carrier_at<PX ? 2 : 1, false>(a, S, slot, 0, ai, __float_as_int(o.w), act[t],
+                                                    x, y, z, step, p, k, ex, ey, ez, azn, qpx,
+                                                    &gone);
+        if (gone) act[t] = (int8_t)kStateCollected;
       }
-      qi += update_carrier<PX ? 2 : 1>(a, S, slot, 0, ai, step, p, k, ex, ey, ez, azn, qpx);
+    } else {
+      // every CTA ranks all keys by a bitonic sort (padding and retired
+      // holes sort last) and updates its own holes
+      for (int t = tid; t < p2; t += nt) {
+        kb[t] = t < nh ? __ldcg(kscr + 2 * (base + t)) : kNone;
+        idx[t] = (uint16_t)t;
+      }
+      __syncthreads();
+      for (int size = 2; size <= p2; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+          for (int t = tid; t < (p2 >> 1); t += nt) {
+            const int l0 = 2 * t - (t & (stride - 1)), h0 = l0 + stride;
+            const bool up = (l0 & size) == 0;
+            const unsigned long long kl = kb[l0], kh = kb[h0];
+            if ((kl > kh) == up) {
+              kb[l0] = kh;
+              kb[h0] = kl;
+              const uint16_t il = idx[l0];
+              idx[l0] = idx[h0];
+              idx[h0] = il;
+            }
+          }
+          __syncthreads();
+        }
+      for (int j = tid; j < p2; j += nt) {
+        const int t = idx[j];
+        const unsigned long long kt = kb[j];
+        if (t < lo || t >= hi || kt == kNone) continue;
+        const int64_t ai = base + t;
+        const float4 o = off[ai];
+        const double x = __ldcg(a.A.px + ai), y = __ldcg(a.A.py + ai), z = __ldcg(a.A.pz + ai);
+        float ex = 0.0f, ey = 0.0f, ez = 0.0f;
+        int q = 0;
+        if (ph.repulsion) {
+          q = j;
+          while (q > 0 && kb[q - 1] == kt) --q;
+        }
+        if (q > 0) {
+          const float rs = rsqrtf((float)__longlong_as_double((long long)kt));
+          const float f = kcf * (float)q * rs * rs * rs;
+          ex = f * o.x;
+          ey = f * o.y;
+          ez = f * o.z;
+        }
+        bool gone = false;
+        qi += update_carrier_at<PX ? 2 : 1, false>(a, S, slot, 0, ai, __float_as_int(o.w),
+                                                    act[t - lo], x, y, z, step, p, k, ex, ey, ez,
+                                                    azn, qpx, &gone);
+        if (gone) act[t - lo] = (int8_t)kStateCollected;
+      }
     }
     add_induced(a, k, slot, qi);
     if constexpr (PX) add_induced_px(a, k, slot, qpx);
     __syncthreads();
   }
+  // the other CTAs may still read this CTA's group sums
+  cl.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -2456,23 +2622,64 @@ cudaError_t launch_bin_points(const Phys& ph, const double* x, const double* y, 
 }
 
 constexpr size_t kSphSmem =
-    (size_t)kSphMax * (sizeof(unsigned long long) + sizeof(int32_t)) + 2 * kSphBins * sizeof(int32_t);
+    (size_t)kSphMax * (sizeof(unsigned long long) + sizeof(uint16_t) + sizeof(int8_t)) +
+    2 * kSphBins * sizeof(int32_t) + (size_t)kSphGroups * 4 * sizeof(double);
+static_assert(kSphSmem <= 227 * 1024, "spherical kernel shared memory");
+
+// Largest number of resident clusters of C spherical CTAs (0 = unknown).
+int g_sph_clusters[5] = {0, 0, 0, 0, 0};
 
 cudaError_t spherical_prepare() {
-  const cudaError_t e = cudaFuncSetAttribute(
-      spherical_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSphSmem);
+  cudaError_t e = cudaFuncSetAttribute(spherical_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSphSmem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(spherical_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kSphSmem);
+  e = cudaFuncSetAttribute(spherical_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kSphSmem);
+  if (e != cudaSuccess) return e;
+  for (int c = 1; c <= 4; c <<= 1) {
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)c;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)c, 1, 1);
+    cfg.blockDim = dim3(1024, 1, 1);
+    cfg.dynamicSmemBytes = kSphSmem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    e = cudaOccupancyMaxActiveClusters(&n, spherical_kernel<false>, &cfg);
+    if (e != cudaSuccess) return e;
+    g_sph_clusters[c] = n;
+  }
+  return cudaSuccess;
 }
 
-cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, cudaStream_t s) {
+int spherical_cluster(int slots, int request) {
+  if (request == 1 || request == 2 || request == 4) return request;
+  // the widest cluster with which every slot's cluster is resident at once
+  for (int c = 4; c >= 2; c >>= 1)
+    if (slots <= g_sph_clusters[c]) return c;
+  return 1;
+}
+
+cudaError_t launch_spherical(const StepArgs& a, int k0, int nk, int cluster, cudaStream_t s) {
   if (a.S <= 0) return cudaSuccess;
-  if (a.induced_px)
-    spherical_kernel<true><<<a.S, 1024, kSphSmem, s>>>(a, k0, nk);
-  else
-    spherical_kernel<false><<<a.S, 1024, kSphSmem, s>>>(a, k0, nk);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(a.S * cluster), 1, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = kSphSmem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (a.induced_px) return cudaLaunchKernelEx(&cfg, spherical_kernel<true>, a, k0, nk);
+  return cudaLaunchKernelEx(&cfg, spherical_kernel<false>, a, k0, nk);
 }
 
 cudaError_t launch_generate(const GenEvent* ev, int n_events, double pitch_um, int grid_n,

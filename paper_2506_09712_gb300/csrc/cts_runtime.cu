@@ -197,6 +197,7 @@ struct sim_t {
   std::vector<int64_t> table_min;
   std::vector<int> table_var;
   int base_variant = 0;
+  int sph_cluster = 1;  // CTAs per event of the spherical model
   std::string autotune_cache;  // copied from the options
   std::string device_name;
 
@@ -760,12 +761,13 @@ int issue_chunk(sim_t* s, int K, bool multi) {
   if (s->d_induced_px)
     CK(cudaMemsetAsync(s->d_induced_px, 0, (size_t)K * s->S * 9 * sizeof(double), s->stream));
   if (s->field.spherical) {
-    // the spherical model: one CTA per slot runs all K steps of its event
+    // the spherical model: one cluster of CTAs per slot runs all K steps of
+    // its event
     const StepArgs a = step_args(s, true);
     const bool timed = s->opt.time_launches != 0 && !plain;
     const unsigned evflag = capturing(s) ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (timed) CK(cudaEventRecordWithFlags(s->lev[0], s->stream, evflag));
-    CK(launch_spherical(a, 0, K, s->stream));
+    CK(launch_spherical(a, 0, K, s->sph_cluster, s->stream));
     if (timed) CK(cudaEventRecordWithFlags(s->lev[1], s->stream, evflag));
     s->st_launch += 1;
   } else if (plain) {
@@ -1339,6 +1341,9 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
       opt.max_carriers < 0 || opt.hbm_budget_bytes < 0 || opt.queue_capacity < 0 ||
       opt.variant < 0 || opt.variant > variant_count())
     return SIM_EINVAL;
+  if (opt.sph_cluster != 0 && opt.sph_cluster != 1 && opt.sph_cluster != 2 &&
+      opt.sph_cluster != 4)
+    return SIM_EINVAL;
   if (opt.keep_induced < 0 || opt.keep_induced > (SIM_INDUCED_TOTAL | SIM_INDUCED_PIXELS))
     return SIM_EINVAL;
   // the 3 x 3 window around the centre pixel must lie inside the grid
@@ -1397,7 +1402,10 @@ int sim_init(const sim_sensor_t* sensor, const sim_field_t* field, const sim_mob
     }
   }
   if (!rc) rc = set_variant(s, choose_variant(s));
-  if (!rc && s->field.spherical && spherical_prepare() != cudaSuccess) rc = SIM_ECUDA;
+  if (!rc && s->field.spherical) {
+    if (spherical_prepare() != cudaSuccess) rc = SIM_ECUDA;
+    else s->sph_cluster = spherical_cluster(s->S, s->opt.sph_cluster);
+  }
   s->base_variant = s->variant;
   {
     cudaDeviceProp prop{};
@@ -1694,6 +1702,7 @@ int sim_get_stats(sim_t* s, sim_stats_t* o) {
   o->h2d_bytes = s->st_h2d;
   o->d2h_bytes = s->st_d2h;
   o->symmetric = s->sym ? 1 : 0;
+  o->sph_cluster = s->field.spherical ? s->sph_cluster : 0;
   return SIM_OK;
 }
 

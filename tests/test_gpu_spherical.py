@@ -1,6 +1,7 @@
 """The simplified spherical model (Sec. 2.2, Eq. 7) on the GPU against the
 oracle: trajectories carrier by carrier, whole events pixel by pixel, the
-launch modes, and the size limit of the in-shared-memory sort."""
+launch modes, the width of the cluster an event is split over, and the size
+limit of the keys held in shared memory."""
 import math
 
 import numpy as np
@@ -52,13 +53,48 @@ def _compare(gpu, ref, n):
 
 
 def test_spherical_events_match_the_oracle():
+    # a handle sized to the batch splits each event over a cluster of CTAs
     for name, k in (("plain_3keV_100um", 8), ("batch_20keV_320um", 3)):
         evs = W.make_events(name, n=k, first_id=40)
         refs = oracle.run_events(_params(name), evs)
-        with _sim(name) as sim:
+        with _sim(name, max_slots=k) as sim:
             got = sim.run(evs)
+            assert sim.stats()["sph_cluster"] > 1
         for g, r in zip(got, refs):
             _compare(g, r, g["n_carriers"])
+
+
+def test_spherical_results_do_not_depend_on_the_cluster_width():
+    # each event's holes split over 1, 2 or 4 CTAs: the centre's group sums
+    # are added in a fixed order and the enclosed counts are exact, so the
+    # results agree bit for bit
+    name = "batch_20keV_320um"
+    evs = W.make_events(name, n=5, first_id=90)
+    outs = []
+    for c in (1, 2, 4):
+        with _sim(name, max_slots=len(evs), sph_cluster=c, keep_final_xy=1) as sim:
+            outs.append(sim.run(evs, keep_xy_capacity=5525))
+            assert sim.stats()["sph_cluster"] == c
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert a["status"] == b["status"] == 0
+            assert a["n_steps"] == b["n_steps"] and a["interactions"] == b["interactions"]
+            assert np.array_equal(a["pixels"], b["pixels"])
+            assert np.array_equal(a["retire_step"], b["retire_step"])
+            assert np.array_equal(a["final_xy"], b["final_xy"])
+
+
+def test_spherical_cluster_width_option():
+    name = "plain_3keV_100um"
+    with _sim(name, max_slots=512) as sim:
+        assert sim.stats()["sph_cluster"] == 1
+    with _sim(name, mode=cts.CTS_MODE_PLAIN) as sim:
+        assert sim.stats()["sph_cluster"] == 4
+    p = W.preset(name)
+    for bad in (3, 8, -1):
+        with pytest.raises(cts.SimError) as e:
+            cts.Simulator(p["sensor"], p["mobility"], SPH, sph_cluster=bad)
+        assert e.value.code == cts.SIM_EINVAL
 
 
 def test_spherical_modes_agree_exactly():
@@ -88,11 +124,13 @@ def test_spherical_rejects_events_beyond_the_sort_size():
         assert r["status"] == 0 and r["n_carriers"] == 16384
 
 
-def test_spherical_equal_radii_take_the_sorting_path():
+@pytest.mark.parametrize("cluster", [1, 2, 4])
+def test_spherical_equal_radii_take_the_sorting_path(cluster):
     # 300 holes at one radius and 300 at a larger one (the six axis points
     # (+-a, 0, 0), (0, +-a, 0), (0, 0, +-a) repeated, so the centre is 0 and
     # the squared radii are equal to the bit): the counting pass finds more
-    # than 256 holes in one bin and ranks by sorting.  Equal radii do not
+    # than 256 holes in one bin and the cluster's first CTA ranks all holes
+    # by sorting.  Equal radii do not
     # count each other: the inner shell feels no field, the outer one the
     # inner 300.  One step without drift and diffusion, constant mobility.
     name = "batch_20keV_320um"
@@ -105,7 +143,7 @@ def test_spherical_equal_radii_take_the_sorting_path():
     xyz = np.concatenate([np.tile(axes * 0.5, (50, 1)), np.tile(axes * 2.0, (50, 1))]) + centre
     ev = W.explicit_event(xyz, seed=5, event_id=7)
     ref = oracle.run_event(oracle.make_params(dict(p["sensor"], max_steps=1), field, mob), ev)
-    with cts.Simulator(p["sensor"], mob, field) as sim:
+    with cts.Simulator(p["sensor"], mob, field, sph_cluster=cluster) as sim:
         pos, st, done = sim.trajectory(dict(ev, n_carriers=600), 1)
     assert done == ref.n_steps == 1
     assert np.array_equal(st, ref.state)
