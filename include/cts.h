@@ -127,7 +127,7 @@ typedef struct sim_options_t {
   int32_t queue_capacity;  /* bound of the admission queue (default 65536) */
   int32_t variant;         /* pair-kernel variant + 1; 0 = default choice: per
                               chunk, the symmetric kernel (variant 13) when
-                              the running events hold at least 6.4e8 carrier
+                              the running events hold at least 2.8e8 carrier
                               pairs (sum of N^2), the per-pair kernel
                               (variant 2) below that; PLAIN: variant 1 */
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */

@@ -38,10 +38,11 @@ constexpr int kDefaultSlots = 256;
 constexpr int kDefaultK = 32;
 constexpr size_t kLaunchLogCap = size_t(1) << 20;
 constexpr int64_t kDefaultBudget = 1ll << 30;
-// Default kernel choice per chunk (measured on the 20 keV batch: the
-// symmetric kernel is faster from about 21 resident events of 5525 carriers,
-// i.e. 6.4e8 carrier pairs, and slower below)
-constexpr double kSymMinWork = 6.4e8;
+// Default kernel choice per chunk (measured launch by launch on the 20 keV
+// batch, 32-step chunks: the symmetric kernel is faster down to about 13
+// running events of partly collected clouds, 2.9e8 carrier pairs per step,
+// and slower from 12 events, 2.6e8 pairs, down)
+constexpr double kSymMinWork = 2.8e8;
 constexpr int kSymVariant = 12;  // sym_nt256_r8_warp (8 warps per SM: as fast as 12 on the
                                  // 20 keV batch, 6 % faster on the 200 keV tracks)
 constexpr int kPairVariant = 1;  // nt256_r2_jpair_dyn
