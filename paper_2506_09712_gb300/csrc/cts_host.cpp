@@ -236,6 +236,83 @@ void sym_shape(int ntiles, int* rb, int* rj) {
   }
 }
 
+namespace {
+
+// The plan of one slot with th hole tiles and te electron tiles: its pair
+// units longest first (partials numbered from 0), its update units, and the
+// partial lists of its tiles in unit order.
+SymSlotTemplate sym_slot_template(int th, int te) {
+  constexpr int B = kSymPlanTpb;
+  SymSlotTemplate T;
+  int rb, rj;
+  sym_shape(th + te, &rb, &rj);
+  std::vector<SymUnitPlan> su;
+  std::vector<int64_t> work;
+  auto rows = [&](int spec_i, int nti, int spec_j, int ntj, bool same) {
+    const int nb = (nti + B - 1) / B;
+    for (int b0 = 0; b0 < nb; b0 += rb) {
+      const int b1 = std::min(b0 + rb, nb);
+      for (int g = same ? b0 * B : 0; g < ntj; g += rj) {
+        const int g1 = std::min(g + rj, ntj);
+        int64_t w = 0;  // tile pairs evaluated
+        for (int b = b0; b < b1; ++b) {
+          const int lo = same ? std::max(g, b * B) : g;
+          w += (int64_t)std::max(g1 - lo, 0) * std::min(B, nti - b * B);
+        }
+        su.push_back(SymUnitPlan{0, spec_i, spec_j, b0, b1, g, g1, 0, 0, 0, 0, 0});
+        work.push_back(w);
+      }
+    }
+  };
+  rows(0, th, 0, th, true);
+  if (te > 0) {
+    rows(0, th, 1, te, false);
+    rows(1, te, 1, te, true);
+  }
+  // the slot's pair units longest first; its first unit does the
+  // bookkeeping of a launch's first step
+  std::vector<int> order(su.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  for (size_t k = 0; k < order.size(); ++k) {
+    SymUnitPlan u = su[order[k]];
+    u.duty = k == 0;
+    u.p_i = (int32_t)T.n_partials;
+    T.n_partials += (int64_t)(u.ib1 - u.ib0) * B;
+    u.p_j = (int32_t)T.n_partials;
+    T.n_partials += u.jt1 - u.jt0;
+    T.pair.push_back(u);
+  }
+  // update units: a few tiles each (at most 64 units a slot)
+  const int nt = th + te;
+  const int tu = std::max(kSymPlanUpdateTiles, (nt + 63) / 64);
+  for (int t = 0; t < nt; t += tu)
+    T.upd.push_back(SymUnitPlan{0, 0, 0, 0, 0, t, std::min(t + tu, nt), 0, 0, 0, 1,
+                                (int32_t)T.pair.size()});
+  // per-tile partial lists, in unit order
+  auto each = [&](const SymUnitPlan& u, auto&& f) {
+    const int nti = u.spec_i ? te : th;
+    const int ti0 = u.spec_i ? th : 0, tj0 = u.spec_j ? th : 0;
+    for (int b = u.ib0; b < u.ib1; ++b)
+      for (int q = 0; q < B && b * B + q < nti; ++q) f(ti0 + b * B + q, u.p_i + (b - u.ib0) * B + q);
+    for (int g = u.jt0; g < u.jt1; ++g) f(tj0 + g, u.p_j + (g - u.jt0));
+  };
+  T.lcnt.assign((size_t)nt, 0);
+  for (const SymUnitPlan& u : T.pair) each(u, [&](int t, int) { T.lcnt[(size_t)t]++; });
+  std::vector<int32_t> start((size_t)nt, 0), fill((size_t)nt, 0);
+  int64_t acc = 0;
+  for (int t = 0; t < nt; ++t) {
+    start[(size_t)t] = (int32_t)acc;
+    acc += T.lcnt[(size_t)t];
+  }
+  T.lists.assign((size_t)acc, -1);
+  for (const SymUnitPlan& u : T.pair)
+    each(u, [&](int t, int pp) { T.lists[(size_t)(start[(size_t)t] + fill[(size_t)t]++)] = pp; });
+  return T;
+}
+
+}  // namespace
+
 int plan_sym(const int32_t* n_h, const int32_t* n_e, int n_slots, int max_units, SymPlan* out) {
   out->units.clear();
   out->tiles.clear();
@@ -244,102 +321,59 @@ int plan_sym(const int32_t* n_h, const int32_t* n_e, int n_slots, int max_units,
   out->slot_ntiles.assign((size_t)std::max(n_slots, 0), 0);
   out->n_partials = 0;
   if (n_slots < 0 || max_units <= 0) return -1;
-  constexpr int T = kSymPlanTile, B = kSymPlanTpb;
-  std::vector<int32_t> th_of((size_t)n_slots, 0);
-  std::vector<std::vector<SymUnitPlan>> upd;   // update units of each planned slot
+  constexpr int T = kSymPlanTile;
+  std::vector<std::pair<int, const SymSlotTemplate*>> upd;  // update units still to place
+  size_t upd_head = 0;
+  auto place_updates = [&](const std::pair<int, const SymSlotTemplate*>& e) {
+    for (SymUnitPlan u : e.second->upd) {
+      u.slot = e.first;
+      out->units.push_back(u);
+    }
+  };
   for (int s = 0; s < n_slots; ++s) {
     const int nh = std::max(n_h[s], 0), ne = std::max(n_e[s], 0);
     if (nh <= 0) continue;  // an event with no hole is finished
     const int th = (nh + T - 1) / T, te = (ne + T - 1) / T;
-    th_of[s] = th;
+    auto it = out->memo.find({th, te});
+    if (it == out->memo.end()) it = out->memo.emplace(std::make_pair(th, te), sym_slot_template(th, te)).first;
+    const SymSlotTemplate& st = it->second;
+    const int64_t pbase = out->n_partials;
+    if (pbase + st.n_partials > INT32_MAX) return -2;
+    const int64_t lbase = (int64_t)out->lists.size();
     out->slot_tile0[s] = (int32_t)out->tiles.size();
     out->slot_ntiles[s] = th + te;
-    for (int spec = 0; spec < 2; ++spec) {
+    int64_t lp = lbase;
+    for (int spec = 0, q = 0; spec < 2; ++spec) {
       const int n = spec ? ne : nh, nt = spec ? te : th;
-      for (int t = 0; t < nt; ++t)
-        out->tiles.push_back(SymTilePlan{s, spec, t, std::min(T, n - T * t), 0, 0});
-    }
-    int rb, rj;
-    sym_shape(th + te, &rb, &rj);
-    std::vector<SymUnitPlan> su;
-    std::vector<int64_t> work;
-    auto rows = [&](int spec_i, int nti, int spec_j, int ntj, bool same) {
-      const int nb = (nti + B - 1) / B;
-      for (int b0 = 0; b0 < nb; b0 += rb) {
-        const int b1 = std::min(b0 + rb, nb);
-        for (int g = same ? b0 * B : 0; g < ntj; g += rj) {
-          const int g1 = std::min(g + rj, ntj);
-          int64_t w = 0;  // tile pairs evaluated
-          for (int b = b0; b < b1; ++b) {
-            const int lo = same ? std::max(g, b * B) : g;
-            w += (int64_t)std::max(g1 - lo, 0) * std::min(B, nti - b * B);
-          }
-          su.push_back(SymUnitPlan{s, spec_i, spec_j, b0, b1, g, g1, 0, 0, 0, 0, 0});
-          work.push_back(w);
-        }
+      for (int t = 0; t < nt; ++t, ++q) {
+        const int32_t lc = st.lcnt[(size_t)q];
+        out->tiles.push_back(SymTilePlan{s, spec, t, std::min(T, n - T * t), (int32_t)lp, lc});
+        lp += lc;
       }
-    };
-    rows(0, th, 0, th, true);
-    if (te > 0) {
-      rows(0, th, 1, te, false);
-      rows(1, te, 1, te, true);
     }
-    // the slot's pair units longest first; its first unit does the
-    // bookkeeping of a launch's first step
-    std::vector<int> order(su.size());
-    for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
-    for (size_t k = 0; k < order.size(); ++k) {
-      SymUnitPlan u = su[order[k]];
-      u.duty = k == 0;
-      u.p_i = (int32_t)out->n_partials;
-      out->n_partials += (int64_t)(u.ib1 - u.ib0) * B;
-      u.p_j = (int32_t)out->n_partials;
-      out->n_partials += u.jt1 - u.jt0;
-      out->units.push_back(u);
+    const size_t l0 = out->lists.size(), nl = st.lists.size();
+    out->lists.resize(l0 + nl);
+    int32_t* ld = out->lists.data() + l0;
+    const int32_t pb = (int32_t)pbase;
+    for (size_t q = 0; q < nl; ++q) ld[q] = st.lists[q] + pb;
+    const size_t u0 = out->units.size(), nu = st.pair.size();
+    out->units.resize(u0 + nu);
+    SymUnitPlan* ud = out->units.data() + u0;
+    for (size_t q = 0; q < nu; ++q) {
+      ud[q] = st.pair[q];
+      ud[q].slot = s;
+      ud[q].p_i += pb;
+      ud[q].p_j += pb;
     }
-    // update units: a few tiles each (at least 2, at most 64 units a slot)
-    const int nt = th + te;
-    const int tu = std::max(kSymPlanUpdateTiles, (nt + 63) / 64);
-    upd.emplace_back();
-    for (int t = 0; t < nt; t += tu)
-      upd.back().push_back(SymUnitPlan{s, 0, 0, 0, 0, t, std::min(t + tu, nt), 0, 0, 0, 1,
-                                       (int32_t)su.size()});
+    out->n_partials += st.n_partials;
     // a slot's update units follow the pair units of kSymPlanUpdateLag more
     // slots, so that its pair work is usually done when they are taken
-    if ((int)upd.size() > kSymPlanUpdateLag) {
-      for (const SymUnitPlan& u : upd.front()) out->units.push_back(u);
-      upd.erase(upd.begin());
-    }
+    upd.emplace_back(s, &st);
+    if (upd.size() - upd_head > (size_t)kSymPlanUpdateLag) place_updates(upd[upd_head++]);
     if ((int64_t)out->units.size() > max_units) return -2;
   }
-  for (const auto& us : upd)
-    for (const SymUnitPlan& u : us) out->units.push_back(u);
+  for (; upd_head < upd.size(); ++upd_head) place_updates(upd[upd_head]);
   if ((int64_t)out->units.size() > max_units) return -2;
-  if (out->n_partials > INT32_MAX) return -2;
-  // per-tile partial lists, in unit order
-  auto gtile = [&](int slot, int spec, int t) {
-    return out->slot_tile0[slot] + (spec ? th_of[slot] : 0) + t;
-  };
-  auto each = [&](const SymUnitPlan& u, auto&& f) {
-    const int nti = u.spec_i ? out->slot_ntiles[u.slot] - th_of[u.slot] : th_of[u.slot];
-    for (int b = u.ib0; b < u.ib1; ++b)
-      for (int q = 0; q < B && b * B + q < nti; ++q)
-        f(gtile(u.slot, u.spec_i, b * B + q), u.p_i + (b - u.ib0) * B + q);
-    for (int g = u.jt0; g < u.jt1; ++g) f(gtile(u.slot, u.spec_j, g), u.p_j + (g - u.jt0));
-  };
-  for (const SymUnitPlan& u : out->units)
-    if (u.kind == 0) each(u, [&](int t, int) { out->tiles[t].lcnt++; });
-  int64_t acc = 0;
-  for (SymTilePlan& t : out->tiles) {
-    t.lptr = (int32_t)acc;
-    acc += t.lcnt;
-  }
-  out->lists.assign((size_t)acc, -1);
-  std::vector<int32_t> fill(out->tiles.size(), 0);
-  for (const SymUnitPlan& u : out->units)
-    if (u.kind == 0)
-      each(u, [&](int t, int p) { out->lists[(size_t)out->tiles[t].lptr + fill[t]++] = p; });
   return 0;
 }
 

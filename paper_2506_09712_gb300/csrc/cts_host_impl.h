@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <map>
+#include <utility>
 #include <vector>
 
 namespace cts {
@@ -41,6 +42,15 @@ struct SymUnitPlan {
 struct SymTilePlan {
   int32_t slot, spec, tile, n, lptr, lcnt;
 };
+// The plan of one slot with th hole tiles and te electron tiles, numbered
+// from the slot's first partial and its first tile (slot field 0).
+struct SymSlotTemplate {
+  std::vector<SymUnitPlan> pair;   // pair units, longest first
+  std::vector<SymUnitPlan> upd;    // update units
+  std::vector<int32_t> lcnt;       // partials listed per tile (holes, then electrons)
+  std::vector<int32_t> lists;      // the slot's tile lists, tile after tile
+  int64_t n_partials = 0;
+};
 struct SymPlan {
   std::vector<SymUnitPlan> units;
   std::vector<SymTilePlan> tiles;
@@ -48,6 +58,8 @@ struct SymPlan {
   std::vector<int32_t> slot_tile0;    // global index of a slot's first tile (-1: none)
   std::vector<int32_t> slot_ntiles;   // tiles of the slot
   int64_t n_partials = 0;             // partial tiles the units write
+  // slot plans by (th, te), kept across calls on the same SymPlan
+  std::map<std::pair<int, int>, SymSlotTemplate> memo;
 };
 // Unit shape (I blocks x J tiles) of a slot with `ntiles` tiles.
 void sym_shape(int ntiles, int* rb, int* rj);
