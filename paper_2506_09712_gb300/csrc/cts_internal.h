@@ -238,7 +238,8 @@ struct StepArgs {
   int32_t* unit_counter;     // [K]: dynamic queue position per step (dynamic plans)
   int32_t dynamic;           // 1: pull units from unit_counter instead of cta_begin
   int32_t* ret;              // [K][S][2]
-  double* partial;           // FP64 partial sums of split tiles (3 x tile_i per piece)
+  double* partial;           // partial sums of split tiles: per piece 3 x tile_i entries of
+                             // 8 bytes, each the compensated FP32 pair (S, c) of a sum S - c
   int32_t* combine_count;    // per i-block
   int32_t* tiles_done;       // [K][S]: tiles of each slot updated at each chunk step
   float* field_out;          // FIELD_ONLY output, SoA [3][capacity]

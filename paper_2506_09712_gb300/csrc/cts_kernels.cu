@@ -172,6 +172,14 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
   return y;
 }
 
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly,
+// s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 
 // The pair loop over n staged sources: acc_i += (r_i - r_j) / (|r_i - r_j|^2 +
 // eps^2)^(3/2), or the reversed difference for sources of the opposite sign.
@@ -882,23 +890,26 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
       vz[r] = sz[r] - cz[r];
     }
 
-    // Completion of the tile: each piece writes its compensated sum (S - c of
-    // two FP32 values is exact in FP64) to its own FP64 slot; the CTA
-    // finishing the tile's last piece adds the pieces in piece order (the
-    // same bits every run), updates the tile's carriers and counts the tile
-    // as done.
+    // Completion of the tile: each piece writes its compensated sum, the
+    // pair (S, c) of FP32 values whose difference S - c it stands for, to
+    // its own slot; the CTA finishing the tile's last piece adds the pieces
+    // in piece order (the same bits every run) by error-free FP32 sums, the
+    // rounding errors and compensations gathered apart (Neumaier's form of
+    // compensated summation), updates the tile's carriers and counts the
+    // tile as done.  No FP64 arithmetic: it is slow on this GPU, and the
+    // last piece's CTA is on the step's critical path.
     bool last = true;
     if (U.nsplit > 1) {
-      double* acc = a.partial + U.pbase;
+      float2* acc = reinterpret_cast<float2*>(a.partial + U.pbase);
       if (!skip) {
-        double* mine = acc + (int64_t)U.split * 3 * TI;
+        float2* mine = acc + (int64_t)U.split * 3 * TI;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const int li = r * NT + tid;
           if (li < U.ni) {
-            mine[li] = (double)sx[r] - (double)cx[r];
-            mine[TI + li] = (double)sy[r] - (double)cy[r];
-            mine[2 * TI + li] = (double)sz[r] - (double)cz[r];
+            mine[li] = make_float2(sx[r], cx[r]);
+            mine[TI + li] = make_float2(sy[r], cy[r]);
+            mine[2 * TI + li] = make_float2(sz[r], cz[r]);
           }
         }
       }
@@ -917,16 +928,22 @@ __global__ void __launch_bounds__(NT, MINB) step_kernel(StepArgs a, int k0, int 
         for (int r = 0; r < R; ++r) {
           const int li = r * NT + tid;
           if (li < U.ni) {
-            double ex = 0.0, ey = 0.0, ez = 0.0;
+            float hx = 0.0f, hy = 0.0f, hz = 0.0f, lx = 0.0f, ly = 0.0f, lz = 0.0f;
             for (int k = 0; k < U.nsplit; ++k) {
-              const double* pk = acc + (int64_t)k * 3 * TI;
-              ex += __ldcg(pk + li);
-              ey += __ldcg(pk + TI + li);
-              ez += __ldcg(pk + 2 * TI + li);
+              const float2* pk = acc + (int64_t)k * 3 * TI;
+              const float2 px = __ldcg(pk + li), py = __ldcg(pk + TI + li),
+                           pz = __ldcg(pk + 2 * TI + li);
+              float e;
+              two_sum(hx, px.x, hx, e);
+              lx = __fadd_rn(lx, __fsub_rn(e, px.y));
+              two_sum(hy, py.x, hy, e);
+              ly = __fadd_rn(ly, __fsub_rn(e, py.y));
+              two_sum(hz, pz.x, hz, e);
+              lz = __fadd_rn(lz, __fsub_rn(e, pz.y));
             }
-            vx[r] = (float)ex;
-            vy[r] = (float)ey;
-            vz[r] = (float)ez;
+            vx[r] = __fadd_rn(hx, lx);
+            vy[r] = __fadd_rn(hy, ly);
+            vz[r] = __fadd_rn(hz, lz);
           }
         }
       }
