@@ -611,7 +611,7 @@ def run_ours(args, rank, world, local):
     dom_inter = inter * float(rows[:, 1].sum()) / covered
     kfpi = FLOPS_PER_INTERACTION_SYM if dominant_sym else FLOPS_PER_PAIR
     rate = dom_inter / (dom_ms * 1e-3) if dom_ms > 0 else None
-    # achieved: SURVEY's algorithmic 16 flops per interaction (the direct
+    # achieved: the algorithmic 16 flops per interaction (the direct
     # evaluation's); the flops the kernel itself executes are reported beside
     achieved = FLOPS_PER_PAIR * rate / 1e12 if rate else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
