@@ -651,7 +651,10 @@ def run_ours(args, rank, world, local):
             "config": dict(workload_config(args.workload, n_ev, world),
                            positions="f64", pair_field="f32 + Kahan",
                            l2="flushed (256 MiB write) before every timed step",
-                           variant=st["variant"], variant_table=table),
+                           variant=args.variant or
+                           "default: chosen per chunk, the symmetric kernel while the resident "
+                           "pair work fills the GPU, the per-pair kernel below",
+                           variant_table=table),
             "events_per_s": events_per_s,
             "roofline": roof, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
             "statuses_ok": all(s == 0 for s in statuses)}
