@@ -126,9 +126,11 @@ typedef struct sim_options_t {
   int64_t hbm_budget_bytes;/* device bytes the handle may allocate (default 1 GiB) */
   int32_t queue_capacity;  /* bound of the admission queue (default 65536) */
   int32_t variant;         /* pair-kernel variant + 1; 0 = default choice: per
-                              chunk, the symmetric kernel (variant 13) when
-                              the running events hold at least 2.8e8 carrier
-                              pairs (sum of N^2), the per-pair kernel
+                              chunk, the symmetric kernel when the running
+                              events hold at least 2.8e8 carrier pairs (sum
+                              of N^2) -- variant 1 (12 warps per SM), or 13
+                              (8 warps) once an event has more than 640
+                              tiles of 64 carriers -- the per-pair kernel
                               (variant 2) below that; PLAIN: variant 1 */
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
   int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */

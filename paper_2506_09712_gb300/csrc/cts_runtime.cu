@@ -43,8 +43,13 @@ constexpr int64_t kDefaultBudget = 1ll << 30;
 // running events of partly collected clouds, 2.9e8 carrier pairs per step,
 // and slower from 12 events, 2.6e8 pairs, down)
 constexpr double kSymMinWork = 2.8e8;
-constexpr int kSymVariant = 12;  // sym_nt256_r8_warp (8 warps per SM: as fast as 12 on the
-                                 // 20 keV batch, 6 % faster on the 200 keV tracks)
+// The symmetric kernel's warps per SM: 12 (two rotation steps per loop
+// iteration) while every running event has at most kSymLargeTiles tiles,
+// 1.8 % faster than 8 on the 20 keV batch; 8 once an event is larger (its
+// units are 8 blocks x 16 tiles; measured 6 % faster on the 200 keV tracks)
+constexpr int kSymVariant = 0;        // sym_nt384_r8_warp
+constexpr int kSymVariantLarge = 12;  // sym_nt256_r8_warp
+constexpr int kSymLargeTiles = 640;
 constexpr int kPairVariant = 1;  // nt256_r2_jpair_dyn
 constexpr int kSymVariantPlain = 0;  // sym_nt384_r8_warp
 constexpr int kMaxUnits = 1 << 16;
@@ -838,9 +843,15 @@ int run_chunk(sim_t* s) {
     // pair work fills the GPU, the per-pair kernel (finer work units, shorter
     // steps) below it; the events' state is the same for both
     double W = 0.0;
+    int max_tiles = 0;
     for (auto& h : s->slots)
-      if (h.used && h.running) W += (double)(h.n_h + h.n_e) * (double)(h.n_h + h.n_e);
-    int rcv = set_variant(s, W >= kSymMinWork ? kSymVariant : kPairVariant);
+      if (h.used && h.running) {
+        W += (double)(h.n_h + h.n_e) * (double)(h.n_h + h.n_e);
+        max_tiles = std::max(max_tiles, (h.n_h + kSymTile - 1) / kSymTile +
+                                            (h.n_e + kSymTile - 1) / kSymTile);
+      }
+    const int sym_v = max_tiles > kSymLargeTiles ? kSymVariantLarge : kSymVariant;
+    int rcv = set_variant(s, W >= kSymMinWork ? sym_v : kPairVariant);
     if (rcv) return rcv;
   }
   // one launch for the whole chunk: the queue replays the step's pieces K
