@@ -127,7 +127,7 @@ typedef struct sim_options_t {
   int32_t queue_capacity;  /* bound of the admission queue (default 65536) */
   int32_t variant;         /* pair-kernel variant + 1; 0 = default choice: per
                               chunk, the symmetric kernel when the running
-                              events hold at least 2.8e8 carrier pairs (sum
+                              events hold at least 4.0e8 carrier pairs (sum
                               of N^2) -- variant 1 (12 warps per SM), or 13
                               (8 warps) once an event has more than 640
                               tiles of 64 carriers -- the per-pair kernel

@@ -38,11 +38,12 @@ constexpr int kDefaultSlots = 256;
 constexpr int kDefaultK = 32;
 constexpr size_t kLaunchLogCap = size_t(1) << 20;
 constexpr int64_t kDefaultBudget = 1ll << 30;
-// Default kernel choice per chunk (measured launch by launch on the 20 keV
-// batch, 32-step chunks: the symmetric kernel is faster down to about 13
-// running events of partly collected clouds, 2.9e8 carrier pairs per step,
-// and slower from 12 events, 2.6e8 pairs, down)
-constexpr double kSymMinWork = 2.8e8;
+// Default kernel choice per chunk: the symmetric kernel from this many
+// resident carrier pairs per step (sum of N^2), the per-pair kernel below.
+// Whole 64-event 20 keV batches with the 12-warp symmetric kernel, 32-step
+// chunks: 462 / 458 / 452 / 448 ms with the switch at 1.2e8 / 1.8e8 / 2.8e8
+// / 4.0e8 pairs (about 17 partly collected events)
+constexpr double kSymMinWork = 4.0e8;
 // The symmetric kernel's warps per SM: 12 (two rotation steps per loop
 // iteration) while every running event has at most kSymLargeTiles tiles,
 // 1.8 % faster than 8 on the 20 keV batch; 8 once an event is larger (its
