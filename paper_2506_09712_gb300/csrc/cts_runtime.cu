@@ -116,7 +116,7 @@ struct sim_t {
   int S = 0, K = 0, variant = 0, grid = 0, tile_i = 0, dynamic = 0;
   bool sym = false;  // the current variant is the symmetric kernel
   int64_t capacity = 0, partial_cap = 0;
-  bool broken = false;
+  std::atomic<bool> broken{false};  // read by polling threads while the engine runs
   std::string err;
 
   // device buffers
@@ -190,7 +190,7 @@ struct sim_t {
   std::thread engine;
   std::atomic<bool> stop{false};
   int64_t order_counter = 0;
-  int inject = 0;
+  std::atomic<int> inject{0};  // set by sim_debug_inject from any thread
   std::vector<int> staged;  // slots admitted by sim_stage, in staging order
 
   // one captured K-step chunk per kernel variant and launch shape
@@ -1531,15 +1531,9 @@ int sim_poll(sim_t* s, sim_result_t* out, int max_out, int* n_out, int timeout_m
     }
     if (rc) return rc;
     if (!progressed) {
-      std::lock_guard<std::mutex> lk(s->dmu);
-      if (s->done.empty()) {
-        bool queued;
-        {
-          std::lock_guard<std::mutex> q(s->qmu);
-          queued = !s->queue.empty();
-        }
-        if (!queued || now_ns() > deadline) return SIM_ETIMEOUT;
-      }
+      // both queues at once, in the order sim_run takes them
+      std::scoped_lock lk(s->qmu, s->dmu);
+      if (s->done.empty() && (s->queue.empty() || now_ns() > deadline)) return SIM_ETIMEOUT;
     }
     if (now_ns() > deadline) {
       std::lock_guard<std::mutex> lk(s->dmu);
@@ -1555,8 +1549,7 @@ int sim_run(sim_t* s, const sim_event_t* ev, int n, sim_result_t* out) {
     std::lock_guard<std::mutex> dl(s->drive_mu);
     for (auto& h : s->slots)
       if (h.used) return SIM_ESTATE;
-    std::lock_guard<std::mutex> lk(s->qmu);
-    std::lock_guard<std::mutex> dk(s->dmu);
+    std::scoped_lock lk(s->qmu, s->dmu);
     if (!s->queue.empty() || !s->done.empty()) return SIM_ESTATE;
     first_order = s->order_counter;
   }
@@ -1603,8 +1596,7 @@ int sim_run(sim_t* s, const sim_event_t* ev, int n, sim_result_t* out) {
     }
     if (rc) return rc;
     if (!progressed) {
-      std::lock_guard<std::mutex> lk(s->dmu);
-      std::lock_guard<std::mutex> q(s->qmu);
+      std::scoped_lock lk(s->qmu, s->dmu);
       if (s->done.empty() && s->queue.empty() && submitted >= n) return SIM_ESTATE;
     }
   }
