@@ -131,7 +131,8 @@ typedef struct sim_options_t {
                               of N^2) -- variant 1 (12 warps per SM), or 13
                               (8 warps) once an event has more than 640
                               tiles of 64 carriers -- the per-pair kernel
-                              (variant 2) below that; PLAIN: variant 1 */
+                              (variant 2) below that; SERVE: variant 13 from
+                              2.8e8 pairs, else variant 2; PLAIN: variant 1 */
   int32_t disable_graphs;  /* 1 = launch K-step chunks directly, not as CUDA graphs */
   int32_t keep_final_xy;   /* 1 = keep collected (x, y) and retire steps for poll */
   int32_t time_launches;   /* 1 = time every step-kernel launch with CUDA events */

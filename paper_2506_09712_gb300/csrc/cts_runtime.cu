@@ -44,6 +44,12 @@ constexpr int64_t kDefaultBudget = 1ll << 30;
 // chunks: 462 / 458 / 452 / 448 ms with the switch at 1.2e8 / 1.8e8 / 2.8e8
 // / 4.0e8 pairs (about 17 partly collected events)
 constexpr double kSymMinWork = 4.0e8;
+// SERVE keeps the 8-warp symmetric kernel and the switch at 2.8e8 pairs: at
+// the moderate occupancy of a served stream (about 27 mixed events at 0.7x
+// saturation) its steps are shorter; the serving mix's p50 / p99 latency at
+// 0.7x saturation: 129 / 257 ms, against 141 / 298 ms with the 12-warp
+// kernel and the 4.0e8 switch (the same saturation rate, 259 events/s)
+constexpr double kSymMinWorkServe = 2.8e8;
 // The symmetric kernel's warps per SM: 12 (two rotation steps per loop
 // iteration) while every running event has at most kSymLargeTiles tiles,
 // 1.8 % faster than 8 on the 20 keV batch; 8 once an event is larger (its
@@ -851,8 +857,9 @@ int run_chunk(sim_t* s) {
         max_tiles = std::max(max_tiles, (h.n_h + kSymTile - 1) / kSymTile +
                                             (h.n_e + kSymTile - 1) / kSymTile);
       }
-    const int sym_v = max_tiles > kSymLargeTiles ? kSymVariantLarge : kSymVariant;
-    int rcv = set_variant(s, W >= kSymMinWork ? sym_v : kPairVariant);
+    const bool serve = s->opt.mode == CTS_MODE_SERVE;
+    const int sym_v = (serve || max_tiles > kSymLargeTiles) ? kSymVariantLarge : kSymVariant;
+    int rcv = set_variant(s, W >= (serve ? kSymMinWorkServe : kSymMinWork) ? sym_v : kPairVariant);
     if (rcv) return rcv;
   }
   // one launch for the whole chunk: the queue replays the step's pieces K
